@@ -1,0 +1,162 @@
+"""Pins for the oracle's sampler: Eq. (pois) with Eq. (pij-ot) / (pij-uot).
+
+- the binary32 decision probabilities agree with the FP64 definitions of
+  Eq. (pij-ot) and Eq. (pij-uot) up to binary32 rounding;
+- lambda -> infinity turns the UOT probabilities into the OT ones (sec. 3.3);
+- unbiasedness E[K~] = K and E[nnz] = sum p* <= s (sec. 3.2), Monte Carlo
+  over Philox seeds, and per-element inclusion frequencies (chi-square);
+- p* = 1 everywhere makes K~ = K and Spar-Sink identical to Sinkhorn;
+- the CSC is the stable transpose of the CSR.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_2306_06581_gb300 import inputs
+
+
+def _prob(orc, w, **kw):
+    args = dict(x=w.x, y=w.y, seed=w.seed, pid=w.pid)
+    args.update(kw)
+    return orc.OracleProblem(w.a, w.b, kw.pop("eps", w.eps), kw.pop("s", w.s), kw.pop("lam", w.lam),
+                             **{k: v for k, v in args.items() if k not in ("eps", "s", "lam")})
+
+
+def _sqdist(x, y):
+    return ((x[:, None, :] - y[None, :, :]) ** 2).sum(-1)
+
+
+def test_ot_probability_matches_definition(orc):
+    w = inputs.small_problem(n=40, m=50, d=3, seed=3)
+    P = orc.OracleProblem(w.a, w.b, w.eps, w.s, math.inf, x=w.x, y=w.y)
+    sq = np.sqrt(np.outer(w.a, w.b))
+    p_def = w.s * sq / sq.sum()                           # s p_ij, Eq. (pij-ot)
+    got = np.array([[P.pstar_raw(i, j) for j in range(w.m)] for i in range(w.n)], np.float64)
+    assert np.allclose(got, p_def, rtol=6e-7, atol=0)
+
+
+@pytest.mark.parametrize("lam,eps", [(1.0, 0.05), (0.1, 0.1), (5.0, 0.01)])
+def test_uot_probability_matches_definition(orc, lam, eps):
+    w = inputs.small_problem(n=30, m=35, d=4, seed=4, mass_b=1.5)
+    P = orc.OracleProblem(w.a, w.b, eps, w.s, lam, x=w.x, y=w.y)
+    C = _sqdist(w.x, w.y)
+    C = C / C.max()
+    K = np.exp(-C / eps)
+    g = lam / (2 * lam + eps)
+    num = np.outer(w.a, w.b) ** g * K ** (eps / (2 * lam + eps))   # Eq. (pij-uot) numerator
+    p_def = w.s * num / num.sum()
+    got = np.array([[P.pstar_raw(i, j) for j in range(w.m)] for i in range(w.n)], np.float64)
+    assert np.allclose(got, p_def, rtol=3e-6, atol=0)
+
+
+def test_uot_probability_tends_to_ot(orc):
+    w = inputs.small_problem(n=25, m=25, d=2, seed=5)
+    Pot = orc.OracleProblem(w.a, w.b, 0.1, w.s, math.inf, x=w.x, y=w.y)
+    Puot = orc.OracleProblem(w.a, w.b, 0.1, w.s, 1e7, x=w.x, y=w.y)
+    for i, j in [(0, 0), (3, 7), (24, 24), (11, 2)]:
+        assert abs(Puot.pstar_raw(i, j) / Pot.pstar_raw(i, j) - 1) < 1e-5
+
+
+def test_unbiased_and_expected_nnz(orc):
+    n, m = 10, 12
+    w = inputs.small_problem(n=n, m=m, d=2, seed=6, eps=0.5)
+    s = 40.0
+    K, _ = orc.OracleProblem(w.a, w.b, w.eps, s, math.inf, x=w.x, y=w.y).dense_kernel()
+    R = 3000
+    acc = np.zeros((n, m))
+    inc = np.zeros((n, m))
+    nnz = []
+    for r in range(R):
+        P = orc.OracleProblem(w.a, w.b, w.eps, s, math.inf, x=w.x, y=w.y, seed=1000 + r)
+        sk = P.sparsify()
+        rows = np.repeat(np.arange(n), np.diff(sk["row_ptr"]))
+        acc[rows, sk["col_idx"]] += sk["val"]
+        inc[rows, sk["col_idx"]] += 1
+        nnz.append(sk["nnz"])
+    P0 = orc.OracleProblem(w.a, w.b, w.eps, s, math.inf, x=w.x, y=w.y)
+    pst = np.array([[min(1.0, P0.pstar_raw(i, j)) for j in range(m)] for i in range(n)])
+    # E[nnz] = sum p* <= s
+    assert pst.sum() <= s * (1 + 1e-6)
+    sd_nnz = math.sqrt((pst * (1 - pst)).sum() / R)
+    assert abs(np.mean(nnz) - pst.sum()) < 5 * sd_nnz
+    # E[K~] = K, with Var K~_ij = K^2 (1/p* - 1)
+    mean = acc / R
+    sd = K * np.sqrt((1 / pst - 1) / R)
+    z = np.abs(mean - K) / np.where(sd > 0, sd, 1)
+    assert z.max() < 5.0
+    # inclusion frequencies: chi-square against p*
+    exp_inc = R * pst
+    mask = (pst > 0) & (pst < 1)
+    chi2 = (((inc - exp_inc) ** 2) / (exp_inc * (1 - pst)))[mask].sum()
+    assert chi2 < stats.chi2.ppf(0.9999, mask.sum())
+
+
+def test_all_included_reduces_to_sinkhorn(orc):
+    w = inputs.small_problem(n=30, m=20, d=3, seed=7, eps=0.2)
+    P = orc.OracleProblem(w.a, w.b, w.eps, 1e9, math.inf, x=w.x, y=w.y)
+    sk = P.sparsify()
+    assert sk["nnz"] == 30 * 20 and (sk["pstar"] == 1.0).all()
+    K, _ = P.dense_kernel()
+    assert np.array_equal(sk["val"].reshape(30, 20), K)
+    sp = orc.spar_sink(P, tol=1e-10, max_iter=2000, sketch=sk)
+    de = orc.dense_sinkhorn(P, tol=1e-10, max_iter=2000)
+    assert sp["info"]["iters"] == de["info"]["iters"]
+    assert np.allclose(sp["alpha"], de["alpha"], rtol=0, atol=1e-12)
+    assert abs(sp["obj"] - de["obj"]) < 1e-12
+    assert sp["obj"] == sp["obj_sparse"]
+
+
+def test_csc_is_stable_transpose(orc):
+    w = inputs.small_problem(n=70, m=90, d=3, seed=8)
+    sk = orc.OracleProblem(w.a, w.b, w.eps, 2000.0, math.inf, x=w.x, y=w.y).sparsify()
+    n, m = 70, 90
+    D = np.zeros((n, m))
+    rows = np.repeat(np.arange(n), np.diff(sk["row_ptr"]))
+    D[rows, sk["col_idx"]] = sk["val"]
+    DT = np.zeros((n, m))
+    cols = np.repeat(np.arange(m), np.diff(sk["col_ptr"]))
+    DT[sk["row_idx"], cols] = sk["valT"]
+    assert np.array_equal(D, DT)
+    for j in range(m):
+        seg = sk["row_idx"][sk["col_ptr"][j]:sk["col_ptr"][j + 1]]
+        assert (np.diff(seg) > 0).all()
+    for i in range(n):
+        seg = sk["col_idx"][sk["row_ptr"][i]:sk["row_ptr"][i + 1]]
+        assert (np.diff(seg) > 0).all()
+    assert np.array_equal(sk["val"][sk["perm"]], sk["valT"])
+
+
+def test_values_and_log_values(orc):
+    w = inputs.small_problem(n=50, m=40, d=5, seed=9, eps=0.05)
+    P = orc.OracleProblem(w.a, w.b, w.eps, 300.0, math.inf, x=w.x, y=w.y)
+    sk = P.sparsify()
+    C = _sqdist(w.x, w.y)
+    C = C / C.max()
+    rows = np.repeat(np.arange(50), np.diff(sk["row_ptr"]))
+    Cs = C[rows, sk["col_idx"]]
+    assert np.allclose(sk["cost"], Cs, rtol=1e-14, atol=1e-15)
+    assert np.allclose(sk["val"], np.exp(-Cs / w.eps) / sk["pstar"], rtol=1e-13)
+    assert np.allclose(sk["logval"], -Cs / w.eps - np.log(sk["pstar"].astype(np.float64)), rtol=1e-13)
+
+
+def test_pattern_deterministic_and_stream_specific(orc):
+    w = inputs.small_problem(n=60, m=60, d=3, seed=10)
+    a = orc.OracleProblem(w.a, w.b, w.eps, 500.0, math.inf, x=w.x, y=w.y, seed=11).sparsify()
+    b = orc.OracleProblem(w.a, w.b, w.eps, 500.0, math.inf, x=w.x, y=w.y, seed=11).sparsify()
+    c = orc.OracleProblem(w.a, w.b, w.eps, 500.0, math.inf, x=w.x, y=w.y, seed=11, pid=1).sparsify()
+    assert np.array_equal(a["col_idx"], b["col_idx"]) and np.array_equal(a["row_ptr"], b["row_ptr"])
+    assert not (a["nnz"] == c["nnz"] and np.array_equal(a["col_idx"], c["col_idx"]))
+
+
+def test_dense_cost_input_equals_points(orc):
+    w = inputs.small_problem(n=20, m=25, d=3, seed=12)
+    C = _sqdist(w.x, w.y)
+    for lam in [math.inf, 1.0]:
+        a = orc.OracleProblem(w.a, w.b, 0.1, 200.0, lam, x=w.x, y=w.y).sparsify()
+        b = orc.OracleProblem(w.a, w.b, 0.1, 200.0, lam, C_=C).sparsify()
+        # the decision cost is binary32 in both forms; the dense form rounds the FP64 cost,
+        # the point form accumulates in binary32, so patterns may differ on rare ties only
+        assert abs(a["nnz"] - b["nnz"]) <= 2
+        assert np.allclose(a["val"][:5], b["val"][:5], rtol=1e-12) or a["nnz"] != b["nnz"]

@@ -1,0 +1,62 @@
+"""Statistical pins for Spar-Sink as a whole (Alg. 3 / Alg. 4).
+
+- Theorem 1 / 2 bound the error of the estimate by c eps sqrt(n^{3-2 alpha}/s):
+  the relative error against dense Sinkhorn falls as s grows, at least as
+  fast as s^{-1/2} (checked with slack on the mean over seeds);
+- Theorem 3: Spar-Sink needs the same order of iterations as Sinkhorn;
+- the sparse problem's own value (cost C~ = C + eps log p*) and the literal
+  output line of Alg. 3 both converge to OT_eps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+
+def _setup(n=200, d=5, seed=0):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 1, (n, d))
+    y = rng.uniform(0, 1, (n, d))
+    a = rng.uniform(0.2, 1, n); a /= a.sum()
+    b = rng.uniform(0.2, 1, n); b /= b.sum()
+    return x, y, a, b
+
+
+@pytest.mark.parametrize("lam", [math.inf, 1.0])
+def test_error_falls_with_budget(orc, lam):
+    n, eps = 200, 0.1
+    x, y, a, b = _setup(n)
+    if not math.isinf(lam):
+        b = 1.5 * b
+    P = orc.OracleProblem(a, b, eps, 1.0, lam, x=x, y=y)
+    dense = orc.dense_sinkhorn(P, tol=1e-10, max_iter=100000)
+    ref = dense["obj"]
+    budgets = [16 * n, 32 * n, 64 * n]
+    err1, err2, iters = [], [], []
+    for s in budgets:
+        e1, e2, it = [], [], []
+        for r in range(12):
+            Ps = orc.OracleProblem(a, b, eps, s, lam, x=x, y=y, seed=100 + r)
+            sp = orc.spar_sink(Ps, tol=1e-10, max_iter=100000)
+            assert sp["info"]["status"] == 0
+            e1.append(abs(sp["obj"] - ref) / abs(ref))
+            e2.append(abs(sp["obj_sparse"] - ref) / abs(ref))
+            it.append(sp["info"]["iters"])
+        err1.append(np.mean(e1)); err2.append(np.mean(e2)); iters.append(np.mean(it))
+    for err in (err1, err2):
+        assert err[0] > err[1] > err[2]
+        assert err[2] / err[0] <= 1.3 * math.sqrt(budgets[0] / budgets[2])
+    # the sparse problem's value is the closer estimate at every budget
+    assert all(e2 < e1 for e1, e2 in zip(err1, err2))
+    # Theorem 3: same order of iterations
+    ratio = np.array(iters) / dense["info"]["iters"]
+    assert (ratio > 0.5).all() and (ratio < 3.0).all()
+
+
+def test_uot_spar_sink_close_to_dense(orc):
+    n = 150
+    x, y, a, b = _setup(n, seed=1)
+    P = orc.OracleProblem(a, 1.5 * b, 0.05, 60 * n, 1.0, x=x, y=y, seed=9)
+    sp = orc.spar_sink(P, tol=1e-10, max_iter=100000)
+    de = orc.dense_sinkhorn(P, tol=1e-10, max_iter=100000)
+    assert abs(sp["obj_sparse"] - de["obj"]) / abs(de["obj"]) < 0.05
