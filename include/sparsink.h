@@ -1,0 +1,184 @@
+/*
+ * sparsink.h -- C ABI of the GB300 (sm_103a) Spar-Sink library.
+ *
+ * Spar-Sink (Li, Yu, Li & Meng, "Importance Sparsification for Sinkhorn
+ * Algorithm", JMLR 24, 2023) approximates entropic optimal transport by
+ * sampling the Gibbs kernel K = exp(-C/eps) element-wise with importance
+ * probabilities and running the Sinkhorn scaling iterations on the sparse,
+ * reweighted sketch K~.
+ *
+ * Conventions shared by every entry point:
+ *  - Memory.  Every pointer in sps_problem / sps_params, the workspace and the
+ *    potential outputs are DEVICE pointers owned by the caller.  The library
+ *    never allocates device memory: it writes only into the caller's
+ *    workspace (size from sps_workspace_bytes) and outputs.  `res` is a HOST
+ *    pointer (or NULL).
+ *  - Streams.  All work is enqueued on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream).  The solvers read convergence flags back between chunks
+ *    of iterations and synchronise `stream` before returning.
+ *  - Errors.  Functions return an sps_status; nothing throws across the ABI.
+ *    Argument errors are detected before any launch.  sps_last_error()
+ *    returns a thread-local message for the last failure on this thread.
+ *    SPS_NOT_CONVERGED still writes valid potentials and results.
+ *  - Layout.  Points are row-major (n x d, m x d); a dense cost is row-major
+ *    n x m; indices are int32.  Potentials are returned in log form
+ *    alpha = eps log u, beta = eps log v (-inf marks an unreachable row or
+ *    column: one with no sampled element carrying mass).
+ *  - Shapes.  n != m is allowed (the paper takes n = m only for brevity,
+ *    section 2.1).  n*m < 2^62, nnz < 2^31.
+ */
+#ifndef SPARSINK_H
+#define SPARSINK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* sps_stream;  /* same type as cudaStream_t */
+
+typedef enum {
+  SPS_OK = 0,
+  SPS_NOT_CONVERGED = 1,   /* max_iter reached; outputs hold the last pair */
+  SPS_ERR_INVALID_ARG = 2, /* bad sizes, eps <= 0, negative weights, ... (no launch made) */
+  SPS_ERR_WORKSPACE = 3,   /* ws_bytes smaller than sps_workspace_bytes() */
+  SPS_ERR_CAPACITY = 4,    /* sampled nnz above the workspace capacity or INT32_MAX */
+  SPS_ERR_NUMERIC = 5,     /* NaN/Inf met in the inputs or the iterates */
+  SPS_ERR_CUDA = 6         /* a CUDA call failed; see sps_last_error() */
+} sps_status;
+
+typedef enum { SPS_F64 = 0, SPS_F32 = 1, SPS_BF16 = 2, SPS_F16 = 3 } sps_dtype;
+
+/* cost_norm */
+#define SPS_COST_RAW 0     /* C = raw cost */
+#define SPS_COST_MAXNORM 1 /* C = raw / max over all (i, j) of raw */
+#define SPS_COST_SCALE 2   /* C = raw / cost_scale */
+
+/* stop_rule */
+#define SPS_STOP_RESIDUAL 0 /* sum_i |u_i^{1/phi} (K~v)_i - a_i| <= tol (row side; see below) */
+#define SPS_STOP_DELTA_UV 1 /* ||u^t - u^{t-1}||_1 + ||v^t - v^{t-1}||_1 <= tol (Alg. 1 / 2) */
+
+/* One OT/UOT problem (section 2): measures a (n) and b (m) on points x, y,
+ * with the squared Euclidean raw cost ||x_i - y_j||^2 (section 5.1) or a
+ * given raw cost matrix. */
+typedef struct {
+  int32_t n, m, d;
+  const void* x;      /* device, n*d, dtype; NULL when C is given */
+  const void* y;      /* device, m*d, dtype; NULL when C is given */
+  const void* C;      /* device, n*m raw cost, dtype; NULL = squared Euclidean */
+  int32_t cost_norm;  /* SPS_COST_* */
+  double cost_scale;  /* divisor for SPS_COST_SCALE */
+  const void* a;      /* device, n, dtype, a_i >= 0 */
+  const void* b;      /* device, m, dtype, b_j >= 0 */
+  sps_dtype dtype;    /* SPS_F32 or SPS_F64: type of x, y, C, a, b */
+} sps_problem;
+
+/* Parameters of a solve. */
+typedef struct {
+  double eps;          /* entropic regularisation, > 0 */
+  double lambda;       /* KL marginal penalty (Eq. ruot); +INFINITY = balanced OT */
+  double s;            /* sample budget: E nnz(K~) <= s (Eq. pois), > 0 */
+  double tol;          /* stopping tolerance */
+  int32_t max_iter;    /* iteration cap (>= 1) */
+  int32_t check_every; /* iterations enqueued between convergence read-backs (0 = auto) */
+  int32_t stop_rule;   /* SPS_STOP_* */
+  uint64_t seed;       /* Philox key of the sampling stream */
+  uint32_t problem_id; /* third Philox counter word (distinct streams per problem) */
+  sps_dtype kdtype;    /* storage of K~ values: F64, F32, BF16 or F16.  F64 iterates in
+                          FP64; the others iterate in FP32 */
+  int32_t log_domain;  /* 1: stabilised (absorbing) iterations for small eps */
+  double absorb_tau;   /* absorb when max |log u~| or |log v~| exceeds this (0 = default 12) */
+  const void* init_alpha; /* optional device warm start (n), iterate type, or NULL */
+  const void* init_beta;  /* optional device warm start (m), iterate type, or NULL */
+} sps_params;
+
+/* Results of a solve (host struct). */
+typedef struct {
+  int32_t status;      /* sps_status of the solve */
+  int32_t iters;       /* iterations of the returned pair (u^t, v^t) */
+  double residual;     /* stopping residual of the returned pair */
+  double obj;          /* <T,C> - eps H(T) (+ lam KL(T1||a) + lam KL(T^T1||b)), output line of Alg. 3/4 */
+  double obj_sparse;   /* obj + eps sum T log p*: the value of the sparse problem (cost C + eps log p*) */
+  double transport;    /* <T, C> */
+  double neg_entropy;  /* sum T (log T - 1) = -H(T) */
+  double logp;         /* sum T log p* (0 for dense) */
+  double mass;         /* sum T */
+  double kl_a, kl_b;   /* KL(T1 || a), KL(T^T 1 || b), section 2 definition */
+  double unreach_a;    /* mass of a on rows with (K~v)_i = 0 */
+  double unreach_b;    /* mass of b on columns with (K~^T u)_j = 0 */
+  int64_t nnz;         /* elements of K~ */
+  int32_t n_absorb;    /* absorptions performed (log_domain) */
+  float ms_sketch, ms_iter, ms_obj; /* device time of the three phases */
+  int32_t launches;    /* kernels this call launched (including iterations enqueued after the stop flag) */
+  int32_t iters_enqueued; /* iterations enqueued (>= iters; the surplus returned at once) */
+} sps_result;
+
+/* Views of a sketch inside the workspace (filled by sparsify_kernel). */
+typedef struct {
+  int32_t n, m;
+  int64_t nnz, capacity;
+  sps_dtype kdtype;
+  int32_t* row_ptr;   /* n+1 */
+  int32_t* col_idx;   /* nnz, ascending inside each row */
+  void* val;          /* nnz, K~_ij = K_ij / p*_ij in kdtype */
+  int32_t* col_ptr;   /* m+1 */
+  int32_t* row_idx;   /* nnz, ascending inside each column (stable transpose) */
+  void* valT;         /* nnz, values in CSC order */
+  int32_t* csr_pos;   /* nnz, CSR position of each CSC entry */
+} sps_sketch;
+
+/* Operation codes for sps_workspace_bytes. */
+#define SPS_OP_SPARSIFY 0
+#define SPS_OP_SPAR_SINK 1
+#define SPS_OP_DENSE 2
+
+/* Bytes of device workspace an operation needs for this problem and these
+ * parameters (0 on invalid arguments).  The sketch capacity is
+ * min(n*m, s + 8 sqrt(s) + 1024) elements: E nnz = sum p* <= s (section 3.1),
+ * and Var nnz <= s, so the capacity is exceeded with probability < 1e-15. */
+size_t sps_workspace_bytes(const sps_problem* prob, const sps_params* prm, int32_t op);
+
+/* Dense Sinkhorn, Alg. 1 (lambda = +INFINITY) or Alg. 2 (finite lambda), on
+ * K = exp(-C/eps) computed on the fly (never stored), section 2; points need
+ * d <= 16 (SPS_ERR_INVALID_ARG otherwise).  Writes
+ * alpha_out (n) and beta_out (m) in the iterate type (FP64 if kdtype = F64,
+ * else FP32).  Stopping: see SPS_STOP_*; the residual of a pair (u^t, v^t)
+ * is its row side because v^t = (b / K^T u^t)^phi makes the column side zero
+ * up to rounding. */
+sps_status sinkhorn_dense(const sps_problem* prob, const sps_params* prm, void* ws,
+                          size_t ws_bytes, void* alpha_out, void* beta_out, sps_result* res,
+                          sps_stream stream);
+
+/* Importance sparsification of K (section 3.1, Eq. pois): element (i, j) is
+ * kept with probability p*_ij = min(1, s p_ij), p_ij from Eq. (pij-ot) when
+ * lambda = +INFINITY and Eq. (pij-uot) otherwise, and stored as K_ij / p*_ij.
+ * The keep/drop decision is a fixed binary32 computation on a Philox4x32-10
+ * stream (counter (j>>2, i, problem_id, 0x5A17), key = seed), so the pattern
+ * is reproducible bit for bit.  Fills `out` with views into `ws`. */
+sps_status sparsify_kernel(const sps_problem* prob, const sps_params* prm, void* ws,
+                           size_t ws_bytes, sps_sketch* out, sps_stream stream);
+
+/* Spar-Sink for OT, Alg. 3 (section 3.2): sparsify with Eq. (pij-ot), run
+ * Alg. 1 on K~, evaluate the objective terms.  Requires lambda = +INFINITY. */
+sps_status spar_sink_ot(const sps_problem* prob, const sps_params* prm, void* ws,
+                        size_t ws_bytes, void* alpha_out, void* beta_out, sps_result* res,
+                        sps_stream stream);
+
+/* Spar-Sink for UOT, Alg. 4 (section 3.3): sparsify with Eq. (pij-uot), run
+ * Alg. 2 (exponent lambda/(lambda+eps)) on K~.  Requires 0 < lambda < inf. */
+sps_status spar_sink_uot(const sps_problem* prob, const sps_params* prm, void* ws,
+                         size_t ws_bytes, void* alpha_out, void* beta_out, sps_result* res,
+                         sps_stream stream);
+
+/* Thread-local message describing the last error on this thread. */
+const char* sps_last_error(void);
+
+/* Library version string. */
+const char* sps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPARSINK_H */

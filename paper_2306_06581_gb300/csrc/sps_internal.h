@@ -1,0 +1,156 @@
+// sps_internal.h -- internal declarations of the Spar-Sink CUDA library:
+// device control block, workspace layout and the host launchers of each
+// kernel family.  Not part of the public ABI (include/sparsink.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/sparsink.h"
+#include "sps_device.cuh"
+
+namespace sps {
+
+// Device-resident control block of one solve.  The iteration kernels read and
+// update it, so a chunk of iterations needs no host involvement; the host
+// reads it back between chunks.
+struct Ctrl {
+  int t;                 // completed iterations (pairs (u^t, v^t) formed)
+  int done;              // 1: stop (converged or numeric failure)
+  int status;            // SPS_OK / SPS_ERR_NUMERIC / SPS_ERR_CAPACITY
+  int iters;             // iterations of the returned pair
+  unsigned int blocks_a; // last-block counters of the two half-iteration kernels
+  unsigned int blocks_b;
+  unsigned int blocks_c;
+  int n_absorb;          // absorptions performed
+  int absorb_req;        // 1: the next absorption step runs
+  int cap_exceeded;      // sampled nnz above capacity
+  long long nnz;         // sampled nnz
+  double residual;       // residual of the returned pair
+  double last_residual;  // residual of the most recent pair evaluated
+  double last_unreach_a; // unreachable a-mass of that pair
+  double unreach_a;      // of the returned pair
+  double unreach_b;      // unreachable b-mass of the current v
+  double delta_u;        // ||u^t - u^{t-1}||_1 of the current iteration
+  float max_logu;        // max |log u~| over the last row pass (absorbing mode)
+  float max_logv;
+};
+
+// Scalars of the sampling decision, computed on the device.
+struct SketchScalars {
+  float dmax32;       // max raw binary32 cost
+  float maxa, maxb;   // max of the row / column factor bases
+  float s32;          // fl32(s)
+  double dmax64;      // max raw FP64 cost (FP64 value path)
+  double sum1, sum2;  // OT: exact sum sqrt(a), sqrt(b); UOT: exact Z in sum1
+  float scale32;      // OT: fl32(1/(sum1 sum2)); UOT: fl32(s/Z)
+  float gamma32;      // UOT exponent lam/(2 lam + eps)
+  float kappa32;      // UOT: fl32(1/(Dnorm (2 lam + eps)))
+  float dn32;         // value path: cost normaliser (binary32)
+  double dn64;        // value path: cost normaliser (FP64)
+  ExactAcc acc1, acc2;
+};
+
+// Result record assembled on the device at the end of a solve.
+struct DevResult {
+  double residual, obj, obj_sparse, transport, neg_entropy, logp, mass, kl_a, kl_b;
+  double unreach_a, unreach_b;
+};
+
+enum IterType { IT_F32 = 0, IT_F64 = 1 };
+
+// Byte offsets of every buffer inside the caller's workspace.
+struct Layout {
+  size_t ctrl, scal, res;
+  size_t x32, y32, a32, b32, C32;   // binary32 copies for the decision
+  size_t a_it, b_it;                // weights in the iterate type
+  size_t rowf, colf;                // decision factors
+  size_t row_cnt, row_ptr, col_cnt, col_ptr, col_cur;
+  size_t col_idx, val, row_idx, valT, csr_pos, tmp_row, tmp_src;
+  size_t u, v, alpha, beta, ahat;   // iterates (u: two buffers)
+  size_t qpart, rpart;              // dense: split partial vectors
+  size_t part;                      // block partials
+  size_t total;
+  int64_t cap;                      // sketch capacity (elements)
+  int nblk_rows, nblk_cols;         // grid sizes of the half-iteration kernels
+  int vbytes, ibytes;               // value / iterate element sizes
+};
+
+constexpr int kPartSlots = 8;      // partial arrays of nblk doubles each
+constexpr int kMaxBlocks = 4096;
+
+bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L);
+
+// ---- error reporting and launch accounting ----
+void add_launches(int k);
+void set_error(const char* fmt, ...);
+sps_status cuda_fail(cudaError_t e, const char* what);
+
+// Kernel argument bundles -----------------------------------------------------
+struct ProbDev {
+  int n, m, d;
+  CostView cv;
+  const void* a;       // input weights (dtype)
+  const void* b;
+  int in_f64;          // 1: inputs FP64
+  int cost_norm;
+  double cost_scale;
+  double eps, lam, s;
+  int is_ot;
+  uint64_t seed;
+  uint32_t pid;
+};
+
+// Host launchers (sps_sketch.cu)
+sps_status launch_prepare(const ProbDev& pd, const Layout& L, char* ws, int it64, cudaStream_t st);
+sps_status launch_cost_max(const ProbDev& pd, const Layout& L, char* ws, int need64, cudaStream_t st);
+sps_status launch_factors(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st);
+sps_status launch_sample(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st);
+sps_status launch_scalars0(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st);
+
+// Host launchers (sps_iter.cu)
+struct IterCfg {
+  int it64;            // iterate in FP64
+  sps_dtype kd;        // value dtype
+  int uot;             // Alg. 2 exponent
+  double phi, eps, tol;
+  int stop_rule;
+  int max_iter;
+};
+sps_status launch_iter_init(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                            const void* init_alpha, const void* init_beta, cudaStream_t st);
+sps_status launch_sparse_iteration(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                   cudaStream_t st);
+sps_status launch_sparse_row_only(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                  cudaStream_t st);
+sps_status launch_sparse_objective(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                   void* alpha_out, void* beta_out, cudaStream_t st);
+
+// Host launchers (sps_dense.cu)
+sps_status launch_dense_iteration(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                  cudaStream_t st);
+sps_status launch_dense_row_only(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                 cudaStream_t st);
+size_t dense_qpart_elems(int n, int m);
+size_t dense_rpart_elems(int n, int m);
+int dense_pass_blocks(int n, int m);
+sps_status launch_dense_objective(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                  void* alpha_out, void* beta_out, cudaStream_t st);
+
+template <typename T> T* at(char* ws, size_t off) { return reinterpret_cast<T*>(ws + off); }
+
+// p*_ij before clipping at 1, in the binary32 decision spec.
+//   OT  (Eq. pij-ot):  fl(r_i c_j)
+//   UOT (Eq. pij-uot): fl(scale fl(fl(A_i B_j) E(-fl(D_ij kappa))))
+// D receives the binary32 raw cost when it is computed (UOT).
+template <bool UOT>
+__device__ __forceinline__ float pstar_raw(const ProbDev& pd, const SketchScalars& sc, float ri,
+                                           const float* colf, int i, int j, float* D) {
+  if (!UOT) return __fmul_rn(ri, colf[j]);
+  const float Dij = raw32(pd.cv, i, j);
+  *D = Dij;
+  const float w = __fmul_rn(__fmul_rn(ri, colf[j]), spec_exp(-__fmul_rn(Dij, sc.kappa32)));
+  return __fmul_rn(sc.scale32, w);
+}
+
+}  // namespace sps

@@ -1,0 +1,267 @@
+"""Python binding of libsparsink.so (include/sparsink.h).
+
+Argument marshalling only: tensors are checked for dtype/contiguity, moved to
+the GPU when given on the host, and their device pointers, sizes and the
+current CUDA stream are passed to the C ABI.  Every step of the method runs in
+the CUDA library; there is no CPU fallback -- without the built library these
+functions raise.
+
+Function names are those of the C ABI: ``sinkhorn_dense``, ``sparsify_kernel``,
+``spar_sink_ot``, ``spar_sink_uot`` and ``sps_workspace_bytes``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsparsink.so")
+
+SPS_OK, SPS_NOT_CONVERGED, SPS_ERR_INVALID_ARG, SPS_ERR_WORKSPACE, SPS_ERR_CAPACITY, SPS_ERR_NUMERIC, SPS_ERR_CUDA = range(7)
+STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "ERR_INVALID_ARG", 3: "ERR_WORKSPACE", 4: "ERR_CAPACITY",
+                5: "ERR_NUMERIC", 6: "ERR_CUDA"}
+F64, F32, BF16, F16 = 0, 1, 2, 3
+DTYPE_CODES = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
+COST_RAW, COST_MAXNORM, COST_SCALE = 0, 1, 2
+STOP_RESIDUAL, STOP_DELTA_UV = 0, 1
+OP_SPARSIFY, OP_SPAR_SINK, OP_DENSE = 0, 1, 2
+
+
+class SpsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Problem(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("d", C.c_int32), ("x", C.c_void_p), ("y", C.c_void_p),
+                ("C", C.c_void_p), ("cost_norm", C.c_int32), ("cost_scale", C.c_double), ("a", C.c_void_p),
+                ("b", C.c_void_p), ("dtype", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("eps", C.c_double), ("lam", C.c_double), ("s", C.c_double), ("tol", C.c_double),
+                ("max_iter", C.c_int32), ("check_every", C.c_int32), ("stop_rule", C.c_int32),
+                ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("kdtype", C.c_int32),
+                ("log_domain", C.c_int32), ("absorb_tau", C.c_double), ("init_alpha", C.c_void_p),
+                ("init_beta", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("residual", C.c_double), ("obj", C.c_double),
+                ("obj_sparse", C.c_double), ("transport", C.c_double), ("neg_entropy", C.c_double),
+                ("logp", C.c_double), ("mass", C.c_double), ("kl_a", C.c_double), ("kl_b", C.c_double),
+                ("unreach_a", C.c_double), ("unreach_b", C.c_double), ("nnz", C.c_int64),
+                ("n_absorb", C.c_int32), ("ms_sketch", C.c_float), ("ms_iter", C.c_float),
+                ("ms_obj", C.c_float), ("launches", C.c_int32), ("iters_enqueued", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Sketch(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nnz", C.c_int64), ("capacity", C.c_int64),
+                ("kdtype", C.c_int32), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("val", C.c_void_p),
+                ("col_ptr", C.c_void_p), ("row_idx", C.c_void_p), ("valT", C.c_void_p), ("csr_pos", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2306_06581_gb300.build.build() "
+                                   "(or __graft_entry__.build()); there is no CPU fallback")
+            L = C.CDLL(LIB_PATH)
+            P = C.c_void_p
+            L.sps_workspace_bytes.argtypes = [P, P, C.c_int32]
+            L.sps_workspace_bytes.restype = C.c_size_t
+            for name in ("sinkhorn_dense", "spar_sink_ot", "spar_sink_uot"):
+                f = getattr(L, name)
+                f.argtypes = [P, P, P, C.c_size_t, P, P, P, P]
+                f.restype = C.c_int
+            L.sparsify_kernel.argtypes = [P, P, P, C.c_size_t, P, P]
+            L.sparsify_kernel.restype = C.c_int
+            L.sps_last_error.restype = C.c_char_p
+            L.sps_version.restype = C.c_char_p
+            _lib = L
+        return _lib
+
+
+def last_error() -> str:
+    return lib().sps_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _dev(t, dtype, device):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(t)
+    if t.dtype != dtype:
+        t = t.to(dtype)
+    if t.device != device:
+        t = t.to(device, non_blocking=t.is_pinned())
+    return t.contiguous()
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Marshalled:
+    prob: Problem
+    keep: tuple
+
+
+def make_problem(a, b, x=None, y=None, C_=None, dtype="f32", cost_norm=COST_MAXNORM, cost_scale=1.0, device=None):
+    """Device copies of the inputs in `dtype` and the sps_problem struct."""
+    device = torch.device("cuda") if device is None else torch.device(device)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    a, b = _dev(a, tdt, device), _dev(b, tdt, device)
+    x, y, C_ = _dev(x, tdt, device), _dev(y, tdt, device), _dev(C_, tdt, device)
+    n, m = a.numel(), b.numel()
+    d = 0 if x is None else (x.shape[1] if x.dim() == 2 else 1)
+    p = Problem(n, m, d, _ptr(x), _ptr(y), _ptr(C_), cost_norm, float(cost_scale), _ptr(a), _ptr(b),
+                F64 if dtype == "f64" else F32)
+    return Marshalled(p, (a, b, x, y, C_))
+
+
+def make_params(eps, lam=math.inf, s=1.0, tol=1e-6, max_iter=1000, check_every=0, stop_rule=STOP_RESIDUAL,
+                seed=0x5EED, problem_id=0, kdtype="f32", log_domain=0, absorb_tau=0.0, init_alpha=None,
+                init_beta=None):
+    return Params(float(eps), float(lam), float(s), float(tol), int(max_iter), int(check_every), int(stop_rule),
+                  int(seed) & ((1 << 64) - 1), int(problem_id), DTYPE_CODES[kdtype] if isinstance(kdtype, str) else kdtype,
+                  int(log_domain), float(absorb_tau), _ptr(init_alpha), _ptr(init_beta))
+
+
+def sps_workspace_bytes(prob: Problem, prm: Params, op: int) -> int:
+    return int(lib().sps_workspace_bytes(C.byref(prob), C.byref(prm), op))
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _workspace(nbytes, device, workspace=None):
+    if workspace is not None and workspace.numel() >= nbytes:
+        return workspace
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def _check(status, allow_not_converged=True):
+    if status == SPS_OK or (allow_not_converged and status == SPS_NOT_CONVERGED):
+        return
+    raise SpsError(status, last_error())
+
+
+def _solve(fn_name, prob: Problem, prm: Params, device, op, workspace=None, raise_on_error=True):
+    nbytes = sps_workspace_bytes(prob, prm, op)
+    if nbytes == 0:
+        raise SpsError(SPS_ERR_INVALID_ARG, last_error())
+    ws = _workspace(nbytes, device, workspace)
+    it_dtype = torch.float64 if prm.kdtype == F64 else torch.float32
+    alpha = torch.empty(prob.n, dtype=it_dtype, device=device)
+    beta = torch.empty(prob.m, dtype=it_dtype, device=device)
+    res = Result()
+    st = getattr(lib(), fn_name)(C.byref(prob), C.byref(prm), _ptr(ws), nbytes, _ptr(alpha), _ptr(beta),
+                                 C.byref(res), _stream())
+    if raise_on_error:
+        _check(st)
+    out = res.as_dict()
+    out["status_code"] = st
+    out["alpha"], out["beta"] = alpha, beta
+    out["workspace"] = ws
+    return out
+
+
+# ---------------------------------------------------------------------------
+# public calls (names of the C ABI)
+# ---------------------------------------------------------------------------
+
+def spar_sink_ot(a, b, x=None, y=None, C_=None, *, eps, s, tol=1e-6, max_iter=1000, dtype="f32", kdtype=None,
+                 seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL,
+                 check_every=0, init_alpha=None, init_beta=None, workspace=None, device=None, raise_on_error=True):
+    """Alg. 3: importance-sparsified Sinkhorn for balanced OT."""
+    M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
+    dev = M.keep[0].device
+    kd = kdtype or dtype
+    it = torch.float64 if kd == "f64" else torch.float32
+    ia, ib = _dev(init_alpha, it, dev), _dev(init_beta, it, dev)
+    prm = make_params(eps, math.inf, s, tol, max_iter, check_every, stop_rule, seed, problem_id, kd, 0, 0.0, ia, ib)
+    return _solve("spar_sink_ot", M.prob, prm, dev, OP_SPAR_SINK, workspace, raise_on_error)
+
+
+def spar_sink_uot(a, b, x=None, y=None, C_=None, *, eps, lam, s, tol=1e-6, max_iter=1000, dtype="f32", kdtype=None,
+                  seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL,
+                  check_every=0, init_alpha=None, init_beta=None, workspace=None, device=None, raise_on_error=True):
+    """Alg. 4: importance-sparsified Sinkhorn for UOT with KL penalty lam."""
+    M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
+    dev = M.keep[0].device
+    kd = kdtype or dtype
+    it = torch.float64 if kd == "f64" else torch.float32
+    ia, ib = _dev(init_alpha, it, dev), _dev(init_beta, it, dev)
+    prm = make_params(eps, lam, s, tol, max_iter, check_every, stop_rule, seed, problem_id, kd, 0, 0.0, ia, ib)
+    return _solve("spar_sink_uot", M.prob, prm, dev, OP_SPAR_SINK, workspace, raise_on_error)
+
+
+def sinkhorn_dense(a, b, x=None, y=None, C_=None, *, eps, lam=math.inf, tol=1e-6, max_iter=1000, dtype="f32",
+                   cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL, check_every=0, workspace=None,
+                   device=None, raise_on_error=True):
+    """Alg. 1 (lam = inf) / Alg. 2 with K = exp(-C/eps) recomputed on the fly."""
+    M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
+    dev = M.keep[0].device
+    prm = make_params(eps, lam, 1.0, tol, max_iter, check_every, stop_rule, 0, 0, dtype)
+    return _solve("sinkhorn_dense", M.prob, prm, dev, OP_DENSE, workspace, raise_on_error)
+
+
+_NP_DT = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
+
+
+def sparsify_kernel(a, b, x=None, y=None, C_=None, *, eps, s, lam=math.inf, dtype="f32", kdtype=None, seed=0x5EED,
+                    problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, workspace=None, device=None):
+    """Eq. (pois) sketch K~ as CSR + CSC tensor views (copied out of the workspace)."""
+    M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
+    dev = M.keep[0].device
+    kd = kdtype or dtype
+    prm = make_params(eps, lam, s, 0.0, 1, 0, 0, seed, problem_id, kd)
+    nbytes = sps_workspace_bytes(M.prob, prm, OP_SPARSIFY)
+    if nbytes == 0:
+        raise SpsError(SPS_ERR_INVALID_ARG, last_error())
+    ws = _workspace(nbytes, dev, workspace)
+    sk = Sketch()
+    st = lib().sparsify_kernel(C.byref(M.prob), C.byref(prm), _ptr(ws), nbytes, C.byref(sk), _stream())
+    _check(st, allow_not_converged=False)
+    base = ws.data_ptr()
+    nnz = int(sk.nnz)
+    vdt = _NP_DT[sk.kdtype]
+
+    def view(ptr, count, dt):
+        off = ptr - base
+        esz = torch.empty((), dtype=dt).element_size()
+        return ws[off:off + count * esz].view(dt).clone()
+
+    n, m = M.prob.n, M.prob.m
+    return {"nnz": nnz, "capacity": int(sk.capacity),
+            "row_ptr": view(sk.row_ptr, n + 1, torch.int32), "col_idx": view(sk.col_idx, nnz, torch.int32),
+            "val": view(sk.val, nnz, vdt), "col_ptr": view(sk.col_ptr, m + 1, torch.int32),
+            "row_idx": view(sk.row_idx, nnz, torch.int32), "valT": view(sk.valT, nnz, vdt),
+            "csr_pos": view(sk.csr_pos, nnz, torch.int32)}
+
+
+def version() -> str:
+    return lib().sps_version().decode()

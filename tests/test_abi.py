@@ -1,0 +1,95 @@
+"""The C ABI library loads and exports every entry point include/sparsink.h
+declares; argument errors are rejected on the host before any launch (these
+calls need no GPU)."""
+import ctypes as C
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2306_06581_gb300 import build, sparsink
+    build.build()
+    return sparsink
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M):
+            if m.group(1) not in ("if", "while", "for", "sizeof"):
+                names.add(m.group(1))
+    return names
+
+
+def test_exports_every_declared_symbol(S):
+    lib = C.CDLL(S.LIB_PATH)
+    declared = _declared_functions()
+    assert {"sinkhorn_dense", "sparsify_kernel", "spar_sink_ot", "spar_sink_uot", "sps_workspace_bytes",
+            "sps_last_error"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _prob(S, n=100, m=120, d=3, dtype=1):
+    fake = C.c_void_p(256)
+    return S.Problem(n, m, d, fake, fake, None, 1, 1.0, fake, fake, dtype)
+
+
+def test_workspace_sizes(S):
+    P = _prob(S)
+    Q = S.make_params(0.1, math.inf, 5000.0, kdtype="f32")
+    sp, it, de = (S.sps_workspace_bytes(P, Q, op) for op in (0, 1, 2))
+    assert 0 < de and 0 < sp < it
+    # capacity grows with s and values with their width
+    Q2 = S.make_params(0.1, math.inf, 10000.0, kdtype="f32")
+    assert S.sps_workspace_bytes(P, Q2, 1) > it
+    Q3 = S.make_params(0.1, math.inf, 5000.0, kdtype="f64")
+    assert S.sps_workspace_bytes(P, Q3, 1) > it
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(eps=-1.0), "eps"), (dict(eps=float("nan")), "eps"), (dict(s=0.0), "budget"),
+    (dict(lam=0.0), "lambda"), (dict(max_iter=0), "max_iter"), (dict(tol=-1.0), "tol"),
+])
+def test_invalid_params_rejected(S, kw, frag):
+    P = _prob(S)
+    base = dict(eps=0.1, lam=math.inf, s=1000.0, tol=1e-6, max_iter=10)
+    base.update(kw)
+    Q = S.make_params(base["eps"], base["lam"], base["s"], base["tol"], base["max_iter"])
+    assert S.sps_workspace_bytes(P, Q, 1) == 0
+    assert frag in S.last_error()
+
+
+def test_invalid_problem_rejected(S):
+    Q = S.make_params(0.1, math.inf, 1000.0)
+    assert S.sps_workspace_bytes(_prob(S, n=0), Q, 1) == 0
+    assert S.sps_workspace_bytes(_prob(S, dtype=3), Q, 1) == 0
+    P = _prob(S)
+    P.x = None
+    assert S.sps_workspace_bytes(P, Q, 1) == 0
+    res = S.Result()
+    # a null workspace is refused before any launch
+    assert S.lib().spar_sink_ot(C.byref(_prob(S)), C.byref(Q), None, 0, None, None, C.byref(res), None) == S.SPS_ERR_INVALID_ARG
+    # OT entry with finite lambda, UOT entry with infinite lambda
+    Qu = S.make_params(0.1, 1.0, 1000.0)
+    assert S.lib().spar_sink_ot(C.byref(_prob(S)), C.byref(Qu), C.c_void_p(256), 1 << 40, None, None, C.byref(res), None) == S.SPS_ERR_INVALID_ARG
+    assert S.lib().spar_sink_uot(C.byref(_prob(S)), C.byref(Q), C.c_void_p(256), 1 << 40, None, None, C.byref(res), None) == S.SPS_ERR_INVALID_ARG
+    # a workspace smaller than required
+    assert S.lib().spar_sink_ot(C.byref(_prob(S)), C.byref(Q), C.c_void_p(256), 16, None, None, C.byref(res), None) == S.SPS_ERR_WORKSPACE
+
+
+def test_binding_fails_loudly_without_library(S, tmp_path, monkeypatch):
+    monkeypatch.setattr(S, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(S, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        S.lib()
