@@ -203,6 +203,10 @@ static sps_status run_sketch(const sps_problem* P, const sps_params* Q, const La
   SPS_TRY(launch_factors(pd, L, ws, st));
   SPS_TRY(launch_sample(pd, L, ws, Q->kdtype, st));
   SPS_TRY(read_ctrl(L, ws, hctrl, st));
+  if (hctrl->status == SPS_ERR_NUMERIC) {
+    set_error("non-finite or negative input weights, or a zero normaliser");
+    return SPS_ERR_NUMERIC;
+  }
   if (hctrl->status == SPS_ERR_CAPACITY || hctrl->cap_exceeded) {
     set_error("sampled nnz %lld exceeds the workspace capacity %lld", (long long)hctrl->nnz, (long long)L.cap);
     return SPS_ERR_CAPACITY;

@@ -314,6 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_count(ProbDev pd, const SketchScal
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_scan2(const int* row_cnt, int* row_ptr, int n, const int* col_cnt,
                                                 int* col_ptr, int* col_cur, int m, long long cap, Ctrl* ctrl) {
+  if (ctrl->status != SPS_OK) return;  // counts were not produced
   const int* cnt = blockIdx.x == 0 ? row_cnt : col_cnt;
   int* ptr = blockIdx.x == 0 ? row_ptr : col_ptr;
   const int len = blockIdx.x == 0 ? n : m;
