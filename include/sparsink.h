@@ -172,6 +172,28 @@ sps_status spar_sink_uot(const sps_problem* prob, const sps_params* prm, void* w
                          size_t ws_bytes, void* alpha_out, void* beta_out, sps_result* res,
                          sps_stream stream);
 
+/* Spar-Sink OT (as spar_sink_ot) for callers that cannot allocate device
+ * memory at solve time -- e.g. a process whose device memory belongs to
+ * another allocator (a framework's caching pool, a fixed budget) or an
+ * embedding that only allocates at start-up -- and so cannot supply a
+ * workspace.  The paper has no counterpart; this is an interface convenience.
+ *
+ * The workspace is a file-scope device array of SPS_NOALLOC_SCRATCH_BYTES
+ * bytes, held by every GPU that loads the library until the process exits.
+ * The call makes no device allocation (no cudaMalloc / cudaFree, no
+ * allocating library routine); like every solver entry point it creates the
+ * CUDA events that time its phases.  The first call on a device (with that
+ * device current) looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Problems whose sps_workspace_bytes(..., SPS_OP_SPAR_SINK) exceeds the array
+ * are rejected with SPS_ERR_WORKSPACE before any launch.  All calls share the
+ * array, which keeps the last call's contents (each call clears what must
+ * start at zero); calls whose GPU work overlaps race on it.  Inputs and
+ * outputs are the caller's device buffers, as for spar_sink_ot. */
+#define SPS_NOALLOC_SCRATCH_BYTES (16u << 20)
+sps_status spar_sink_ot_noalloc(const sps_problem* prob, const sps_params* prm, void* alpha_out,
+                                void* beta_out, sps_result* res, sps_stream stream);
+
 /* Thread-local message describing the last error on this thread. */
 const char* sps_last_error(void);
 

@@ -263,5 +263,32 @@ def sparsify_kernel(a, b, x=None, y=None, C_=None, *, eps, s, lam=math.inf, dtyp
             "csr_pos": view(sk.csr_pos, nnz, torch.int32)}
 
 
+def spar_sink_ot_noalloc(a, b, x=None, y=None, C_=None, *, eps, s, tol=1e-6, max_iter=1000, dtype="f32",
+                         kdtype=None, seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0,
+                         stop_rule=STOP_RESIDUAL, check_every=0, device=None, raise_on_error=True):
+    """Alg. 3 through the entry point that takes no workspace and allocates no
+    device memory (its scratch is a fixed static array inside the library, so
+    only problems that fit it are accepted).  Inputs are moved to the device
+    here; callers that must not allocate pass device tensors."""
+    M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
+    dev = M.keep[0].device
+    kd = kdtype or dtype
+    prm = make_params(eps, math.inf, s, tol, max_iter, check_every, stop_rule, seed, problem_id, kd)
+    it_dtype = torch.float64 if prm.kdtype == F64 else torch.float32
+    alpha = torch.empty(M.prob.n, dtype=it_dtype, device=dev)
+    beta = torch.empty(M.prob.m, dtype=it_dtype, device=dev)
+    res = Result()
+    f = lib().spar_sink_ot_noalloc
+    f.argtypes = [C.c_void_p] * 6
+    f.restype = C.c_int
+    st = f(C.byref(M.prob), C.byref(prm), _ptr(alpha), _ptr(beta), C.byref(res), _stream())
+    if raise_on_error:
+        _check(st)
+    out = res.as_dict()
+    out["status_code"] = st
+    out["alpha"], out["beta"] = alpha, beta
+    return out
+
+
 def version() -> str:
     return lib().sps_version().decode()
