@@ -75,7 +75,7 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
   L->b_it = take((size_t)m * ib);
   L->rowf = take((size_t)n * 4);
   L->colf = take((size_t)m * 4);
-  int nb = (int)std::min<int64_t>(152 * 16, std::max<int64_t>(1, ((int64_t)std::max(n, m) + 7) / 8));
+  int nb = (int)std::min<int64_t>(152 * 8, std::max<int64_t>(1, ((int64_t)std::max(n, m) + 7) / 8));
   if (op == SPS_OP_SPARSIFY || op == SPS_OP_SPAR_SINK) {
     const int64_t cap = sketch_capacity(P, Q);
     L->cap = cap;
@@ -84,6 +84,7 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
     L->col_cnt = take((size_t)m * 4);
     L->col_ptr = take((size_t)(m + 1) * 4);
     L->col_cur = take((size_t)m * 4);
+    L->cnt2 = take((size_t)sweep_geometry(n, m).nchunk * n * 4);
     L->col_idx = take((size_t)cap * 4);
     L->val = take((size_t)cap * vb);
     L->row_idx = take((size_t)cap * 4);
@@ -101,7 +102,7 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
   }
   if (op == SPS_OP_SPAR_SINK || op == SPS_OP_DENSE) {
     L->u = take((size_t)2 * n * ib);
-    L->v = take((size_t)m * ib);
+    L->v = take((size_t)2 * m * ib);
     L->alpha = take((size_t)n * 4);
     L->beta = take((size_t)m * 4);
     L->ahat = take((size_t)n * 4);
@@ -203,6 +204,15 @@ static sps_status run_sketch(const sps_problem* P, const sps_params* Q, const La
   SPS_TRY(launch_factors(pd, L, ws, st));
   SPS_TRY(launch_sample(pd, L, ws, Q->kdtype, st));
   SPS_TRY(read_ctrl(L, ws, hctrl, st));
+  if (hctrl->status == SPS_OK && hctrl->nnz != hctrl->nnz_cols) {
+    set_error("internal error: row and column counts of the sketch disagree (%lld vs %lld)",
+              (long long)hctrl->nnz, (long long)hctrl->nnz_cols);
+    return SPS_ERR_CUDA;
+  }
+  if (hctrl->sketch_fault) {
+    set_error("internal error: the fill pass disagreed with the count pass (writes skipped)");
+    return SPS_ERR_CUDA;
+  }
   if (hctrl->status == SPS_ERR_NUMERIC) {
     set_error("non-finite or negative input weights, or a zero normaliser");
     return SPS_ERR_NUMERIC;
@@ -220,29 +230,38 @@ static sps_status run_sketch(const sps_problem* P, const sps_params* Q, const La
 
 // The iteration driver: chunks of iterations are enqueued back to back; the
 // device-side stop flag turns the rest of a chunk into no-ops.
-typedef sps_status (*IterFn)(const ProbDev&, const Layout&, char*, const IterCfg&, cudaStream_t);
+typedef sps_status (*IterFn)(const ProbDev&, const Layout&, char*, const IterCfg&, int, cudaStream_t);
+typedef sps_status (*RowFn)(const ProbDev&, const Layout&, char*, const IterCfg&, cudaStream_t);
 
 static thread_local int g_iters_enqueued = 0;
 
 static sps_status run_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, const sps_params* Q,
-                                 IterFn full, IterFn row_only, cudaStream_t st, Ctrl* h) {
+                                 IterFn full, RowFn row_only, cudaStream_t st, Ctrl* h) {
   SPS_TRY(launch_iter_init(pd, L, ws, ic, Q->init_alpha, Q->init_beta, st));
   int launched = 0;
-  int chunk = Q->check_every > 0 ? Q->check_every : 4;
+  int chunk = Q->check_every > 0 ? Q->check_every : (ic.persistent ? 32 : 4);
   for (;;) {
     const int k = std::min(chunk, ic.max_iter - launched);
-    for (int r = 0; r < k; ++r) SPS_TRY(full(pd, L, ws, ic, st));
+    SPS_TRY(full(pd, L, ws, ic, k, st));
     launched += k;
     g_iters_enqueued = launched;
     SPS_TRY(read_ctrl(L, ws, h, st));
     if (h->done || launched >= ic.max_iter) break;
-    if (Q->check_every <= 0) chunk = std::min(chunk * 2, 64);
+    if (Q->check_every <= 0) chunk = std::min(chunk * 2, ic.persistent ? 4096 : 64);
   }
   if (!h->done) {
     SPS_TRY(row_only(pd, L, ws, ic, st));  // residual of the final pair
     SPS_TRY(read_ctrl(L, ws, h, st));
   }
   return SPS_OK;
+}
+
+// Lanes that share one row of the sparse product: long rows get a whole warp,
+// short rows a half or quarter warp so that more rows are in flight.
+static int lanes_per_row(double mean_nnz) {
+  if (mean_nnz >= 192.0) return 32;
+  if (mean_nnz >= 24.0) return 16;
+  return 8;
 }
 
 static void fill_result(sps_result* res, const DevResult& dr, const Ctrl& h, const sps_params* Q, int64_t nnz) {
@@ -296,7 +315,9 @@ static sps_status spar_sink_impl(const sps_problem* P, const sps_params* Q, void
   ic.tol = Q->tol;
   ic.stop_rule = Q->stop_rule;
   ic.max_iter = Q->max_iter;
-  SPS_TRY(run_iterations(pd, L, ws, ic, Q, launch_sparse_iteration, launch_sparse_row_only, st, &h));
+  ic.lpr_rows = lanes_per_row((double)nnz / P->n);
+  ic.lpr_cols = lanes_per_row((double)nnz / P->m);
+  SPS_TRY(run_iterations(pd, L, ws, ic, Q, launch_sparse_iterations, launch_sparse_row_only, st, &h));
   ev.rec(2, st);
   SPS_TRY(launch_sparse_objective(pd, L, ws, ic, alpha_out, beta_out, st));
   ev.rec(3, st);
@@ -310,6 +331,7 @@ static sps_status spar_sink_impl(const sps_problem* P, const sps_params* Q, void
   r.ms_obj = ev.ms(2, 3);
   if (res) *res = r;
   if (r.status == SPS_ERR_NUMERIC) set_error("non-finite value in the iterates");
+  if (h.wait_timeout) set_error("a device-side grid barrier of the iteration kernel timed out");
   return (sps_status)r.status;
 }
 
@@ -399,7 +421,8 @@ sps_status sinkhorn_dense(const sps_problem* prob, const sps_params* prm, void* 
   ic.stop_rule = prm->stop_rule;
   ic.max_iter = prm->max_iter;
   Ctrl h;
-  SPS_TRY(run_iterations(pd, L, ws, ic, prm, launch_dense_iteration, launch_dense_row_only, st, &h));
+  ic.persistent = 0;
+  SPS_TRY(run_iterations(pd, L, ws, ic, prm, launch_dense_iterations, launch_dense_row_only, st, &h));
   ev.rec(2, st);
   SPS_TRY(launch_dense_objective(pd, L, ws, ic, alpha_out, beta_out, st));
   ev.rec(3, st);

@@ -64,17 +64,19 @@ __device__ __forceinline__ T ldpt(const float* p32, const double* p64, int64_t o
 
 // mode 0: out[split][p] = sum_{q in range} K_pq w_q
 // mode 1: block partials of transport, neg_entropy, mass over the range
-template <typename T, int DM, int MODE>
+template <typename T, int DM, bool EXACT, int MODE>
 __global__ void __launch_bounds__(kTI) k_dense_pass(PassArgs A) {
   if (A.gate && A.ctrl->done) return;
   __shared__ T qs[kTJ * DM];
   __shared__ T ws[kTJ];
+  __shared__ T lws[kTJ];   // mode 1: log of the column scaling
   __shared__ double sh[32];
   const DenseView& V = A.V;
   const int d = V.d;
   const bool dense_cost = V.C32 || V.C64;
   const double dn = sizeof(T) == 8 ? A.sc->dn64 : (double)A.sc->dn32;
   const T k2 = (T)((sizeof(T) == 8 ? 1.0 : 1.4426950408889634) / (dn * A.eps));
+  const T inv_dn = (T)(1.0 / dn), inv_eps = (T)(1.0 / A.eps);
   const T* w = (const T*)A.w;
   if (A.wsel == 1) w = (const T*)A.ubuf + (size_t)((A.ctrl->t + 1) & 1) * A.n_u;
   if (A.wsel == 2) w = (const T*)A.ubuf + (size_t)(returned_iter(A.ctrl) & 1) * A.n_u;
@@ -95,6 +97,9 @@ __global__ void __launch_bounds__(kTI) k_dense_pass(PassArgs A) {
     for (int k = 0; k < DM; ++k) pr[r][k] = (p < V.np && k < d && !dense_cost) ? ldpt<T>(V.P32, V.P64, (int64_t)p * d + k) : (T)0;
     if (MODE == 1 && p < V.np) lu[r] = urow[p];
   }
+  T llu[kRPT];
+#pragma unroll
+  for (int r = 0; r < kRPT; ++r) llu[r] = (MODE == 1 && lu[r] > (T)0) ? log(lu[r]) : (T)0;
   for (int q0 = q_begin; q0 < q_end; q0 += kTJ) {
     const int qn = min(kTJ, q_end - q0);
     __syncthreads();
@@ -103,8 +108,13 @@ __global__ void __launch_bounds__(kTI) k_dense_pass(PassArgs A) {
         const int qq = t / d, k = t - qq * d;
         qs[qq * DM + k] = ldpt<T>(V.Q32, V.Q64, (int64_t)(q0 + qq) * d + k);
       }
-    for (int t = threadIdx.x; t < qn; t += kTI) ws[t] = (MODE == 0) ? w[q0 + t] : ((const T*)A.v)[q0 + t];
+    for (int t = threadIdx.x; t < qn; t += kTI) {
+      const T wv = (MODE == 0) ? w[q0 + t] : ((const T*)A.v)[q0 + t];
+      ws[t] = wv;
+      if (MODE == 1) lws[t] = wv > (T)0 ? log(wv) : (T)0;
+    }
     __syncthreads();
+    T ttr = 0, tne = 0, tms = 0;   // per-tile sums (mode 1), added to FP64 per tile
     for (int qq = 0; qq < qn; ++qq) {
       const T wq = ws[qq];
 #pragma unroll
@@ -119,7 +129,7 @@ __global__ void __launch_bounds__(kTI) k_dense_pass(PassArgs A) {
         } else {
 #pragma unroll
           for (int k = 0; k < DM; ++k) {
-            if (k < d) {
+            if (EXACT || k < d) {
               const T t = pr[r][k] - qs[qq * DM + k];
               D = fma(t, t, D);
             }
@@ -131,14 +141,15 @@ __global__ void __launch_bounds__(kTI) k_dense_pass(PassArgs A) {
         } else if (p < V.np) {
           const T Tpq = lu[r] * K * wq;
           if (Tpq > (T)0) {
-            const double C = (double)D / dn;
-            tr += (double)Tpq * C;
-            ne += (double)Tpq * (log((double)lu[r]) + log((double)wq) - C / A.eps - 1.0);
-            ms += (double)Tpq;
+            const T C = D * inv_dn;
+            ttr += Tpq * C;
+            tne += Tpq * (llu[r] + lws[qq] - C * inv_eps - (T)1);
+            tms += Tpq;
           }
         }
       }
     }
+    if (MODE == 1) { tr += (double)ttr; ne += (double)tne; ms += (double)tms; }
   }
   if (MODE == 0) {
     T* out = (T*)A.out;
@@ -367,7 +378,8 @@ PassArgs base_args(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& 
 
 template <typename T, int DM, int MODE>
 void pass(const PassArgs& A, const Geo& g, cudaStream_t st) {
-  k_dense_pass<T, DM, MODE><<<g.grid, kTI, 0, st>>>(A);
+  if (A.V.d == DM || A.V.C32 || A.V.C64) k_dense_pass<T, DM, true, MODE><<<g.grid, kTI, 0, st>>>(A);
+  else k_dense_pass<T, DM, false, MODE><<<g.grid, kTI, 0, st>>>(A);
 }
 
 template <typename T, int DM>
@@ -421,8 +433,11 @@ void dense_dispatch(const ProbDev& pd, const Layout& L, char* ws, const IterCfg&
   else if (what == 1) dense_iteration_t<T, DMV>(pd, L, ws, ic, true, st); \
   else dense_objective_t<T, DMV>(pd, L, ws, ic, al, be, st);
   if (d <= 2) { SPS_DENSE_CASE(2) }
+  else if (d == 3) { SPS_DENSE_CASE(3) }
   else if (d <= 4) { SPS_DENSE_CASE(4) }
+  else if (d == 5) { SPS_DENSE_CASE(5) }
   else if (d <= 8) { SPS_DENSE_CASE(8) }
+  else if (d == 10) { SPS_DENSE_CASE(10) }
   else { SPS_DENSE_CASE(16) }
 #undef SPS_DENSE_CASE
 }
@@ -437,10 +452,13 @@ int dense_pass_blocks(int n, int m) {
   return std::max((int)(a.grid.x * a.grid.y), (int)(b.grid.x * b.grid.y));
 }
 
-sps_status launch_dense_iteration(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, cudaStream_t st) {
-  if (ic.it64) dense_dispatch<double>(pd, L, ws, ic, 0, nullptr, nullptr, st);
-  else dense_dispatch<float>(pd, L, ws, ic, 0, nullptr, nullptr, st);
-  add_launches(4);
+sps_status launch_dense_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, int iters,
+                                   cudaStream_t st) {
+  for (int k = 0; k < iters; ++k) {
+    if (ic.it64) dense_dispatch<double>(pd, L, ws, ic, 0, nullptr, nullptr, st);
+    else dense_dispatch<float>(pd, L, ws, ic, 0, nullptr, nullptr, st);
+  }
+  add_launches(4 * iters);
   return cuda_fail(cudaGetLastError(), "dense iteration");
 }
 

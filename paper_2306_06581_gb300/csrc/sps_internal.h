@@ -26,14 +26,20 @@ struct Ctrl {
   int absorb_req;        // 1: the next absorption step runs
   int cap_exceeded;      // sampled nnz above capacity
   long long nnz;         // sampled nnz
+  long long nnz_cols;    // the same counted by columns (must agree)
   double residual;       // residual of the returned pair
   double last_residual;  // residual of the most recent pair evaluated
   double last_unreach_a; // unreachable a-mass of that pair
   double unreach_a;      // of the returned pair
   double unreach_b;      // unreachable b-mass of the current v
   double delta_u;        // ||u^t - u^{t-1}||_1 of the current iteration
+  double delta_v;        // ||v^t - v^{t-1}||_1 of the current iteration
   float max_logu;        // max |log u~| over the last row pass (absorbing mode)
   float max_logv;
+  unsigned int bar_count; // grid barrier of the persistent iteration kernel: arrivals
+  unsigned int bar_gen;   //   and generation
+  int wait_timeout;       // a bounded device wait gave up
+  int sketch_fault;       // fill disagreed with count (write skipped instead of out of range)
 };
 
 // Scalars of the sampling decision, computed on the device.
@@ -65,7 +71,7 @@ struct Layout {
   size_t x32, y32, a32, b32, C32;   // binary32 copies for the decision
   size_t a_it, b_it;                // weights in the iterate type
   size_t rowf, colf;                // decision factors
-  size_t row_cnt, row_ptr, col_cnt, col_ptr, col_cur;
+  size_t row_cnt, row_ptr, col_cnt, col_ptr, col_cur, cnt2;
   size_t col_idx, val, row_idx, valT, csr_pos, tmp_row, tmp_src;
   size_t u, v, alpha, beta, ahat;   // iterates (u: two buffers)
   size_t qpart, rpart;              // dense: split partial vectors
@@ -101,6 +107,13 @@ struct ProbDev {
   uint32_t pid;
 };
 
+// Sweep geometry (sps_sweep.cu): column chunks of the n x m sweeps.
+struct SweepGeo { int nchunk, chunk, row_blocks; };
+SweepGeo sweep_geometry(int n, int m);
+void launch_uot_Z(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st);
+void launch_count(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st);
+void launch_fill(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st);
+
 // Host launchers (sps_sketch.cu)
 sps_status launch_prepare(const ProbDev& pd, const Layout& L, char* ws, int it64, cudaStream_t st);
 sps_status launch_cost_max(const ProbDev& pd, const Layout& L, char* ws, int need64, cudaStream_t st);
@@ -116,19 +129,22 @@ struct IterCfg {
   double phi, eps, tol;
   int stop_rule;
   int max_iter;
+  int lpr_rows = 32;   // lanes per row of the row pass (8, 16, 32)
+  int lpr_cols = 32;   // lanes per column of the column pass
+  int persistent = 1;  // run chunks of iterations in one cooperative launch
 };
 sps_status launch_iter_init(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                             const void* init_alpha, const void* init_beta, cudaStream_t st);
-sps_status launch_sparse_iteration(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
-                                   cudaStream_t st);
+sps_status launch_sparse_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                    int iters, cudaStream_t st);
 sps_status launch_sparse_row_only(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                                   cudaStream_t st);
 sps_status launch_sparse_objective(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                                    void* alpha_out, void* beta_out, cudaStream_t st);
 
 // Host launchers (sps_dense.cu)
-sps_status launch_dense_iteration(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
-                                  cudaStream_t st);
+sps_status launch_dense_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                   int iters, cudaStream_t st);
 sps_status launch_dense_row_only(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                                  cudaStream_t st);
 size_t dense_qpart_elems(int n, int m);

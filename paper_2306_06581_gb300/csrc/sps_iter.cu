@@ -2,21 +2,26 @@
 // run on K~, as Alg. 3 / Alg. 4 prescribe) and the objective of their
 // output line.
 //
-// One iteration t -> t+1 is two kernels:
-//   row pass  q = K~ v^t (CSR, one warp per row), u^{t+1} = (a / q)^phi into
-//             the other u buffer, and -- fused, at no extra pass -- the
-//             stopping residual of the pair (u^t, v^t):
-//                 rho_t = sum over reachable i of | (u^t_i)^{1/phi} q_i - a_i |
-//             (the column side of that pair is zero up to rounding because
-//             v^t was computed from u^t).  The last block to finish reduces
-//             the block partials in a fixed order and sets the stop flag.
-//   col pass  r = K~^T u^{t+1} (CSC), v^{t+1} = (b / r)^phi in place; the last
-//             block advances the iteration counter.
-// Both kernels return at once when the stop flag is set, so any number of
-// iterations can be enqueued ahead of the convergence read-back.
-// Rows (columns) whose product is zero get u_i = 0 (v_j = 0): they carry
-// mass no plan on the sketch can move, are left out of the residual, and
-// their mass is reported.
+// Iteration t -> t+1 has two phases:
+//   row phase  q = K~ v^t (CSR; LPR lanes per row), u^{t+1} = (a / q)^phi, and
+//              -- fused, at no extra pass -- the stopping residual of the pair
+//              (u^t, v^t):
+//                  rho_t = sum over reachable i of | (u^t_i)^{1/phi} q_i - a_i |
+//              (the column side of that pair is zero up to rounding because
+//              v^t was computed from u^t);
+//   col phase  r = K~^T u^{t+1} (CSC), v^{t+1} = (b / r)^phi.
+// u and v are double-buffered by the parity of t, so the pair (u^t, v^t)
+// survives the phase that follows it and the convergence decision may lag
+// half an iteration.  Rows (columns) whose product is zero get u_i = 0
+// (v_j = 0): they carry mass no plan on the sketch can move, are left out of
+// the residual, and their mass is reported.
+//
+// Two executions of the same phases:
+//   - a persistent cooperative kernel that runs a whole chunk of iterations in
+//     one launch, with two grid barriers per iteration (bounded spin waits);
+//     block 0 reduces the block partials in a fixed order and decides;
+//   - one kernel per phase (the last block to finish reduces the partials),
+//     used for the final residual and when a cooperative launch is refused.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -30,41 +35,45 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr long long kSpinLimit = 20000000;  // grid-barrier wait limit (about 1-2 s)
 
-// Warp-cooperative sparse dot product of one row: four independent chains
-// per lane so that index and value loads of several strides are in flight.
-template <typename V, typename T>
-__device__ __forceinline__ T warp_row_dot(const int* __restrict__ idx, const V* __restrict__ val,
-                                          const T* __restrict__ x, int lo, int hi, int lane) {
+// Sparse dot product of one row by a segment of LPR lanes (LPR in 8, 16, 32):
+// four independent chains per lane so that index and value loads of several
+// strides are in flight, then a butterfly reduction inside the segment.
+template <int LPR, typename V, typename T>
+__device__ __forceinline__ T seg_row_dot(const int* __restrict__ idx, const V* __restrict__ val,
+                                         const T* __restrict__ x, int lo, int hi, int sl) {
   T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-  int k = lo + lane;
-  for (; k + 96 < hi; k += 128) {
-    const int i0 = __ldg(idx + k), i1 = __ldg(idx + k + 32), i2 = __ldg(idx + k + 64), i3 = __ldg(idx + k + 96);
-    const T v0 = load_as<T>(val + k), v1 = load_as<T>(val + k + 32), v2 = load_as<T>(val + k + 64),
-            v3 = load_as<T>(val + k + 96);
+  int k = lo + sl;
+  for (; k + 3 * LPR < hi; k += 4 * LPR) {
+    const int i0 = __ldg(idx + k), i1 = __ldg(idx + k + LPR), i2 = __ldg(idx + k + 2 * LPR),
+              i3 = __ldg(idx + k + 3 * LPR);
+    const T v0 = load_as<T>(val + k), v1 = load_as<T>(val + k + LPR), v2 = load_as<T>(val + k + 2 * LPR),
+            v3 = load_as<T>(val + k + 3 * LPR);
     a0 += v0 * __ldg(x + i0);
     a1 += v1 * __ldg(x + i1);
     a2 += v2 * __ldg(x + i2);
     a3 += v3 * __ldg(x + i3);
   }
-  for (; k < hi; k += 32) a0 += load_as<T>(val + k) * __ldg(x + __ldg(idx + k));
-  return warp_sum((a0 + a1) + (a2 + a3));
+  for (; k < hi; k += LPR) a0 += load_as<T>(val + k) * __ldg(x + __ldg(idx + k));
+  T s = (a0 + a1) + (a2 + a3);
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
 }
 
 template <typename T> __device__ __forceinline__ T powT(T x, T y);
 template <> __device__ __forceinline__ float powT<float>(float x, float y) { return powf(x, y); }
 template <> __device__ __forceinline__ double powT<double>(double x, double y) { return pow(x, y); }
 
-struct HalfArgs {
-  int rows;            // rows of this pass (n for CSR, m for CSC)
-  const int* ptr;
-  const int* idx;
-  const void* val;
-  const void* xin;     // gathered vector (v for the row pass; unused for the col pass)
-  void* ubuf;          // u buffers (2 x n)
-  void* vbuf;          // v (m)
-  const void* marg;    // a (row pass) or b (col pass), iterate type
-  int n;               // length of one u buffer
+struct IterArgs {
+  int n, m;
+  const int *row_ptr, *col_idx, *col_ptr, *row_idx;
+  const void *val, *valT;
+  void* ubuf;          // u buffers (2 x n), parity of t
+  void* vbuf;          // v buffers (2 x m), parity of t
+  const void* a;       // iterate type
+  const void* b;
   double phi, inv_phi, tol;
   int stop_rule;
   Ctrl* ctrl;
@@ -72,44 +81,69 @@ struct HalfArgs {
   int nblk;
 };
 
-// Deterministic reduction of `nparts` arrays of block partials by the last block.
-__device__ void reduce_parts(const double* part, int nblk, int nparts, double* out, double* sh) {
-  for (int p = 0; p < nparts; ++p) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(part + (size_t)p * nblk + b);
-    s = block_sum_d(s, sh);
-    if (threadIdx.x == 0) out[p] = s;
-    __syncthreads();
+// Sum of NV doubles over the block with one barrier; result in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum_multi(double (&v)[NV], double* sh /* NV x 32 */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int p = 0; p < NV; ++p) v[p] = warp_sum(v[p]);
+  if (lane == 0) {
+#pragma unroll
+    for (int p = 0; p < NV; ++p) sh[p * 32 + w] = v[p];
   }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int p = 0; p < NV; ++p) {
+      const double x = lane < (int)(blockDim.x >> 5) ? sh[p * 32 + lane] : 0.0;
+      v[p] = warp_sum(x);
+    }
+  }
+  __syncthreads();
 }
 
-__device__ __forceinline__ bool last_block(unsigned int* counter) {
-  __shared__ bool am_last;
-  __threadfence();
+// Deterministic reduction of NP arrays of block partials (fixed strided
+// subsets per thread, fixed tree); result in out[] (shared), valid after return.
+template <int NP>
+__device__ void reduce_parts(const double* part, int nblk, double* out, double* sh) {
+  double s[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) s[p] = 0.0;
+#pragma unroll 4
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) s[p] += __ldcg(part + (size_t)p * nblk + b);
+  }
+  block_sum_multi<NP>(s, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) out[p] = s[p];
+  }
   __syncthreads();
-  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  return am_last;
 }
 
-template <typename V, typename T, bool UOT>
-__global__ void __launch_bounds__(kThreads) k_row_pass(HalfArgs A) {
-  Ctrl* ctrl = A.ctrl;
-  if (ctrl->done) return;
-  __shared__ double sh[32];
-  const int t = ctrl->t;
-  const T* v = (const T*)A.xin;
+// Row phase of iteration t -> t+1 for the rows of this block; returns the
+// block sums (thread 0) of residual, unreachable a-mass and |u^{t+1} - u^t|.
+template <int LPR, typename V, typename T, bool UOT>
+__device__ __forceinline__ void row_phase(const IterArgs& A, int t, double (&out)[3], double* sh) {
+  const T* v = (const T*)A.vbuf + (size_t)(t & 1) * A.m;
   const T* uold = (const T*)A.ubuf + (size_t)(t & 1) * A.n;
   T* unew = (T*)A.ubuf + (size_t)((t + 1) & 1) * A.n;
-  const T* a = (const T*)A.marg;
+  const T* a = (const T*)A.a;
   const V* val = (const V*)A.val;
-  const int lane = threadIdx.x & 31;
+  constexpr int RPW = 32 / LPR;
+  const int lane = threadIdx.x & 31, sl = lane & (LPR - 1);
   const T phi = (T)A.phi, inv_phi = (T)A.inv_phi;
   double res = 0.0, unr = 0.0, dl = 0.0;
-  for (int i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < A.rows; i += gridDim.x * kWarps) {
-    const T q = warp_row_dot<V, T>(A.idx, val, v, A.ptr[i], A.ptr[i + 1], lane);
-    if (lane == 0) {
-      const T ai = a[i], uo = uold[i];
+  const int wg = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  for (int base = wg * RPW; base < A.n; base += gridDim.x * kWarps * RPW) {
+    const int i = base + lane / LPR;
+    const bool ok = i < A.n;
+    const int lo = ok ? __ldg(A.row_ptr + i) : 0, hi = ok ? __ldg(A.row_ptr + i + 1) : 0;
+    T ai = 0, uo = 0;
+    if (ok && sl == 0) { ai = a[i]; uo = uold[i]; }  // issued before the dot product
+    const T q = seg_row_dot<LPR, V, T>(A.col_idx, val, v, lo, hi, sl);
+    if (ok && sl == 0) {
       T un;
       if (q > (T)0) {
         un = UOT ? powT<T>(ai / q, phi) : ai / q;
@@ -123,53 +157,31 @@ __global__ void __launch_bounds__(kThreads) k_row_pass(HalfArgs A) {
       unew[i] = un;
     }
   }
-  res = block_sum_d(res, sh);
-  __syncthreads();
-  unr = block_sum_d(unr, sh);
-  __syncthreads();
-  dl = block_sum_d(dl, sh);
-  if (threadIdx.x == 0) {
-    A.part[0 * A.nblk + blockIdx.x] = res;
-    A.part[1 * A.nblk + blockIdx.x] = unr;
-    A.part[2 * A.nblk + blockIdx.x] = dl;
-  }
-  if (!last_block(&ctrl->blocks_a)) return;
-  double tot[3];
-  __shared__ double outv[3];
-  reduce_parts(A.part, A.nblk, 3, outv, sh);
-  if (threadIdx.x == 0) {
-    tot[0] = outv[0]; tot[1] = outv[1]; tot[2] = outv[2];
-    ctrl->last_residual = tot[0];
-    ctrl->last_unreach_a = tot[1];
-    ctrl->delta_u = tot[2];
-    if (A.stop_rule == SPS_STOP_RESIDUAL) {
-      if (!isfinite(tot[0])) {
-        ctrl->done = 1; ctrl->status = SPS_ERR_NUMERIC; ctrl->iters = t; ctrl->residual = tot[0];
-      } else if (t >= 1 && tot[0] <= A.tol) {
-        ctrl->done = 1; ctrl->iters = t; ctrl->residual = tot[0]; ctrl->unreach_a = tot[1];
-      }
-    }
-    ctrl->blocks_a = 0u;
-  }
+  out[0] = res; out[1] = unr; out[2] = dl;
+  block_sum_multi<3>(out, sh);
 }
 
-template <typename V, typename T, bool UOT>
-__global__ void __launch_bounds__(kThreads) k_col_pass(HalfArgs A) {
-  Ctrl* ctrl = A.ctrl;
-  if (ctrl->done) return;
-  __shared__ double sh[32];
-  const int t = ctrl->t;
+// Column phase: v^{t+1} from u^{t+1}; block sums of unreachable b-mass and |v^{t+1} - v^t|.
+template <int LPR, typename V, typename T, bool UOT>
+__device__ __forceinline__ void col_phase(const IterArgs& A, int t, double (&out)[2], double* sh) {
   const T* u = (const T*)A.ubuf + (size_t)((t + 1) & 1) * A.n;
-  T* v = (T*)A.vbuf;
-  const T* b = (const T*)A.marg;
-  const V* val = (const V*)A.val;
-  const int lane = threadIdx.x & 31;
+  const T* vold = (const T*)A.vbuf + (size_t)(t & 1) * A.m;
+  T* vnew = (T*)A.vbuf + (size_t)((t + 1) & 1) * A.m;
+  const T* b = (const T*)A.b;
+  const V* val = (const V*)A.valT;
+  constexpr int RPW = 32 / LPR;
+  const int lane = threadIdx.x & 31, sl = lane & (LPR - 1);
   const T phi = (T)A.phi;
   double unb = 0.0, dl = 0.0;
-  for (int j = blockIdx.x * kWarps + (threadIdx.x >> 5); j < A.rows; j += gridDim.x * kWarps) {
-    const T r = warp_row_dot<V, T>(A.idx, val, u, A.ptr[j], A.ptr[j + 1], lane);
-    if (lane == 0) {
-      const T bj = b[j], vo = v[j];
+  const int wg = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  for (int base = wg * RPW; base < A.m; base += gridDim.x * kWarps * RPW) {
+    const int j = base + lane / LPR;
+    const bool ok = j < A.m;
+    const int lo = ok ? __ldg(A.col_ptr + j) : 0, hi = ok ? __ldg(A.col_ptr + j + 1) : 0;
+    T bj = 0, vo = 0;
+    if (ok && sl == 0) { bj = b[j]; vo = vold[j]; }
+    const T r = seg_row_dot<LPR, V, T>(A.row_idx, val, u, lo, hi, sl);
+    if (ok && sl == 0) {
       T vn;
       if (r > (T)0) {
         vn = UOT ? powT<T>(bj / r, phi) : bj / r;
@@ -178,36 +190,163 @@ __global__ void __launch_bounds__(kThreads) k_col_pass(HalfArgs A) {
         unb += (double)bj;
       }
       dl += fabs((double)vn - (double)vo);
-      v[j] = vn;
+      vnew[j] = vn;
     }
   }
-  unb = block_sum_d(unb, sh);
-  __syncthreads();
-  dl = block_sum_d(dl, sh);
-  if (threadIdx.x == 0) {
-    A.part[3 * A.nblk + blockIdx.x] = unb;
-    A.part[4 * A.nblk + blockIdx.x] = dl;
-  }
-  if (!last_block(&ctrl->blocks_b)) return;
-  __shared__ double outv[2];
-  reduce_parts(A.part + 3 * (size_t)A.nblk, A.nblk, 2, outv, sh);
-  if (threadIdx.x == 0) {
-    ctrl->unreach_b = outv[0];
-    const int tn = t + 1;
-    ctrl->t = tn;
-    if (A.stop_rule == SPS_STOP_DELTA_UV) {
-      const double tot = ctrl->delta_u + outv[1];
-      if (!isfinite(tot)) {
-        ctrl->done = 1; ctrl->status = SPS_ERR_NUMERIC; ctrl->iters = tn; ctrl->residual = tot;
-      } else if (tot <= A.tol) {
-        ctrl->done = 1; ctrl->iters = tn; ctrl->residual = tot; ctrl->unreach_a = ctrl->last_unreach_a;
+  out[0] = unb; out[1] = dl;
+  block_sum_multi<2>(out, sh);
+}
+
+// Decisions taken by one thread from the reduced partials.  Only the row
+// phase of iteration t -> t+1 stops a solve, and always on the pair
+// (u^t, v^t), whose buffers that iteration does not overwrite:
+//   residual rule:  rho_t (this row phase) <= tol;
+//   paper's rule:   ||u^t - u^{t-1}||_1 (row phase of iteration t, stored) +
+//                   ||v^t - v^{t-1}||_1 (column phase of iteration t, stored) <= tol.
+__device__ __forceinline__ void decide_row(Ctrl* ctrl, const IterArgs& A, int t, const double* tot) {
+  ctrl->last_residual = tot[0];
+  ctrl->last_unreach_a = tot[1];
+  if (!ctrl->done) {
+    if (A.stop_rule == SPS_STOP_RESIDUAL) {
+      if (!isfinite(tot[0])) {
+        ctrl->done = 1; ctrl->status = SPS_ERR_NUMERIC; ctrl->iters = t; ctrl->residual = tot[0];
+      } else if (t >= 1 && tot[0] <= A.tol) {
+        ctrl->done = 1; ctrl->iters = t; ctrl->residual = tot[0]; ctrl->unreach_a = tot[1];
+      }
+    } else if (t >= 1) {
+      const double d = ctrl->delta_u + ctrl->delta_v;
+      if (!isfinite(d)) {
+        ctrl->done = 1; ctrl->status = SPS_ERR_NUMERIC; ctrl->iters = t; ctrl->residual = d;
+      } else if (d <= A.tol) {
+        ctrl->done = 1; ctrl->iters = t; ctrl->residual = d; ctrl->unreach_a = tot[1];
       }
     }
+  }
+  ctrl->delta_u = tot[2];   // ||u^{t+1} - u^t||_1, judged with the next column phase
+}
+
+__device__ __forceinline__ void decide_col(Ctrl* ctrl, const IterArgs& A, int t, const double* tot) {
+  (void)A;
+  ctrl->unreach_b = tot[0];
+  ctrl->delta_v = tot[1];
+  ctrl->t = t + 1;
+}
+
+// Thread 0 publishes the block's partials, fences, and counts the block in;
+// the block that arrives last sees every partial.
+__device__ __forceinline__ bool publish_and_check_last(unsigned int* counter, double* part, int nblk,
+                                                       const double* vals, int nvals, int slot0) {
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < nvals; ++k) part[(size_t)(slot0 + k) * nblk + blockIdx.x] = vals[k];
+    __threadfence();
+    am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  return am_last;
+}
+
+// Grid barrier of the cooperative kernel: arrival counter plus generation;
+// the waiting threads spin with a sleep and give up after kSpinLimit polls,
+// recording a failure instead of hanging.
+__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &ctrl->bar_gen;
+    const unsigned int g = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&ctrl->bar_count, 1u) == gridDim.x - 1) {
+      ctrl->bar_count = 0u;
+      __threadfence();
+      atomicAdd(&ctrl->bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g) {
+        __nanosleep(64);
+        if (++spins > kSpinLimit) { ok = 0; break; }
+      }
+    }
+    __threadfence();
+    if (!ok) { ctrl->wait_timeout = 1; ctrl->done = 1; ctrl->status = SPS_ERR_CUDA; }
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+template <int LR, int LC, typename V, typename T, bool UOT>
+__global__ void __launch_bounds__(kThreads) k_iterate(IterArgs A, int iters) {
+  __shared__ double sh[3 * 32];
+  __shared__ double tot[3];
+  Ctrl* ctrl = A.ctrl;
+  if (ctrl->done) return;
+  int t = ctrl->t;
+  for (int k = 0; k < iters; ++k) {
+    double r3[3];
+    row_phase<LR, V, T, UOT>(A, t, r3, sh);
+    if (threadIdx.x == 0) {
+      A.part[0 * (size_t)A.nblk + blockIdx.x] = r3[0];
+      A.part[1 * (size_t)A.nblk + blockIdx.x] = r3[1];
+      A.part[2 * (size_t)A.nblk + blockIdx.x] = r3[2];
+    }
+    if (!grid_barrier(ctrl)) return;
+    if (blockIdx.x == 0) {
+      reduce_parts<3>(A.part, A.nblk, tot, sh);
+      if (threadIdx.x == 0) decide_row(ctrl, A, t, tot);
+    }
+    double c2[2];
+    col_phase<LC, V, T, UOT>(A, t, c2, sh);
+    if (threadIdx.x == 0) {
+      A.part[3 * (size_t)A.nblk + blockIdx.x] = c2[0];
+      A.part[4 * (size_t)A.nblk + blockIdx.x] = c2[1];
+    }
+    if (!grid_barrier(ctrl)) return;
+    if (*(volatile int*)&ctrl->done) return;
+    if (blockIdx.x == 0) {
+      reduce_parts<2>(A.part + 3 * (size_t)A.nblk, A.nblk, tot, sh);
+      if (threadIdx.x == 0) decide_col(ctrl, A, t, tot);
+    }
+    ++t;
+  }
+}
+
+template <int LPR, typename V, typename T, bool UOT>
+__global__ void __launch_bounds__(kThreads) k_row_pass(IterArgs A) {
+  __shared__ double sh[3 * 32];
+  __shared__ double tot[3];
+  Ctrl* ctrl = A.ctrl;
+  if (ctrl->done) return;
+  const int t = ctrl->t;
+  double r3[3];
+  row_phase<LPR, V, T, UOT>(A, t, r3, sh);
+  if (!publish_and_check_last(&ctrl->blocks_a, A.part, A.nblk, r3, 3, 0)) return;
+  reduce_parts<3>(A.part, A.nblk, tot, sh);
+  if (threadIdx.x == 0) {
+    decide_row(ctrl, A, t, tot);
+    ctrl->blocks_a = 0u;
+  }
+}
+
+template <int LPR, typename V, typename T, bool UOT>
+__global__ void __launch_bounds__(kThreads) k_col_pass(IterArgs A) {
+  __shared__ double sh[3 * 32];
+  __shared__ double tot[3];
+  Ctrl* ctrl = A.ctrl;
+  if (ctrl->done) return;
+  const int t = ctrl->t;
+  double c2[2];
+  col_phase<LPR, V, T, UOT>(A, t, c2, sh);
+  if (!publish_and_check_last(&ctrl->blocks_b, A.part, A.nblk, c2, 2, 3)) return;
+  reduce_parts<2>(A.part + 3 * (size_t)A.nblk, A.nblk, tot, sh);
+  if (threadIdx.x == 0) {
+    decide_col(ctrl, A, t, tot);
     ctrl->blocks_b = 0u;
   }
 }
 
-// u^0 = exp(alpha0/eps) (or 1) in buffer 0, v^0 = exp(beta0/eps) (or 1).
+// u^0 = exp(alpha0/eps) (or 1), v^0 = exp(beta0/eps) (or 1), in buffer 0.
 template <typename T>
 __global__ void k_iter_init(int n, int m, T* u0, T* v0, const T* al, const T* be, double eps, Ctrl* ctrl) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -217,6 +356,7 @@ __global__ void k_iter_init(int n, int m, T* u0, T* v0, const T* al, const T* be
   if (tid == 0) {
     ctrl->t = 0; ctrl->done = 0; ctrl->iters = 0;
     ctrl->blocks_a = ctrl->blocks_b = ctrl->blocks_c = 0u;
+    ctrl->bar_count = 0u;
     if (ctrl->status != SPS_OK) { ctrl->done = 1; }
   }
 }
@@ -233,17 +373,20 @@ __device__ __forceinline__ double kl_term(double x, double y) {
   return x * log(x / y) - x + y;
 }
 
+__device__ __forceinline__ int returned_iter(const Ctrl* c) { return c->done ? c->iters : c->t; }
+
 template <typename V, typename T, bool UOT>
 __global__ void __launch_bounds__(kThreads) k_obj_rows(ProbDev pd, const SketchScalars* __restrict__ scp,
                                                        const float* __restrict__ rowf,
                                                        const float* __restrict__ colf, const int* ptr,
                                                        const int* idx, const V* val, const T* ubuf,
-                                                       const T* v, const T* a, const Ctrl* ctrl,
+                                                       const T* vbuf, const T* a, const Ctrl* ctrl,
                                                        double* part, int nblk) {
   __shared__ double sh[32];
   const SketchScalars sc = *scp;
-  const int it = ctrl->done ? ctrl->iters : ctrl->t;
+  const int it = returned_iter(ctrl);
   const T* u = ubuf + (size_t)(it & 1) * pd.n;
+  const T* v = vbuf + (size_t)(it & 1) * pd.m;
   const int lane = threadIdx.x & 31;
   double tr = 0.0, ne = 0.0, lp = 0.0, ms = 0.0, kla = 0.0;
   for (int i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < pd.n; i += gridDim.x * kWarps) {
@@ -284,11 +427,12 @@ __global__ void __launch_bounds__(kThreads) k_obj_rows(ProbDev pd, const SketchS
 
 template <typename V, typename T>
 __global__ void __launch_bounds__(kThreads) k_obj_cols(int m, const int* ptr, const int* idx, const V* valT,
-                                                       const T* ubuf, const T* v, const T* b, int n,
+                                                       const T* ubuf, const T* vbuf, const T* b, int n,
                                                        const Ctrl* ctrl, double* part, int nblk) {
   __shared__ double sh[32];
-  const int it = ctrl->done ? ctrl->iters : ctrl->t;
+  const int it = returned_iter(ctrl);
   const T* u = ubuf + (size_t)(it & 1) * n;
+  const T* v = vbuf + (size_t)(it & 1) * m;
   const int lane = threadIdx.x & 31;
   double klb = 0.0;
   for (int j = blockIdx.x * kWarps + (threadIdx.x >> 5); j < m; j += gridDim.x * kWarps) {
@@ -303,15 +447,13 @@ __global__ void __launch_bounds__(kThreads) k_obj_cols(int m, const int* ptr, co
   if (threadIdx.x == 0) part[5 * (size_t)nblk + blockIdx.x] = s;
 }
 
-// Final reduction, potentials alpha = eps log u, beta = eps log v.
 template <typename T>
-__global__ void k_obj_final(const double* part, int nblk_r, int nblk_c, DevResult* out, const Ctrl* ctrl) {
+__global__ void k_obj_final(const double* part, int nblk, DevResult* out, const Ctrl* ctrl) {
   __shared__ double sh[32];
   double r[6];
   for (int p = 0; p < 6; ++p) {
-    const int nb = p == 5 ? nblk_c : nblk_r;
     double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(size_t)p * nblk_r + b];
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(size_t)p * nblk + b];
     s = block_sum_d(s, sh);
     __syncthreads();
     r[p] = s;
@@ -325,51 +467,114 @@ __global__ void k_obj_final(const double* part, int nblk_r, int nblk_c, DevResul
   }
 }
 
-template <typename T, typename O>
-__global__ void k_potentials(int n, int m, const T* ubuf, const T* v, double eps, const Ctrl* ctrl, O* al, O* be) {
-  const int it = ctrl->done ? ctrl->iters : ctrl->t;
+// Potentials alpha = eps log u, beta = eps log v of the returned pair.
+template <typename T>
+__global__ void k_potentials(int n, int m, const T* ubuf, const T* vbuf, double eps, const Ctrl* ctrl, T* al, T* be) {
+  const int it = returned_iter(ctrl);
   const T* u = ubuf + (size_t)(it & 1) * n;
+  const T* v = vbuf + (size_t)(it & 1) * m;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = tid; i < n; i += stride) al[i] = (O)(eps * log((double)u[i]));
-  for (int64_t j = tid; j < m; j += stride) be[j] = (O)(eps * log((double)v[j]));
+  for (int64_t i = tid; i < n; i += stride) al[i] = (T)(eps * log((double)u[i]));
+  for (int64_t j = tid; j < m; j += stride) be[j] = (T)(eps * log((double)v[j]));
 }
 
-template <typename V, typename T>
-HalfArgs row_args(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic) {
-  HalfArgs A;
-  A.rows = pd.n; A.ptr = at<int>(ws, L.row_ptr); A.idx = at<int>(ws, L.col_idx); A.val = ws + L.val;
-  A.xin = ws + L.v; A.ubuf = ws + L.u; A.vbuf = ws + L.v; A.marg = ws + L.a_it; A.n = pd.n;
+IterArgs make_args(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic) {
+  IterArgs A;
+  A.n = pd.n; A.m = pd.m;
+  A.row_ptr = at<int>(ws, L.row_ptr); A.col_idx = at<int>(ws, L.col_idx);
+  A.col_ptr = at<int>(ws, L.col_ptr); A.row_idx = at<int>(ws, L.row_idx);
+  A.val = ws + L.val; A.valT = ws + L.valT;
+  A.ubuf = ws + L.u; A.vbuf = ws + L.v; A.a = ws + L.a_it; A.b = ws + L.b_it;
   A.phi = ic.phi; A.inv_phi = 1.0 / ic.phi; A.tol = ic.tol; A.stop_rule = ic.stop_rule;
   A.ctrl = at<Ctrl>(ws, L.ctrl); A.part = at<double>(ws, L.part); A.nblk = L.nblk_rows;
   return A;
 }
 
-template <typename V, typename T>
-HalfArgs col_args(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic) {
-  HalfArgs A = row_args<V, T>(pd, L, ws, ic);
-  A.rows = pd.m; A.ptr = at<int>(ws, L.col_ptr); A.idx = at<int>(ws, L.row_idx); A.val = ws + L.valT;
-  A.marg = ws + L.b_it; A.nblk = L.nblk_cols;
-  return A;
+template <int LPR, typename V, typename T>
+void pass_lpr(const IterArgs& A, bool uot, bool row, cudaStream_t st) {
+  if (row) {
+    if (uot) k_row_pass<LPR, V, T, true><<<A.nblk, kThreads, 0, st>>>(A);
+    else k_row_pass<LPR, V, T, false><<<A.nblk, kThreads, 0, st>>>(A);
+  } else {
+    if (uot) k_col_pass<LPR, V, T, true><<<A.nblk, kThreads, 0, st>>>(A);
+    else k_col_pass<LPR, V, T, false><<<A.nblk, kThreads, 0, st>>>(A);
+  }
 }
 
 template <typename V, typename T>
-void iteration_vt(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, bool row_only, cudaStream_t st) {
-  const HalfArgs R = row_args<V, T>(pd, L, ws, ic);
-  if (ic.uot) k_row_pass<V, T, true><<<L.nblk_rows, kThreads, 0, st>>>(R);
-  else k_row_pass<V, T, false><<<L.nblk_rows, kThreads, 0, st>>>(R);
-  if (row_only) return;
-  const HalfArgs Cc = col_args<V, T>(pd, L, ws, ic);
-  if (ic.uot) k_col_pass<V, T, true><<<L.nblk_cols, kThreads, 0, st>>>(Cc);
-  else k_col_pass<V, T, false><<<L.nblk_cols, kThreads, 0, st>>>(Cc);
+void one_pass(const IterArgs& A, bool uot, bool row, int lpr, cudaStream_t st) {
+  if (lpr >= 32) pass_lpr<32, V, T>(A, uot, row, st);
+  else if (lpr >= 16) pass_lpr<16, V, T>(A, uot, row, st);
+  else pass_lpr<8, V, T>(A, uot, row, st);
 }
 
-void iteration_dispatch(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, bool row_only, cudaStream_t st) {
+// Cooperative launch of the persistent kernel; false when the device refuses it
+// (then the per-phase kernels are used).
+template <int LR, int LC, typename V, typename T, bool UOT>
+bool coop_launch(IterArgs A, int iters, cudaStream_t st) {
+  auto fn = k_iterate<LR, LC, V, T, UOT>;
+  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0) != cudaSuccess || per_sm < 1) return false;
+  const int grid = std::min(A.nblk, nsm * per_sm);
+  A.nblk = grid;
+  void* args[] = {(void*)&A, (void*)&iters};
+  if (cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kThreads), args, 0, st) != cudaSuccess) {
+    cudaGetLastError();  // clear the refusal
+    return false;
+  }
+  return true;
+}
+
+template <int LR, typename V, typename T, bool UOT>
+bool coop_lc(const IterArgs& A, int lc, int iters, cudaStream_t st) {
+  if (lc >= 32) return coop_launch<LR, 32, V, T, UOT>(A, iters, st);
+  if (lc >= 16) return coop_launch<LR, 16, V, T, UOT>(A, iters, st);
+  return coop_launch<LR, 8, V, T, UOT>(A, iters, st);
+}
+
+template <typename V, typename T, bool UOT>
+bool coop(const IterArgs& A, int lr, int lc, int iters, cudaStream_t st) {
+  if (lr >= 32) return coop_lc<32, V, T, UOT>(A, lc, iters, st);
+  if (lr >= 16) return coop_lc<16, V, T, UOT>(A, lc, iters, st);
+  return coop_lc<8, V, T, UOT>(A, lc, iters, st);
+}
+
+// Enqueue `iters` iterations; returns the number of kernels launched.
+template <typename V, typename T>
+int iterate_vt(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, int iters, cudaStream_t st) {
+  const IterArgs A = make_args(pd, L, ws, ic);
+  if (ic.persistent) {
+    const bool ok = ic.uot ? coop<V, T, true>(A, ic.lpr_rows, ic.lpr_cols, iters, st)
+                           : coop<V, T, false>(A, ic.lpr_rows, ic.lpr_cols, iters, st);
+    if (ok) return 1;
+  }
+  for (int k = 0; k < iters; ++k) {
+    one_pass<V, T>(A, ic.uot, true, ic.lpr_rows, st);
+    one_pass<V, T>(A, ic.uot, false, ic.lpr_cols, st);
+  }
+  return 2 * iters;
+}
+
+int iterate_dispatch(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, int iters, cudaStream_t st) {
   switch (ic.kd) {
-    case SPS_F64: iteration_vt<double, double>(pd, L, ws, ic, row_only, st); break;
-    case SPS_F32: iteration_vt<float, float>(pd, L, ws, ic, row_only, st); break;
-    case SPS_BF16: iteration_vt<__nv_bfloat16, float>(pd, L, ws, ic, row_only, st); break;
-    case SPS_F16: iteration_vt<__half, float>(pd, L, ws, ic, row_only, st); break;
+    case SPS_F64: return iterate_vt<double, double>(pd, L, ws, ic, iters, st);
+    case SPS_F32: return iterate_vt<float, float>(pd, L, ws, ic, iters, st);
+    case SPS_BF16: return iterate_vt<__nv_bfloat16, float>(pd, L, ws, ic, iters, st);
+    default: return iterate_vt<__half, float>(pd, L, ws, ic, iters, st);
+  }
+}
+
+void row_only_dispatch(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, cudaStream_t st) {
+  const IterArgs A = make_args(pd, L, ws, ic);
+  switch (ic.kd) {
+    case SPS_F64: one_pass<double, double>(A, ic.uot, true, ic.lpr_rows, st); break;
+    case SPS_F32: one_pass<float, float>(A, ic.uot, true, ic.lpr_rows, st); break;
+    case SPS_BF16: one_pass<__nv_bfloat16, float>(A, ic.uot, true, ic.lpr_rows, st); break;
+    default: one_pass<__half, float>(A, ic.uot, true, ic.lpr_rows, st); break;
   }
 }
 
@@ -380,18 +585,18 @@ void objective_vt(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& i
   double* part = at<double>(ws, L.part);
   const T* u = at<T>(ws, L.u);
   const T* v = at<T>(ws, L.v);
+  const int nb = L.nblk_rows;
   if (ic.uot)
-    k_obj_rows<V, T, true><<<L.nblk_rows, kThreads, 0, st>>>(pd, sc, at<float>(ws, L.rowf), at<float>(ws, L.colf),
-        at<int>(ws, L.row_ptr), at<int>(ws, L.col_idx), at<V>(ws, L.val), u, v, at<T>(ws, L.a_it), ctrl, part, L.nblk_rows);
+    k_obj_rows<V, T, true><<<nb, kThreads, 0, st>>>(pd, sc, at<float>(ws, L.rowf), at<float>(ws, L.colf),
+        at<int>(ws, L.row_ptr), at<int>(ws, L.col_idx), at<V>(ws, L.val), u, v, at<T>(ws, L.a_it), ctrl, part, nb);
   else
-    k_obj_rows<V, T, false><<<L.nblk_rows, kThreads, 0, st>>>(pd, sc, at<float>(ws, L.rowf), at<float>(ws, L.colf),
-        at<int>(ws, L.row_ptr), at<int>(ws, L.col_idx), at<V>(ws, L.val), u, v, at<T>(ws, L.a_it), ctrl, part, L.nblk_rows);
-  k_obj_cols<V, T><<<L.nblk_cols, kThreads, 0, st>>>(pd.m, at<int>(ws, L.col_ptr), at<int>(ws, L.row_idx),
-      at<V>(ws, L.valT), u, v, at<T>(ws, L.b_it), pd.n, ctrl, part, L.nblk_rows);
-  k_obj_final<T><<<1, kThreads, 0, st>>>(part, L.nblk_rows, L.nblk_cols, at<DevResult>(ws, L.res), ctrl);
+    k_obj_rows<V, T, false><<<nb, kThreads, 0, st>>>(pd, sc, at<float>(ws, L.rowf), at<float>(ws, L.colf),
+        at<int>(ws, L.row_ptr), at<int>(ws, L.col_idx), at<V>(ws, L.val), u, v, at<T>(ws, L.a_it), ctrl, part, nb);
+  k_obj_cols<V, T><<<nb, kThreads, 0, st>>>(pd.m, at<int>(ws, L.col_ptr), at<int>(ws, L.row_idx),
+      at<V>(ws, L.valT), u, v, at<T>(ws, L.b_it), pd.n, ctrl, part, nb);
+  k_obj_final<T><<<1, kThreads, 0, st>>>(part, nb, at<DevResult>(ws, L.res), ctrl);
   const int g = (int)std::min<int64_t>(4096, (std::max(pd.n, pd.m) + kThreads - 1) / kThreads);
-  if (al && be)
-    k_potentials<T, T><<<std::max(g, 1), kThreads, 0, st>>>(pd.n, pd.m, u, v, ic.eps, ctrl, (T*)al, (T*)be);
+  if (al && be) k_potentials<T><<<std::max(g, 1), kThreads, 0, st>>>(pd.n, pd.m, u, v, ic.eps, ctrl, (T*)al, (T*)be);
 }
 
 }  // namespace
@@ -409,14 +614,14 @@ sps_status launch_iter_init(const ProbDev& pd, const Layout& L, char* ws, const 
   return cuda_fail(cudaGetLastError(), "iter_init");
 }
 
-sps_status launch_sparse_iteration(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, cudaStream_t st) {
-  iteration_dispatch(pd, L, ws, ic, false, st);
-  add_launches(2);
-  return cuda_fail(cudaGetLastError(), "sparse iteration");
+sps_status launch_sparse_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, int iters,
+                                    cudaStream_t st) {
+  add_launches(iterate_dispatch(pd, L, ws, ic, iters, st));
+  return cuda_fail(cudaGetLastError(), "sparse iterations");
 }
 
 sps_status launch_sparse_row_only(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, cudaStream_t st) {
-  iteration_dispatch(pd, L, ws, ic, true, st);
+  row_only_dispatch(pd, L, ws, ic, st);
   add_launches(1);
   return cuda_fail(cudaGetLastError(), "sparse row pass");
 }

@@ -246,69 +246,6 @@ __global__ void k_uot_factors(ProbDev pd, SketchScalars* sc, const float* a32, c
   }
 }
 
-// UOT weight w_ij = (A_i B_j) E(-(D_ij kappa)), the numerator of Eq. (pij-uot).
-__device__ __forceinline__ float uot_w(const CostView& cv, float Ai, float Bj, float kappa, int i, int j) {
-  return __fmul_rn(__fmul_rn(Ai, Bj), spec_exp(-__fmul_rn(raw32(cv, i, j), kappa)));
-}
-
-// UOT normaliser Z = sum_ij w_ij, exact.  One warp per row.
-__global__ void k_uot_Z(ProbDev pd, SketchScalars* sc, const float* rowf, const float* colf) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const float bound = __fmul_rn(sc->maxa, sc->maxb);
-  const int B = exact_floor_for(fmaxf(bound, 1e-30f));
-  if (blockIdx.x == 0 && threadIdx.x == 0) sc->acc1.B = B;
-  const float kappa = sc->kappa32;
-  U128 acc{0ull, 0ull};
-  for (int i = warp; i < pd.n; i += nwarps) {
-    const float Ai = rowf[i];
-    if (Ai == 0.0f) continue;
-    for (int j = lane; j < pd.m; j += 32) exact_add(acc, &sc->acc1, B, uot_w(pd.cv, Ai, colf[j], kappa, i, j));
-  }
-  exact_flush(acc, &sc->acc1);
-}
-
-// ---------------------------------------------------------------------------
-// count: one warp per row; lane l handles the Philox block of columns
-// 4q .. 4q+3 with q = q0 + l.
-// ---------------------------------------------------------------------------
-template <bool UOT>
-__global__ void __launch_bounds__(kThreads) k_count(ProbDev pd, const SketchScalars* __restrict__ scp,
-                                                    const float* __restrict__ rowf,
-                                                    const float* __restrict__ colf, int* row_cnt,
-                                                    int* col_cnt, const Ctrl* ctrl) {
-  if (ctrl->status != SPS_OK) return;
-  const SketchScalars sc = *scp;
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int nq = (pd.m + 3) >> 2;
-  for (int i = warp; i < pd.n; i += nwarps) {
-    const float ri = rowf[i];
-    int cnt = 0;
-    if (ri > 0.0f) {
-      for (int q = lane; q < nq; q += 32) {
-        const uint4 dr = draw4(pd.seed, pd.pid, (uint32_t)i, (uint32_t)q);
-        const uint32_t dd4[4] = {dr.x, dr.y, dr.z, dr.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int j = 4 * q + e;
-          if (j < pd.m) {
-            float D;
-            if (keep(dd4[e], pstar_raw<UOT>(pd, sc, ri, colf, i, j, &D))) {
-              ++cnt;
-              atomicAdd(&col_cnt[j], 1);
-            }
-          }
-        }
-      }
-    }
-    cnt = warp_sum(cnt);
-    if (lane == 0) row_cnt[i] = cnt;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // scan: block 0 scans the row counts, block 1 the column counts.
 // ---------------------------------------------------------------------------
@@ -342,93 +279,10 @@ __global__ void __launch_bounds__(1024) k_scan2(const int* row_cnt, int* row_ptr
     run += cnt[k];
   }
   if (t == T - 1) ptr[len] = ok ? (int)total : 0;
-  if (t == 0 && blockIdx.x == 0) {
-    ctrl->nnz = total;
+  if (t == 0) {
+    if (blockIdx.x == 0) ctrl->nnz = total;
+    else ctrl->nnz_cols = total;
     if (!ok) { ctrl->cap_exceeded = 1; ctrl->status = SPS_ERR_CAPACITY; }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// fill: same traversal as count; a warp-wide exclusive scan of the per-lane
-// counts places the kept elements of a 128-column chunk in ascending order.
-// ---------------------------------------------------------------------------
-template <typename V> struct ValMath;
-template <> struct ValMath<double> {
-  __device__ static double value(const ProbDev& pd, const SketchScalars& sc, int i, int j, float, float ps) {
-    const double C = __ddiv_rn(raw64(pd.cv, i, j), sc.dn64);
-    return exp(-C / pd.eps) / (double)ps;
-  }
-};
-template <typename V> struct ValMath {
-  __device__ static double value(const ProbDev& pd, const SketchScalars& sc, int i, int j, float D, float ps) {
-    const float C = __fdiv_rn(D, sc.dn32);
-    return (double)(expf(-C / (float)pd.eps) / ps);
-  }
-};
-
-template <bool UOT, typename V>
-__global__ void __launch_bounds__(kThreads) k_fill(ProbDev pd, const SketchScalars* __restrict__ scp,
-                                                   const float* __restrict__ rowf,
-                                                   const float* __restrict__ colf,
-                                                   const int* __restrict__ row_ptr, int* col_idx, V* val,
-                                                   int* col_cur, int* tmp_row, int* tmp_src, const Ctrl* ctrl) {
-  if (ctrl->status != SPS_OK) return;
-  const SketchScalars sc = *scp;
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int nq = (pd.m + 3) >> 2;
-  for (int i = warp; i < pd.n; i += nwarps) {
-    const float ri = rowf[i];
-    if (!(ri > 0.0f)) continue;
-    int pos0 = row_ptr[i];
-    for (int q0 = 0; q0 < nq; q0 += 32) {
-      const int q = q0 + lane;
-      unsigned mask = 0u;
-      float pe[4], De[4];
-      if (q < nq) {
-        const uint4 dr = draw4(pd.seed, pd.pid, (uint32_t)i, (uint32_t)q);
-        const uint32_t dd4[4] = {dr.x, dr.y, dr.z, dr.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int j = 4 * q + e;
-          pe[e] = 0.0f;
-          De[e] = 0.0f;
-          if (j < pd.m) {
-            const float p = pstar_raw<UOT>(pd, sc, ri, colf, i, j, &De[e]);
-            pe[e] = p;
-            if (keep(dd4[e], p)) mask |= 1u << e;
-          }
-        }
-      }
-      const int c = __popc(mask);
-      int incl = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int total = __shfl_sync(0xffffffffu, incl, 31);
-      int pos = pos0 + incl - c;
-      if (mask) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          if (mask & (1u << e)) {
-            const int j = 4 * q + e;
-            const float ps = pe[e] < 1.0f ? pe[e] : 1.0f;
-            float D = De[e];
-            if (!UOT) D = raw32(pd.cv, i, j);
-            col_idx[pos] = j;
-            val[pos] = from_d<V>(ValMath<V>::value(pd, sc, i, j, D, ps));
-            const int slot = atomicAdd(&col_cur[j], 1);
-            tmp_row[slot] = i;
-            tmp_src[slot] = pos;
-            ++pos;
-          }
-        }
-      }
-      pos0 += total;
-    }
   }
 }
 
@@ -440,9 +294,17 @@ __global__ void __launch_bounds__(kThreads) k_fill(ProbDev pd, const SketchScala
 constexpr int kSortCap = 1024;
 constexpr int kSortWarps = 8;
 
+// Gather of the value from its CSR position, bounds-checked against nnz.
+template <typename V>
+__device__ __forceinline__ V gather_val(const V* val, int src, long long nnz, Ctrl* ctrl) {
+  if (src < 0 || (long long)src >= nnz) { ctrl->sketch_fault = 1; return from_d<V>(0.0); }
+  return val[src];
+}
+
 template <int Q, typename V>
 __device__ __forceinline__ void rank_place(const int* sm, int L, int s0, int lane, const int* tmp_src,
-                                           const V* val, int* row_idx, int* csr_pos, V* valT) {
+                                           const V* val, int* row_idx, int* csr_pos, V* valT,
+                                           long long nnz, Ctrl* ctrl) {
   int r[Q], src[Q], rank[Q];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
@@ -462,7 +324,7 @@ __device__ __forceinline__ void rank_place(const int* sm, int L, int s0, int lan
     if (e < L) {
       row_idx[s0 + rank[k]] = r[k];
       csr_pos[s0 + rank[k]] = src[k];
-      valT[s0 + rank[k]] = val[src[k]];
+      valT[s0 + rank[k]] = gather_val(val, src[k], nnz, ctrl);
     }
   }
 }
@@ -472,8 +334,9 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_csc_sort(int m, const int* 
                                                               const int* __restrict__ tmp_row,
                                                               const int* __restrict__ tmp_src,
                                                               const V* __restrict__ val, int* row_idx,
-                                                              int* csr_pos, V* valT, const Ctrl* ctrl) {
-  if (ctrl->status != SPS_OK) return;
+                                                              int* csr_pos, V* valT, Ctrl* ctrl) {
+  if (ctrl->status != SPS_OK || ctrl->sketch_fault) return;
+  const long long nnz = ctrl->nnz;
   __shared__ int sm_all[kSortWarps][kSortCap];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -488,9 +351,9 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_csc_sort(int m, const int* 
       __syncwarp();
       for (int e = lane; e < L; e += 32) sm[e] = tmp_row[s0 + e];
       __syncwarp();
-      if (L <= 64) rank_place<2>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT);
-      else if (L <= 256) rank_place<8>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT);
-      else rank_place<32>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT);
+      if (L <= 64) rank_place<2>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl);
+      else if (L <= 256) rank_place<8>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl);
+      else rank_place<32>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl);
     } else {
       for (int e = lane; e < L; e += 32) {
         const int re = tmp_row[s0 + e];
@@ -499,7 +362,7 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_csc_sort(int m, const int* 
         const int src = tmp_src[s0 + e];
         row_idx[s0 + rank] = re;
         csr_pos[s0 + rank] = src;
-        valT[s0 + rank] = val[src];
+        valT[s0 + rank] = gather_val(val, src, nnz, ctrl);
       }
     }
   }
@@ -574,50 +437,38 @@ sps_status launch_factors(const ProbDev& pd, const Layout& L, char* ws, cudaStre
     cudaMemsetAsync(&sc->maxa, 0, sizeof(float), st);
     cudaMemsetAsync(&sc->maxb, 0, sizeof(float), st);
     k_uot_factors<<<g, kThreads, 0, st>>>(pd, sc, a32, b32, rowf, colf);
-    k_uot_Z<<<grid_for((int64_t)pd.n * 32, kThreads), kThreads, 0, st>>>(pd, sc, rowf, colf);
+    launch_uot_Z(pd, L, ws, st);
     k_scalars<<<1, 32, 0, st>>>(pd, sc, ctrl, 2);
   }
   add_launches(4);
   return cuda_fail(cudaGetLastError(), "factors");
 }
 
-template <bool UOT, typename V>
-static void fill_and_sort(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st) {
-  const SketchScalars* sc = at<SketchScalars>(ws, L.scal);
-  const Ctrl* ctrl = at<Ctrl>(ws, L.ctrl);
-  const int g = grid_for((int64_t)pd.n * 32, kThreads);
-  k_fill<UOT, V><<<g, kThreads, 0, st>>>(pd, sc, at<float>(ws, L.rowf), at<float>(ws, L.colf),
-                                         at<int>(ws, L.row_ptr), at<int>(ws, L.col_idx), at<V>(ws, L.val),
-                                         at<int>(ws, L.col_cur), at<int>(ws, L.tmp_row),
-                                         at<int>(ws, L.tmp_src), ctrl);
+template <typename V>
+static void csc_sort(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st) {
   const int gs = grid_for((int64_t)pd.m * 32, 32 * kSortWarps);
   k_csc_sort<V><<<gs, 32 * kSortWarps, 0, st>>>(pd.m, at<int>(ws, L.col_ptr), at<int>(ws, L.tmp_row),
                                                 at<int>(ws, L.tmp_src), at<V>(ws, L.val),
                                                 at<int>(ws, L.row_idx), at<int>(ws, L.csr_pos),
-                                                at<V>(ws, L.valT), ctrl);
+                                                at<V>(ws, L.valT), at<Ctrl>(ws, L.ctrl));
 }
 
 sps_status launch_sample(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st) {
-  const SketchScalars* sc = at<SketchScalars>(ws, L.scal);
   Ctrl* ctrl = at<Ctrl>(ws, L.ctrl);
   int* row_cnt = at<int>(ws, L.row_cnt);
   int* col_cnt = at<int>(ws, L.col_cnt);
   cudaMemsetAsync(col_cnt, 0, sizeof(int) * (size_t)pd.m, st);
-  const int g = grid_for((int64_t)pd.n * 32, kThreads);
-  if (pd.is_ot)
-    k_count<false><<<g, kThreads, 0, st>>>(pd, sc, at<float>(ws, L.rowf), at<float>(ws, L.colf), row_cnt, col_cnt, ctrl);
-  else
-    k_count<true><<<g, kThreads, 0, st>>>(pd, sc, at<float>(ws, L.rowf), at<float>(ws, L.colf), row_cnt, col_cnt, ctrl);
+  launch_count(pd, L, ws, st);
   k_scan2<<<2, 1024, 0, st>>>(row_cnt, at<int>(ws, L.row_ptr), pd.n, col_cnt, at<int>(ws, L.col_ptr),
                               at<int>(ws, L.col_cur), pd.m, (long long)L.cap, ctrl);
-  const bool ot = pd.is_ot;
+  launch_fill(pd, L, ws, kd, st);
   switch (kd) {
-    case SPS_F64: ot ? fill_and_sort<false, double>(pd, L, ws, st) : fill_and_sort<true, double>(pd, L, ws, st); break;
-    case SPS_F32: ot ? fill_and_sort<false, float>(pd, L, ws, st) : fill_and_sort<true, float>(pd, L, ws, st); break;
-    case SPS_BF16: ot ? fill_and_sort<false, __nv_bfloat16>(pd, L, ws, st) : fill_and_sort<true, __nv_bfloat16>(pd, L, ws, st); break;
-    case SPS_F16: ot ? fill_and_sort<false, __half>(pd, L, ws, st) : fill_and_sort<true, __half>(pd, L, ws, st); break;
+    case SPS_F64: csc_sort<double>(pd, L, ws, st); break;
+    case SPS_F32: csc_sort<float>(pd, L, ws, st); break;
+    case SPS_BF16: csc_sort<__nv_bfloat16>(pd, L, ws, st); break;
+    case SPS_F16: csc_sort<__half>(pd, L, ws, st); break;
   }
-  add_launches(4);
+  add_launches(5);
   return cuda_fail(cudaGetLastError(), "sample");
 }
 

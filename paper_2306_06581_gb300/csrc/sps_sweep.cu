@@ -1,0 +1,335 @@
+// sps_sweep.cu -- the n x m sweeps of the sketch (section 3, Eq. pois):
+//   Z      UOT normaliser Z = sum_ij A_i B_j exp(-D_ij kappa) (Eq. pij-uot), exact
+//   COUNT  kept elements per (row, column chunk) and per column
+//   FILL   CSR entries (columns ascending) and an unordered CSC scatter
+// All three walk the same tiling: a block owns 32 rows (4 per warp) and one
+// column chunk; the chunk is cut into tiles of kTJ columns whose decision
+// factors c_j and (UOT) binary32 coordinates are staged in shared memory,
+// coordinates transposed so that a lane reads the four columns of its Philox
+// block with one 128-bit load per coordinate.  Lane l of a warp handles the
+// Philox block q = tile_q0 + s*32 + l (columns 4q .. 4q+3) at step s.
+// The per-element decision is the binary32 computation of pstar_raw().
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "sps_internal.h"
+
+namespace sps {
+
+namespace {
+
+constexpr int kRW = 4;          // rows per warp
+constexpr int kSweepThreads = 256;  // 8 warps
+constexpr int kRB = (kSweepThreads / 32) * kRW;  // rows per block
+constexpr int kTJ = 512;        // columns per shared-memory tile
+constexpr int kSteps = kTJ / 128;
+constexpr int kMaxDSmem = 16;   // coordinates staged for d <= 16; larger d reads global memory
+
+enum { SW_Z = 0, SW_COUNT = 1, SW_FILL = 2 };
+
+struct SweepArgs {
+  ProbDev pd;
+  SketchScalars* sc;
+  const float* rowf;
+  const float* colf;
+  int* cnt2;          // [nchunk][n] kept elements per (chunk, row)
+  int* col_cnt;       // [m]
+  const int* row_ptr;
+  int* col_idx;
+  void* val;
+  int* col_cur;
+  const int* col_end;   // col_ptr + 1: end of every column segment
+  int* tmp_row;
+  int* tmp_src;
+  Ctrl* ctrl;
+  int chunk;          // columns per chunk (multiple of kTJ)
+  int nchunk;
+};
+
+template <typename V> struct ValMath;
+template <> struct ValMath<double> {
+  __device__ static double value(const ProbDev& pd, const SketchScalars& sc, int i, int j, float, float ps) {
+    const double C = __ddiv_rn(raw64(pd.cv, i, j), sc.dn64);
+    return exp(-C / pd.eps) / (double)ps;
+  }
+};
+template <typename V> struct ValMath {
+  __device__ static double value(const ProbDev& pd, const SketchScalars& sc, int i, int j, float D, float ps) {
+    const float C = __fdiv_rn(D, sc.dn32);
+    return (double)(expf(-C / (float)pd.eps) / ps);
+  }
+};
+
+template <int MODE, bool UOT, int D, typename V>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
+  if (A.ctrl->status != SPS_OK) return;
+  extern __shared__ __align__(16) float smem[];
+  const ProbDev& pd = A.pd;
+  const int n = pd.n, m = pd.m;
+  const int d = pd.d;
+  const bool stage_y = UOT && !pd.cv.C32 && d <= kMaxDSmem;
+  float* ct = smem;           // [kTJ]
+  float* yT = smem + kTJ;     // [d][kTJ]
+  const float kappa = A.sc->kappa32, scale = A.sc->scale32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.y;
+  const int jc0 = c * A.chunk;
+  const int jc1 = min(m, jc0 + A.chunk);
+  U128 acc{0ull, 0ull};
+  int Bz = 0;
+  if (MODE == SW_Z) {
+    Bz = exact_floor_for(fmaxf(__fmul_rn(A.sc->maxa, A.sc->maxb), 1e-30f));
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) A.sc->acc1.B = Bz;
+  }
+  constexpr int DR = D > 0 ? D : kMaxDSmem;
+  if (blockDim.x != kSweepThreads) return;  // the row mapping assumes 8 warps
+  for (int rb = blockIdx.x * kRB; rb < n; rb += gridDim.x * kRB) {
+    // rows rb + warp*kRW + r, r < kRW, handled one after the other on each tile
+    int cnt[kRW], pos0[kRW], pend[kRW];
+#pragma unroll
+    for (int r = 0; r < kRW; ++r) {
+      const int i = rb + warp * kRW + r;
+      cnt[r] = 0;
+      pos0[r] = 0;
+      pend[r] = 0;
+      if (MODE == SW_FILL && i < n) pend[r] = A.row_ptr[i + 1];
+      if (MODE == SW_FILL && i < n && A.rowf[i] > 0.0f) {
+        int p = A.row_ptr[i];
+        for (int cc = 0; cc < c; ++cc) p += A.cnt2[(size_t)cc * n + i];
+        pos0[r] = p;
+      }
+    }
+    for (int j0 = jc0; j0 < jc1; j0 += kTJ) {
+      const int jn = min(kTJ, jc1 - j0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < kTJ; t += blockDim.x) ct[t] = t < jn ? A.colf[j0 + t] : 0.0f;
+      if (stage_y) {
+        for (int t = threadIdx.x; t < jn; t += blockDim.x) {
+          const float* yr = pd.cv.y32 + (int64_t)(j0 + t) * d;
+#pragma unroll
+          for (int k = 0; k < DR; ++k)
+            if (D > 0 || k < d) yT[k * kTJ + t] = yr[k];
+        }
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int r = 0; r < kRW; ++r) {
+        const int i = rb + warp * kRW + r;
+        const bool rv = i < n;
+        const float ri = rv ? A.rowf[i] : 0.0f;
+        if (!(rv && ri > 0.0f)) continue;  // uniform over the warp
+        float xi[DR];
+#pragma unroll
+        for (int k = 0; k < DR; ++k) xi[k] = (UOT && stage_y && k < d) ? pd.cv.x32[(int64_t)i * d + k] : 0.0f;
+#pragma unroll 1
+        for (int s = 0; s < kSteps; ++s) {
+          const int jl = 4 * (s * 32 + lane);
+          const int j = j0 + jl;
+          unsigned mask = 0u;
+          float pe[4] = {0.f, 0.f, 0.f, 0.f};
+          float Dv[4] = {0.f, 0.f, 0.f, 0.f};
+          if (jl < jn) {
+            const float4 c4 = *reinterpret_cast<const float4*>(&ct[jl]);
+            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+            if (UOT) {
+              if (stage_y) {
+#pragma unroll
+                for (int k = 0; k < DR; ++k) {
+                  if (D > 0 || k < d) {
+                    const float4 y4 = *reinterpret_cast<const float4*>(&yT[k * kTJ + jl]);
+                    float t;
+                    t = __fsub_rn(xi[k], y4.x); Dv[0] = __fmaf_rn(t, t, Dv[0]);
+                    t = __fsub_rn(xi[k], y4.y); Dv[1] = __fmaf_rn(t, t, Dv[1]);
+                    t = __fsub_rn(xi[k], y4.z); Dv[2] = __fmaf_rn(t, t, Dv[2]);
+                    t = __fsub_rn(xi[k], y4.w); Dv[3] = __fmaf_rn(t, t, Dv[3]);
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) Dv[e] = (j + e < jc1) ? raw32(pd.cv, i, j + e) : 0.0f;
+              }
+            }
+            uint4 dr = make_uint4(0u, 0u, 0u, 0u);
+            if (MODE != SW_Z) dr = draw4(pd.seed, pd.pid, (uint32_t)i, (uint32_t)(j >> 2));
+            const uint32_t dd[4] = {dr.x, dr.y, dr.z, dr.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (j + e < jc1) {
+                float p;
+                if (UOT) {
+                  const float w = __fmul_rn(__fmul_rn(ri, cv[e]), spec_exp(-__fmul_rn(Dv[e], kappa)));
+                  if (MODE == SW_Z) { exact_add(acc, &A.sc->acc1, Bz, w); continue; }
+                  p = __fmul_rn(scale, w);
+                } else {
+                  p = __fmul_rn(ri, cv[e]);
+                }
+                pe[e] = p;
+                if (keep(dd[e], p)) mask |= 1u << e;
+              }
+            }
+          }
+          if (MODE == SW_COUNT) {
+            cnt[r] += __popc(mask);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (mask & (1u << e)) atomicAdd(&A.col_cnt[j + e], 1);
+          } else if (MODE == SW_FILL) {
+            const int cnum = __popc(mask);
+            int incl = cnum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int y = __shfl_up_sync(0xffffffffu, incl, o);
+              if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            int pos = pos0[r] + incl - cnum;
+            if (mask) {
+              const SketchScalars& sc = *A.sc;
+              V* val = (V*)A.val;
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                if (mask & (1u << e)) {
+                  const int jj = j + e;
+                  const float ps = pe[e] < 1.0f ? pe[e] : 1.0f;
+                  const float Dd = UOT ? Dv[e] : raw32(pd.cv, i, jj);
+                  // bounds checks: a count/fill mismatch is recorded, never written out of range
+                  if (pos >= pend[r]) { A.ctrl->sketch_fault = 1; ++pos; continue; }
+                  A.col_idx[pos] = jj;
+                  val[pos] = from_d<V>(ValMath<V>::value(pd, sc, i, jj, Dd, ps));
+                  const int slot = atomicAdd(&A.col_cur[jj], 1);
+                  if (slot < A.col_end[jj]) {
+                    A.tmp_row[slot] = i;
+                    A.tmp_src[slot] = pos;
+                  } else {
+                    A.ctrl->sketch_fault = 1;
+                  }
+                  ++pos;
+                }
+              }
+            }
+            pos0[r] += total;
+          }
+        }
+      }
+    }
+    if (MODE == SW_COUNT) {
+#pragma unroll
+      for (int r = 0; r < kRW; ++r) {
+        const int i = rb + warp * kRW + r;
+        const int cs = warp_sum(cnt[r]);
+        if (lane == 0 && i < n) A.cnt2[(size_t)c * n + i] = cs;
+      }
+    }
+  }
+  if (MODE == SW_Z) exact_flush(acc, &A.sc->acc1);
+}
+
+// Row counts: sum of the per-chunk counts in chunk order.
+__global__ void k_sum_chunks(int n, int nchunk, const int* cnt2, int* row_cnt, const Ctrl* ctrl) {
+  if (ctrl->status != SPS_OK) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int s = 0;
+    for (int c = 0; c < nchunk; ++c) s += cnt2[(size_t)c * n + i];
+    row_cnt[i] = s;
+  }
+}
+
+template <int MODE, bool UOT, int D, typename V>
+void launch_sweep_d(const SweepArgs& A, dim3 grid, cudaStream_t st) {
+  const bool stage = UOT && !A.pd.cv.C32 && A.pd.d <= kMaxDSmem;
+  const size_t shm = (size_t)kTJ * sizeof(float) * (1 + (stage ? A.pd.d : 0));
+  k_sweep<MODE, UOT, D, V><<<grid, kSweepThreads, shm, st>>>(A);
+}
+
+template <int MODE, bool UOT, typename V>
+void launch_sweep(const SweepArgs& A, dim3 grid, cudaStream_t st) {
+  if (!UOT) { launch_sweep_d<MODE, false, 1, V>(A, grid, st); return; }
+  switch (A.pd.cv.C32 ? 0 : A.pd.d) {
+    case 2: launch_sweep_d<MODE, true, 2, V>(A, grid, st); break;
+    case 3: launch_sweep_d<MODE, true, 3, V>(A, grid, st); break;
+    case 5: launch_sweep_d<MODE, true, 5, V>(A, grid, st); break;
+    case 10: launch_sweep_d<MODE, true, 10, V>(A, grid, st); break;
+    default: launch_sweep_d<MODE, true, 0, V>(A, grid, st); break;
+  }
+}
+
+}  // namespace
+
+// Geometry: row groups of 8 and column chunks (multiples of kTJ) chosen so
+// that the grid holds at least four waves of 1216 blocks when n is small.
+SweepGeo sweep_geometry(int n, int m) {
+  const int groups = (n + kRB - 1) / kRB;
+  int nchunk = (4 * 1216 + groups - 1) / groups;
+  const int max_chunks = (m + kTJ - 1) / kTJ;
+  nchunk = std::max(1, std::min(nchunk, std::min(max_chunks, 16)));
+  int chunk = (m + nchunk - 1) / nchunk;
+  chunk = ((chunk + kTJ - 1) / kTJ) * kTJ;
+  nchunk = (m + chunk - 1) / chunk;
+  SweepGeo g;
+  g.nchunk = nchunk;
+  g.chunk = chunk;
+  g.row_blocks = std::min(groups, 152 * 64);
+  return g;
+}
+
+static SweepArgs base_args(const ProbDev& pd, const Layout& L, char* ws) {
+  SweepArgs A;
+  memset(&A, 0, sizeof(A));
+  A.pd = pd;
+  A.sc = at<SketchScalars>(ws, L.scal);
+  A.rowf = at<float>(ws, L.rowf);
+  A.colf = at<float>(ws, L.colf);
+  A.ctrl = at<Ctrl>(ws, L.ctrl);
+  const SweepGeo g = sweep_geometry(pd.n, pd.m);
+  A.chunk = g.chunk;
+  A.nchunk = g.nchunk;
+  A.cnt2 = at<int>(ws, L.cnt2);
+  return A;
+}
+
+void launch_uot_Z(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st) {
+  SweepArgs A = base_args(pd, L, ws);
+  const SweepGeo g = sweep_geometry(pd.n, pd.m);
+  launch_sweep<SW_Z, true, float>(A, dim3(g.row_blocks, g.nchunk), st);
+}
+
+void launch_count(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st) {
+  SweepArgs A = base_args(pd, L, ws);
+  A.col_cnt = at<int>(ws, L.col_cnt);
+  const SweepGeo g = sweep_geometry(pd.n, pd.m);
+  const dim3 grid(g.row_blocks, g.nchunk);
+  if (pd.is_ot) launch_sweep<SW_COUNT, false, float>(A, grid, st);
+  else launch_sweep<SW_COUNT, true, float>(A, grid, st);
+  k_sum_chunks<<<std::max(1, std::min(1216, (pd.n + 255) / 256)), 256, 0, st>>>(pd.n, g.nchunk, A.cnt2,
+                                                                                 at<int>(ws, L.row_cnt), A.ctrl);
+}
+
+template <typename V>
+static void fill_v(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st) {
+  SweepArgs A = base_args(pd, L, ws);
+  A.row_ptr = at<int>(ws, L.row_ptr);
+  A.col_idx = at<int>(ws, L.col_idx);
+  A.val = ws + L.val;
+  A.col_cur = at<int>(ws, L.col_cur);
+  A.col_end = at<int>(ws, L.col_ptr) + 1;
+  A.tmp_row = at<int>(ws, L.tmp_row);
+  A.tmp_src = at<int>(ws, L.tmp_src);
+  const SweepGeo g = sweep_geometry(pd.n, pd.m);
+  const dim3 grid(g.row_blocks, g.nchunk);
+  if (pd.is_ot) launch_sweep<SW_FILL, false, V>(A, grid, st);
+  else launch_sweep<SW_FILL, true, V>(A, grid, st);
+}
+
+void launch_fill(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st) {
+  switch (kd) {
+    case SPS_F64: fill_v<double>(pd, L, ws, st); break;
+    case SPS_F32: fill_v<float>(pd, L, ws, st); break;
+    case SPS_BF16: fill_v<__nv_bfloat16>(pd, L, ws, st); break;
+    case SPS_F16: fill_v<__half>(pd, L, ws, st); break;
+  }
+}
+
+}  // namespace sps
