@@ -33,33 +33,39 @@ namespace sps {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;        // objective and set-up kernels
+constexpr int kIterThreads = 1024;   // iteration kernels: one or two blocks per SM
 constexpr int kWarps = kThreads / 32;
 constexpr long long kSpinLimit = 20000000;  // grid-barrier wait limit (about 1-2 s)
 
-// Sparse dot product of one row by a segment of LPR lanes (LPR in 8, 16, 32):
-// four independent chains per lane so that index and value loads of several
-// strides are in flight, then a butterfly reduction inside the segment.
+// Sparse dot product of one row by a segment of LPR lanes (LPR in 4 .. 32).
+// A lane takes kU elements of the row per batch: all their index and value
+// loads are issued first, then all gathers of x, so a batch costs two memory
+// round trips however long it is; a butterfly reduction closes the segment.
 template <int LPR, typename V, typename T>
 __device__ __forceinline__ T seg_row_dot(const int* __restrict__ idx, const V* __restrict__ val,
                                          const T* __restrict__ x, int lo, int hi, int sl) {
-  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-  int k = lo + sl;
-  for (; k + 3 * LPR < hi; k += 4 * LPR) {
-    const int i0 = __ldg(idx + k), i1 = __ldg(idx + k + LPR), i2 = __ldg(idx + k + 2 * LPR),
-              i3 = __ldg(idx + k + 3 * LPR);
-    const T v0 = load_as<T>(val + k), v1 = load_as<T>(val + k + LPR), v2 = load_as<T>(val + k + 2 * LPR),
-            v3 = load_as<T>(val + k + 3 * LPR);
-    a0 += v0 * __ldg(x + i0);
-    a1 += v1 * __ldg(x + i1);
-    a2 += v2 * __ldg(x + i2);
-    a3 += v3 * __ldg(x + i3);
-  }
-  for (; k < hi; k += LPR) a0 += load_as<T>(val + k) * __ldg(x + __ldg(idx + k));
-  T s = (a0 + a1) + (a2 + a3);
+  constexpr int kU = sizeof(T) == 8 ? 4 : (LPR >= 32 ? 8 : (LPR == 16 ? 12 : 16));
+  T acc = 0;
+  for (int k0 = lo + sl; k0 < hi; k0 += LPR * kU) {
+    int id[kU];
+    T vv[kU];
 #pragma unroll
-  for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
+    for (int u = 0; u < kU; ++u) {
+      const int k = k0 + u * LPR;
+      const bool in = k < hi;
+      id[u] = in ? __ldg(idx + k) : -1;
+      vv[u] = in ? load_as<T>(val + k) : (T)0;
+    }
+    T xv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) xv[u] = id[u] >= 0 ? __ldg(x + id[u]) : (T)0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) acc += vv[u] * xv[u];
+  }
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
 }
 
 template <typename T> __device__ __forceinline__ T powT(T x, T y);
@@ -81,9 +87,11 @@ struct IterArgs {
   int nblk;
 };
 
-// Sum of NV doubles over the block with one barrier; result in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum_multi(double (&v)[NV], double* sh /* NV x 32 */) {
+// Sum of NV values over the block with one barrier; result in thread 0.
+// Accumulations inside a phase use the iterate type: on this GPU the FP64
+// pipe is narrow, and only the per-block partials need FP64.
+template <int NV, typename R>
+__device__ __forceinline__ void block_sum_multi(R (&v)[NV], R* sh /* NV x 32 */) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int p = 0; p < NV; ++p) v[p] = warp_sum(v[p]);
@@ -95,7 +103,7 @@ __device__ __forceinline__ void block_sum_multi(double (&v)[NV], double* sh /* N
   if (w == 0) {
 #pragma unroll
     for (int p = 0; p < NV; ++p) {
-      const double x = lane < (int)(blockDim.x >> 5) ? sh[p * 32 + lane] : 0.0;
+      const R x = lane < (int)(blockDim.x >> 5) ? sh[p * 32 + lane] : (R)0;
       v[p] = warp_sum(x);
     }
   }
@@ -104,20 +112,22 @@ __device__ __forceinline__ void block_sum_multi(double (&v)[NV], double* sh /* N
 
 // Deterministic reduction of NP arrays of block partials (fixed strided
 // subsets per thread, fixed tree); result in out[] (shared), valid after return.
-template <int NP>
-__device__ void reduce_parts(const double* part, int nblk, double* out, double* sh) {
-  double s[NP];
+template <int NP, typename R>
+__device__ void reduce_parts(const double* part, int nblk, double* out) {
+  if (threadIdx.x < 32) {
+    R s[NP];
 #pragma unroll
-  for (int p = 0; p < NP; ++p) s[p] = 0.0;
+    for (int p = 0; p < NP; ++p) s[p] = (R)0;
 #pragma unroll 4
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    for (int b = threadIdx.x; b < nblk; b += 32) {
 #pragma unroll
-    for (int p = 0; p < NP; ++p) s[p] += __ldcg(part + (size_t)p * nblk + b);
-  }
-  block_sum_multi<NP>(s, sh);
-  if (threadIdx.x == 0) {
+      for (int p = 0; p < NP; ++p) s[p] += (R)__ldcg(part + (size_t)p * nblk + b);
+    }
 #pragma unroll
-    for (int p = 0; p < NP; ++p) out[p] = s[p];
+    for (int p = 0; p < NP; ++p) {
+      s[p] = warp_sum(s[p]);
+      if (threadIdx.x == 0) out[p] = (double)s[p];
+    }
   }
   __syncthreads();
 }
@@ -125,7 +135,7 @@ __device__ void reduce_parts(const double* part, int nblk, double* out, double* 
 // Row phase of iteration t -> t+1 for the rows of this block; returns the
 // block sums (thread 0) of residual, unreachable a-mass and |u^{t+1} - u^t|.
 template <int LPR, typename V, typename T, bool UOT>
-__device__ __forceinline__ void row_phase(const IterArgs& A, int t, double (&out)[3], double* sh) {
+__device__ __forceinline__ void row_phase(const IterArgs& A, int t, double (&out)[3], T* sh) {
   const T* v = (const T*)A.vbuf + (size_t)(t & 1) * A.m;
   const T* uold = (const T*)A.ubuf + (size_t)(t & 1) * A.n;
   T* unew = (T*)A.ubuf + (size_t)((t + 1) & 1) * A.n;
@@ -134,9 +144,10 @@ __device__ __forceinline__ void row_phase(const IterArgs& A, int t, double (&out
   constexpr int RPW = 32 / LPR;
   const int lane = threadIdx.x & 31, sl = lane & (LPR - 1);
   const T phi = (T)A.phi, inv_phi = (T)A.inv_phi;
-  double res = 0.0, unr = 0.0, dl = 0.0;
-  const int wg = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  for (int base = wg * RPW; base < A.n; base += gridDim.x * kWarps * RPW) {
+  T res = 0, unr = 0, dl = 0;
+  const int nw = blockDim.x >> 5;
+  const int wg = blockIdx.x * nw + (threadIdx.x >> 5);
+  for (int base = wg * RPW; base < A.n; base += gridDim.x * nw * RPW) {
     const int i = base + lane / LPR;
     const bool ok = i < A.n;
     const int lo = ok ? __ldg(A.row_ptr + i) : 0, hi = ok ? __ldg(A.row_ptr + i + 1) : 0;
@@ -148,22 +159,23 @@ __device__ __forceinline__ void row_phase(const IterArgs& A, int t, double (&out
       if (q > (T)0) {
         un = UOT ? powT<T>(ai / q, phi) : ai / q;
         const T lhs = (UOT ? powT<T>(uo, inv_phi) : uo) * q;
-        res += fabs((double)lhs - (double)ai);
+        res += fabs(lhs - ai);
       } else {
         un = (T)0;
-        unr += (double)ai;
+        unr += ai;
       }
-      dl += fabs((double)un - (double)uo);
+      dl += fabs(un - uo);
       unew[i] = un;
     }
   }
-  out[0] = res; out[1] = unr; out[2] = dl;
-  block_sum_multi<3>(out, sh);
+  T o[3] = {res, unr, dl};
+  block_sum_multi<3, T>(o, sh);
+  out[0] = (double)o[0]; out[1] = (double)o[1]; out[2] = (double)o[2];
 }
 
 // Column phase: v^{t+1} from u^{t+1}; block sums of unreachable b-mass and |v^{t+1} - v^t|.
 template <int LPR, typename V, typename T, bool UOT>
-__device__ __forceinline__ void col_phase(const IterArgs& A, int t, double (&out)[2], double* sh) {
+__device__ __forceinline__ void col_phase(const IterArgs& A, int t, double (&out)[2], T* sh) {
   const T* u = (const T*)A.ubuf + (size_t)((t + 1) & 1) * A.n;
   const T* vold = (const T*)A.vbuf + (size_t)(t & 1) * A.m;
   T* vnew = (T*)A.vbuf + (size_t)((t + 1) & 1) * A.m;
@@ -172,9 +184,10 @@ __device__ __forceinline__ void col_phase(const IterArgs& A, int t, double (&out
   constexpr int RPW = 32 / LPR;
   const int lane = threadIdx.x & 31, sl = lane & (LPR - 1);
   const T phi = (T)A.phi;
-  double unb = 0.0, dl = 0.0;
-  const int wg = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  for (int base = wg * RPW; base < A.m; base += gridDim.x * kWarps * RPW) {
+  T unb = 0, dl = 0;
+  const int nw = blockDim.x >> 5;
+  const int wg = blockIdx.x * nw + (threadIdx.x >> 5);
+  for (int base = wg * RPW; base < A.m; base += gridDim.x * nw * RPW) {
     const int j = base + lane / LPR;
     const bool ok = j < A.m;
     const int lo = ok ? __ldg(A.col_ptr + j) : 0, hi = ok ? __ldg(A.col_ptr + j + 1) : 0;
@@ -187,15 +200,24 @@ __device__ __forceinline__ void col_phase(const IterArgs& A, int t, double (&out
         vn = UOT ? powT<T>(bj / r, phi) : bj / r;
       } else {
         vn = (T)0;
-        unb += (double)bj;
+        unb += bj;
       }
-      dl += fabs((double)vn - (double)vo);
+      dl += fabs(vn - vo);
       vnew[j] = vn;
     }
   }
-  out[0] = unb; out[1] = dl;
-  block_sum_multi<2>(out, sh);
+  T o[2] = {unb, dl};
+  block_sum_multi<2, T>(o, sh);
+  out[0] = (double)o[0]; out[1] = (double)o[1];
 }
+
+// Decision state of the solve.  The persistent kernel keeps it in block 0's
+// shared memory across iterations (only written to the control block); the
+// per-phase kernels load it from the control block.
+struct DecState {
+  int done;
+  double delta_u, delta_v;
+};
 
 // Decisions taken by one thread from the reduced partials.  Only the row
 // phase of iteration t -> t+1 stops a solve, and always on the pair
@@ -203,33 +225,47 @@ __device__ __forceinline__ void col_phase(const IterArgs& A, int t, double (&out
 //   residual rule:  rho_t (this row phase) <= tol;
 //   paper's rule:   ||u^t - u^{t-1}||_1 (row phase of iteration t, stored) +
 //                   ||v^t - v^{t-1}||_1 (column phase of iteration t, stored) <= tol.
-__device__ __forceinline__ void decide_row(Ctrl* ctrl, const IterArgs& A, int t, const double* tot) {
+__device__ __forceinline__ void decide_row(Ctrl* ctrl, DecState& S, const IterArgs& A, int t, const double* tot) {
   ctrl->last_residual = tot[0];
   ctrl->last_unreach_a = tot[1];
-  if (!ctrl->done) {
+  if (!S.done) {
+    int stop = 0, numeric = 0;
+    double r = tot[0];
     if (A.stop_rule == SPS_STOP_RESIDUAL) {
-      if (!isfinite(tot[0])) {
-        ctrl->done = 1; ctrl->status = SPS_ERR_NUMERIC; ctrl->iters = t; ctrl->residual = tot[0];
-      } else if (t >= 1 && tot[0] <= A.tol) {
-        ctrl->done = 1; ctrl->iters = t; ctrl->residual = tot[0]; ctrl->unreach_a = tot[1];
-      }
+      numeric = !isfinite(r);
+      stop = numeric || (t >= 1 && r <= A.tol);
     } else if (t >= 1) {
-      const double d = ctrl->delta_u + ctrl->delta_v;
-      if (!isfinite(d)) {
-        ctrl->done = 1; ctrl->status = SPS_ERR_NUMERIC; ctrl->iters = t; ctrl->residual = d;
-      } else if (d <= A.tol) {
-        ctrl->done = 1; ctrl->iters = t; ctrl->residual = d; ctrl->unreach_a = tot[1];
-      }
+      r = S.delta_u + S.delta_v;
+      numeric = !isfinite(r);
+      stop = numeric || r <= A.tol;
+    }
+    if (stop) {
+      S.done = 1;
+      ctrl->iters = t;
+      ctrl->residual = r;
+      ctrl->unreach_a = tot[1];
+      if (numeric) ctrl->status = SPS_ERR_NUMERIC;
+      __threadfence();
+      ctrl->done = 1;
     }
   }
-  ctrl->delta_u = tot[2];   // ||u^{t+1} - u^t||_1, judged with the next column phase
+  S.delta_u = tot[2];   // ||u^{t+1} - u^t||_1, judged with the next column phase
+  ctrl->delta_u = tot[2];
 }
 
-__device__ __forceinline__ void decide_col(Ctrl* ctrl, const IterArgs& A, int t, const double* tot) {
-  (void)A;
+__device__ __forceinline__ void decide_col(Ctrl* ctrl, DecState& S, int t, const double* tot) {
   ctrl->unreach_b = tot[0];
+  S.delta_v = tot[1];
   ctrl->delta_v = tot[1];
   ctrl->t = t + 1;
+}
+
+__device__ __forceinline__ DecState load_state(const Ctrl* ctrl) {
+  DecState S;
+  S.done = ctrl->done;
+  S.delta_u = ctrl->delta_u;
+  S.delta_v = ctrl->delta_v;
+  return S;
 }
 
 // Thread 0 publishes the block's partials, fences, and counts the block in;
@@ -264,7 +300,7 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl) {
     } else {
       long long spins = 0;
       while (*gen == g) {
-        __nanosleep(64);
+        if (spins > 4096) __nanosleep(32);
         if (++spins > kSpinLimit) { ok = 0; break; }
       }
     }
@@ -277,12 +313,14 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl) {
 }
 
 template <int LR, int LC, typename V, typename T, bool UOT>
-__global__ void __launch_bounds__(kThreads) k_iterate(IterArgs A, int iters) {
-  __shared__ double sh[3 * 32];
+__global__ void __launch_bounds__(kIterThreads) k_iterate(IterArgs A, int iters) {
+  __shared__ T sh[3 * 32];
   __shared__ double tot[3];
+  __shared__ DecState S;   // block 0's decision state
   Ctrl* ctrl = A.ctrl;
   if (ctrl->done) return;
   int t = ctrl->t;
+  if (blockIdx.x == 0 && threadIdx.x == 0) S = load_state(ctrl);
   for (int k = 0; k < iters; ++k) {
     double r3[3];
     row_phase<LR, V, T, UOT>(A, t, r3, sh);
@@ -293,8 +331,8 @@ __global__ void __launch_bounds__(kThreads) k_iterate(IterArgs A, int iters) {
     }
     if (!grid_barrier(ctrl)) return;
     if (blockIdx.x == 0) {
-      reduce_parts<3>(A.part, A.nblk, tot, sh);
-      if (threadIdx.x == 0) decide_row(ctrl, A, t, tot);
+      reduce_parts<3, T>(A.part, A.nblk, tot);
+      if (threadIdx.x == 0) decide_row(ctrl, S, A, t, tot);
     }
     double c2[2];
     col_phase<LC, V, T, UOT>(A, t, c2, sh);
@@ -305,16 +343,16 @@ __global__ void __launch_bounds__(kThreads) k_iterate(IterArgs A, int iters) {
     if (!grid_barrier(ctrl)) return;
     if (*(volatile int*)&ctrl->done) return;
     if (blockIdx.x == 0) {
-      reduce_parts<2>(A.part + 3 * (size_t)A.nblk, A.nblk, tot, sh);
-      if (threadIdx.x == 0) decide_col(ctrl, A, t, tot);
+      reduce_parts<2, T>(A.part + 3 * (size_t)A.nblk, A.nblk, tot);
+      if (threadIdx.x == 0) decide_col(ctrl, S, t, tot);
     }
     ++t;
   }
 }
 
 template <int LPR, typename V, typename T, bool UOT>
-__global__ void __launch_bounds__(kThreads) k_row_pass(IterArgs A) {
-  __shared__ double sh[3 * 32];
+__global__ void __launch_bounds__(kIterThreads) k_row_pass(IterArgs A) {
+  __shared__ T sh[3 * 32];
   __shared__ double tot[3];
   Ctrl* ctrl = A.ctrl;
   if (ctrl->done) return;
@@ -322,16 +360,17 @@ __global__ void __launch_bounds__(kThreads) k_row_pass(IterArgs A) {
   double r3[3];
   row_phase<LPR, V, T, UOT>(A, t, r3, sh);
   if (!publish_and_check_last(&ctrl->blocks_a, A.part, A.nblk, r3, 3, 0)) return;
-  reduce_parts<3>(A.part, A.nblk, tot, sh);
+  reduce_parts<3, T>(A.part, A.nblk, tot);
   if (threadIdx.x == 0) {
-    decide_row(ctrl, A, t, tot);
+    DecState S = load_state(ctrl);
+    decide_row(ctrl, S, A, t, tot);
     ctrl->blocks_a = 0u;
   }
 }
 
 template <int LPR, typename V, typename T, bool UOT>
-__global__ void __launch_bounds__(kThreads) k_col_pass(IterArgs A) {
-  __shared__ double sh[3 * 32];
+__global__ void __launch_bounds__(kIterThreads) k_col_pass(IterArgs A) {
+  __shared__ T sh[3 * 32];
   __shared__ double tot[3];
   Ctrl* ctrl = A.ctrl;
   if (ctrl->done) return;
@@ -339,9 +378,10 @@ __global__ void __launch_bounds__(kThreads) k_col_pass(IterArgs A) {
   double c2[2];
   col_phase<LPR, V, T, UOT>(A, t, c2, sh);
   if (!publish_and_check_last(&ctrl->blocks_b, A.part, A.nblk, c2, 2, 3)) return;
-  reduce_parts<2>(A.part + 3 * (size_t)A.nblk, A.nblk, tot, sh);
+  reduce_parts<2, T>(A.part + 3 * (size_t)A.nblk, A.nblk, tot);
   if (threadIdx.x == 0) {
-    decide_col(ctrl, A, t, tot);
+    DecState S = load_state(ctrl);
+    decide_col(ctrl, S, t, tot);
     ctrl->blocks_b = 0u;
   }
 }
@@ -388,10 +428,11 @@ __global__ void __launch_bounds__(kThreads) k_obj_rows(ProbDev pd, const SketchS
   const T* u = ubuf + (size_t)(it & 1) * pd.n;
   const T* v = vbuf + (size_t)(it & 1) * pd.m;
   const int lane = threadIdx.x & 31;
+  // per-element terms and per-row sums in the iterate type, FP64 across rows
   double tr = 0.0, ne = 0.0, lp = 0.0, ms = 0.0, kla = 0.0;
   for (int i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < pd.n; i += gridDim.x * kWarps) {
     const T ui = u[i];
-    double rs = 0.0;
+    T rtr = 0, rne = 0, rlp = 0, rs = 0;
     if (ui > (T)0) {
       const float ri = rowf[i];
       for (int k = ptr[i] + lane; k < ptr[i + 1]; k += 32) {
@@ -400,21 +441,21 @@ __global__ void __launch_bounds__(kThreads) k_obj_rows(ProbDev pd, const SketchS
         if (!(Tij > (T)0)) continue;
         float D = 0.0f;
         const float p = pstar_raw<UOT>(pd, sc, ri, colf, i, j, &D);
-        const double ps = p < 1.0f ? (double)p : 1.0;
-        double C;
-        if (sizeof(T) == 8) C = raw64(pd.cv, i, j) / sc.dn64;
-        else C = (double)__fdiv_rn(UOT ? D : raw32(pd.cv, i, j), sc.dn32);
-        const double td = (double)Tij;
-        tr += td * C;
-        ne += td * ((double)log(Tij) - 1.0);
-        lp += td * log(ps);
-        rs += td;
+        const T ps = p < 1.0f ? (T)p : (T)1;
+        T C;
+        if (sizeof(T) == 8) C = (T)(raw64(pd.cv, i, j) / sc.dn64);
+        else C = (T)__fdiv_rn(UOT ? D : raw32(pd.cv, i, j), sc.dn32);
+        rtr += Tij * C;
+        rne += Tij * (log(Tij) - (T)1);
+        rlp += Tij * log(ps);
+        rs += Tij;
       }
     }
-    rs = warp_sum(rs);
+    rtr = warp_sum(rtr); rne = warp_sum(rne); rlp = warp_sum(rlp); rs = warp_sum(rs);
     if (lane == 0) {
-      ms += rs;
-      kla += kl_term(rs, (double)a[i]);
+      tr += (double)rtr; ne += (double)rne; lp += (double)rlp;
+      ms += (double)rs;
+      kla += kl_term((double)rs, (double)a[i]);
     }
   }
   const double vals[5] = {tr, ne, lp, ms, kla};
@@ -491,14 +532,24 @@ IterArgs make_args(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& 
   return A;
 }
 
+// Blocks of the iteration kernels: all SMs, as many per SM as fit, never more
+// than the partial arrays hold.
+template <typename K>
+int iter_grid(K fn, int cap) {
+  int dev = 0, nsm = 152, per_sm = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kIterThreads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  return std::max(1, std::min(cap, nsm * per_sm));
+}
+
 template <int LPR, typename V, typename T>
-void pass_lpr(const IterArgs& A, bool uot, bool row, cudaStream_t st) {
+void pass_lpr(IterArgs A, bool uot, bool row, cudaStream_t st) {
   if (row) {
-    if (uot) k_row_pass<LPR, V, T, true><<<A.nblk, kThreads, 0, st>>>(A);
-    else k_row_pass<LPR, V, T, false><<<A.nblk, kThreads, 0, st>>>(A);
+    if (uot) { auto f = k_row_pass<LPR, V, T, true>; A.nblk = iter_grid(f, A.nblk); f<<<A.nblk, kIterThreads, 0, st>>>(A); }
+    else { auto f = k_row_pass<LPR, V, T, false>; A.nblk = iter_grid(f, A.nblk); f<<<A.nblk, kIterThreads, 0, st>>>(A); }
   } else {
-    if (uot) k_col_pass<LPR, V, T, true><<<A.nblk, kThreads, 0, st>>>(A);
-    else k_col_pass<LPR, V, T, false><<<A.nblk, kThreads, 0, st>>>(A);
+    if (uot) { auto f = k_col_pass<LPR, V, T, true>; A.nblk = iter_grid(f, A.nblk); f<<<A.nblk, kIterThreads, 0, st>>>(A); }
+    else { auto f = k_col_pass<LPR, V, T, false>; A.nblk = iter_grid(f, A.nblk); f<<<A.nblk, kIterThreads, 0, st>>>(A); }
   }
 }
 
@@ -506,7 +557,8 @@ template <typename V, typename T>
 void one_pass(const IterArgs& A, bool uot, bool row, int lpr, cudaStream_t st) {
   if (lpr >= 32) pass_lpr<32, V, T>(A, uot, row, st);
   else if (lpr >= 16) pass_lpr<16, V, T>(A, uot, row, st);
-  else pass_lpr<8, V, T>(A, uot, row, st);
+  else if (lpr >= 8) pass_lpr<8, V, T>(A, uot, row, st);
+  else pass_lpr<4, V, T>(A, uot, row, st);
 }
 
 // Cooperative launch of the persistent kernel; false when the device refuses it
@@ -518,11 +570,11 @@ bool coop_launch(IterArgs A, int iters, cudaStream_t st) {
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0) != cudaSuccess || per_sm < 1) return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kIterThreads, 0) != cudaSuccess || per_sm < 1) return false;
   const int grid = std::min(A.nblk, nsm * per_sm);
   A.nblk = grid;
   void* args[] = {(void*)&A, (void*)&iters};
-  if (cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kThreads), args, 0, st) != cudaSuccess) {
+  if (cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kIterThreads), args, 0, st) != cudaSuccess) {
     cudaGetLastError();  // clear the refusal
     return false;
   }
@@ -533,14 +585,17 @@ template <int LR, typename V, typename T, bool UOT>
 bool coop_lc(const IterArgs& A, int lc, int iters, cudaStream_t st) {
   if (lc >= 32) return coop_launch<LR, 32, V, T, UOT>(A, iters, st);
   if (lc >= 16) return coop_launch<LR, 16, V, T, UOT>(A, iters, st);
-  return coop_launch<LR, 8, V, T, UOT>(A, iters, st);
+  if (lc >= 8) return coop_launch<LR, 8, V, T, UOT>(A, iters, st);
+  return coop_launch<LR, 4, V, T, UOT>(A, iters, st);
 }
 
+// Instantiated lane pairs: equal lanes for rows and columns, or neighbours.
 template <typename V, typename T, bool UOT>
 bool coop(const IterArgs& A, int lr, int lc, int iters, cudaStream_t st) {
   if (lr >= 32) return coop_lc<32, V, T, UOT>(A, lc, iters, st);
   if (lr >= 16) return coop_lc<16, V, T, UOT>(A, lc, iters, st);
-  return coop_lc<8, V, T, UOT>(A, lc, iters, st);
+  if (lr >= 8) return coop_lc<8, V, T, UOT>(A, lc, iters, st);
+  return coop_lc<4, V, T, UOT>(A, lc, iters, st);
 }
 
 // Enqueue `iters` iterations; returns the number of kernels launched.
