@@ -44,7 +44,7 @@ def build_oracle(force: bool = False) -> str:
 class Problem(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("d", C.c_int32),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("C", C.c_void_p),
-                ("cost_norm", C.c_int32), ("a", C.c_void_p), ("b", C.c_void_p),
+                ("cost_norm", C.c_int32), ("cost_scale", C.c_double), ("a", C.c_void_p), ("b", C.c_void_p),
                 ("eps", C.c_double), ("lam", C.c_double), ("s", C.c_double),
                 ("seed", C.c_uint64), ("pid", C.c_uint32)]
 
@@ -164,7 +164,7 @@ class OracleProblem:
     """Holds the numpy arrays of one problem alive for the C struct."""
 
     def __init__(self, a, b, eps, s, lam=math.inf, x=None, y=None, C_=None, cost_norm=1,
-                 seed=0x5EED, pid=0):
+                 seed=0x5EED, pid=0, cost_scale=1.0):
         self.a = _c(a, np.float64)
         self.b = _c(b, np.float64)
         self.x = _c(x, np.float64)
@@ -174,10 +174,11 @@ class OracleProblem:
         self.d = 0 if self.x is None else (self.x.shape[1] if self.x.ndim == 2 else 1)
         self.eps, self.lam, self.s = float(eps), float(lam), float(s)
         self.cost_norm = int(cost_norm)
+        self.cost_scale = float(cost_scale)
         self.seed, self.pid = int(seed), int(pid)
         self.struct = Problem(self.n, self.m, self.d, _ptr(self.x), _ptr(self.y), _ptr(self.C),
-                              self.cost_norm, _ptr(self.a), _ptr(self.b), self.eps, self.lam,
-                              self.s, self.seed, self.pid)
+                              self.cost_norm, self.cost_scale, _ptr(self.a), _ptr(self.b), self.eps,
+                              self.lam, self.s, self.seed, self.pid)
         self._factors = None
 
     @property

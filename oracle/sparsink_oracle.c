@@ -263,6 +263,17 @@ static double raw_cost64(const orc_problem* P, int32_t i, int32_t j) {
 
 static int is_ot(const orc_problem* P) { return isinf(P->lambda) && P->lambda > 0; }
 
+/* Divisor of the raw cost: C = D / divisor.  With cost_norm = 1 it is the
+ * maximum of the binary32 raw costs over all pairs (a maximum is exact, so
+ * every implementation of the spec finds the same number); with cost_norm = 2
+ * the given cost_scale; otherwise 1.  Both the decision and the value path
+ * use it. */
+static double cost_divisor(const orc_problem* P, const orc_scalars* S) {
+  if (P->cost_norm == 1 && S->dmax32 > 0.0f) return (double)S->dmax32;
+  if (P->cost_norm == 2 && P->cost_scale > 0.0) return P->cost_scale;
+  return 1.0;
+}
+
 /* UOT weight w_ij = (A_i B_j) E(-D_ij kappa): the numerator of Eq. (pij-uot),
  * since K_ij^{eps/(2lam+eps)} = exp(-C_ij/(2lam+eps)). */
 static float uot_weight(const orc_problem* P, const float* rowf, const float* colf,
@@ -283,6 +294,7 @@ static int check_problem(const orc_problem* P) {
   if (P->n < 1 || P->m < 1) return -1;
   if (!P->C && (P->d < 1 || !P->x || !P->y)) return -1;
   if (!(P->eps > 0.0) || !(P->s > 0.0) || !(P->lambda > 0.0)) return -1;
+  if (P->cost_norm == 2 && !(P->cost_scale > 0.0)) return -1;
   if (!P->a || !P->b) return -1;
   for (int32_t i = 0; i < P->n; ++i) if (!(P->a[i] >= 0.0) || isinf(P->a[i])) return -1;
   for (int32_t j = 0; j < P->m; ++j) if (!(P->b[j] >= 0.0) || isinf(P->b[j])) return -1;
@@ -328,8 +340,7 @@ int orc_factors(const orc_problem* P, float* rowf, float* colf, orc_scalars* S) 
   /* Eq. (pij-uot) */
   double t = 2.0 * P->lambda + P->eps;
   S->gamma32 = (float)(P->lambda / t);
-  double dn = (P->cost_norm && dmax32 > 0.0f) ? (double)dmax32 : 1.0;
-  S->kappa32 = (float)(1.0 / (dn * t));
+  S->kappa32 = (float)(1.0 / (cost_divisor(P, S) * t));
   for (int32_t i = 0; i < n; ++i) {
     float a32 = (float)P->a[i];
     rowf[i] = a32 > 0.0f ? orc_exp32(S->gamma32 * orc_log32(a32)) : 0.0f;
@@ -389,7 +400,7 @@ int32_t orc_sample_row(const orc_problem* P, const float* rowf, const float* col
     float ps;
     if (!sample_elem(P, rowf, colf, S, i, j, &ps)) continue;
     double d64 = raw_cost64(P, i, j);
-    double Cn = (P->cost_norm && S->dmax64 > 0.0) ? d64 / S->dmax64 : d64;
+    double Cn = d64 / cost_divisor(P, S);
     double Kij = exp(-Cn / P->eps);
     if (cols) cols[c] = j;
     if (val) val[c] = Kij / (double)ps;
@@ -443,16 +454,18 @@ int64_t orc_sparsify(const orc_problem* P, int32_t* row_ptr, int32_t* col_idx, d
 
 int orc_dense_kernel(const orc_problem* P, double* K, double* Cn) {
   if (check_problem(P)) return -1;
-  double dmax = 0.0;
+  orc_scalars S;
+  memset(&S, 0, sizeof(S));
   for (int32_t i = 0; i < P->n; ++i)
     for (int32_t j = 0; j < P->m; ++j) {
-      double d = raw_cost64(P, i, j);
-      if (d > dmax) dmax = d;
+      float d = raw_cost32(P, i, j);
+      if (d > S.dmax32) S.dmax32 = d;
     }
+  const double dv = cost_divisor(P, &S);
   for (int32_t i = 0; i < P->n; ++i)
     for (int32_t j = 0; j < P->m; ++j) {
       double d = raw_cost64(P, i, j);
-      double c = (P->cost_norm && dmax > 0.0) ? d / dmax : d;
+      double c = d / dv;
       if (Cn) Cn[(int64_t)i * P->m + j] = c;
       if (K) K[(int64_t)i * P->m + j] = exp(-c / P->eps);
     }

@@ -72,7 +72,9 @@ typedef struct {
   const double* x;      /* n*d row-major, or NULL when C is given */
   const double* y;      /* m*d row-major, or NULL when C is given */
   const double* C;      /* n*m raw cost, or NULL (then squared Euclidean) */
-  int32_t cost_norm;    /* 1: divide the raw cost by its max over all pairs */
+  int32_t cost_norm;    /* 1: divide the raw cost by the max of its binary32 values over all pairs;
+                           2: divide by cost_scale; 0: raw */
+  double cost_scale;
   const double* a;      /* n */
   const double* b;      /* m */
   double eps;

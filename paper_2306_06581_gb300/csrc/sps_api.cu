@@ -200,7 +200,7 @@ static sps_status run_sketch(const sps_problem* P, const sps_params* Q, const La
   SPS_TRY(cuda_fail(cudaMemsetAsync(ws + L.scal, 0, sizeof(SketchScalars), st), "memset scalars"));
   const int it64 = Q->kdtype == SPS_F64;
   SPS_TRY(launch_prepare(pd, L, ws, it64, st));
-  if (P->cost_norm == SPS_COST_MAXNORM) SPS_TRY(launch_cost_max(pd, L, ws, it64 && pd.in_f64, st));
+  if (P->cost_norm == SPS_COST_MAXNORM) SPS_TRY(launch_cost_max(pd, L, ws, 0, st));
   SPS_TRY(launch_factors(pd, L, ws, st));
   SPS_TRY(launch_sample(pd, L, ws, Q->kdtype, st));
   SPS_TRY(read_ctrl(L, ws, hctrl, st));
@@ -412,7 +412,7 @@ sps_status sinkhorn_dense(const sps_problem* prob, const sps_params* prm, void* 
   SPS_TRY(cuda_fail(cudaMemsetAsync(ws + L.scal, 0, sizeof(SketchScalars), st), "memset scalars"));
   const int it64 = prm->kdtype == SPS_F64;
   SPS_TRY(launch_prepare(pd, L, ws, it64, st));
-  if (prob->cost_norm == SPS_COST_MAXNORM) SPS_TRY(launch_cost_max(pd, L, ws, it64 && pd.in_f64, st));
+  if (prob->cost_norm == SPS_COST_MAXNORM) SPS_TRY(launch_cost_max(pd, L, ws, 0, st));
   SPS_TRY(launch_scalars0(pd, L, ws, st));
   ev.rec(1, st);
   IterCfg ic;

@@ -182,7 +182,7 @@ __global__ void k_scalars(ProbDev pd, SketchScalars* sc, Ctrl* ctrl, int stage) 
     float dn32 = 1.0f;
     if (pd.cost_norm == SPS_COST_MAXNORM) {
       if (sc->dmax32 > 0.0f) dn32 = sc->dmax32;
-      if (sc->dmax64 > 0.0) dn64 = sc->dmax64; else dn64 = (double)dn32;
+      dn64 = (double)dn32;   // one divisor for both paths: the exact binary32 maximum
     } else if (pd.cost_norm == SPS_COST_SCALE) {
       dn64 = pd.cost_scale;
       dn32 = __double2float_rn(pd.cost_scale);

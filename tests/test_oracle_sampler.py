@@ -136,9 +136,15 @@ def test_values_and_log_values(orc):
     C = C / C.max()
     rows = np.repeat(np.arange(50), np.diff(sk["row_ptr"]))
     Cs = C[rows, sk["col_idx"]]
-    assert np.allclose(sk["cost"], Cs, rtol=1e-14, atol=1e-15)
-    assert np.allclose(sk["val"], np.exp(-Cs / w.eps) / sk["pstar"], rtol=1e-13)
-    assert np.allclose(sk["logval"], -Cs / w.eps - np.log(sk["pstar"].astype(np.float64)), rtol=1e-13)
+    # the divisor is the max of the binary32 distances: within binary32 rounding of the FP64 max
+    assert np.allclose(sk["cost"], Cs, rtol=2e-7, atol=1e-15)
+    Cx = sk["cost"]
+    assert np.allclose(sk["val"], np.exp(-Cx / w.eps) / sk["pstar"], rtol=1e-13)
+    assert np.allclose(sk["logval"], -Cx / w.eps - np.log(sk["pstar"].astype(np.float64)), rtol=1e-13)
+    # the cost at the sampled elements is the raw distance over one common divisor
+    D = ((w.x[:, None, :] - w.y[None]) ** 2).sum(-1)[rows, sk["col_idx"]]
+    ratio = D / Cx
+    assert np.allclose(ratio, ratio[0], rtol=1e-13)
 
 
 def test_pattern_deterministic_and_stream_specific(orc):
