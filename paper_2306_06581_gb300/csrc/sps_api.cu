@@ -92,6 +92,10 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
     L->csr_pos = take((size_t)cap * 4);
     L->tmp_row = take((size_t)cap * 4);
     L->tmp_src = take((size_t)cap * 4);
+    if (Q->log_domain) {
+      L->logval = take((size_t)cap * 4);
+      L->logvalT = take((size_t)cap * 4);
+    }
   }
   int part_blocks = nb;
   if (op == SPS_OP_DENSE) {
@@ -106,6 +110,13 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
     L->alpha = take((size_t)n * 4);
     L->beta = take((size_t)m * 4);
     L->ahat = take((size_t)n * 4);
+    if (Q->log_domain) {
+      L->bhat = take((size_t)m * 4);
+      L->erow = take((size_t)n * 4);
+      L->ecol = take((size_t)m * 4);
+      L->pot_a = take((size_t)n * 4);
+      L->pot_b = take((size_t)m * 4);
+    }
   }
   L->nblk_rows = nb;
   L->nblk_cols = nb;
@@ -136,7 +147,10 @@ static sps_status validate(const sps_problem* P, const sps_params* Q, int op) {
   if (!valid_dtype(Q->kdtype)) { set_error("bad kdtype"); return SPS_ERR_INVALID_ARG; }
   if (op == SPS_OP_DENSE && Q->kdtype != SPS_F64 && Q->kdtype != SPS_F32) { set_error("dense Sinkhorn iterates in F64 or F32"); return SPS_ERR_INVALID_ARG; }
   if (op == SPS_OP_DENSE && !P->C && P->d > 16) { set_error("dense Sinkhorn on points supports d <= 16 (d=%d)", P->d); return SPS_ERR_INVALID_ARG; }
-  if (Q->log_domain) { set_error("log_domain is not available in this build"); return SPS_ERR_INVALID_ARG; }
+  if (Q->log_domain && op == SPS_OP_DENSE) { set_error("log_domain applies to the sparse solvers"); return SPS_ERR_INVALID_ARG; }
+  if (Q->log_domain && Q->kdtype == SPS_F64) { set_error("log_domain stores K' in F32, BF16 or F16"); return SPS_ERR_INVALID_ARG; }
+  if (Q->log_domain && Q->stop_rule != SPS_STOP_RESIDUAL) { set_error("log_domain stops on the residual rule"); return SPS_ERR_INVALID_ARG; }
+  if (Q->log_domain && Q->absorb_tau < 0.0) { set_error("absorb_tau must be >= 0"); return SPS_ERR_INVALID_ARG; }
   if (op != SPS_OP_DENSE && (double)Q->s + 8.0 * sqrt(Q->s) + 1024.0 > 2147483647.0 &&
       (double)P->n * (double)P->m > 2147483647.0) {
     set_error("sample budget too large for int32 indices"); return SPS_ERR_CAPACITY;
@@ -237,11 +251,22 @@ static thread_local int g_iters_enqueued = 0;
 
 static sps_status run_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, const sps_params* Q,
                                  IterFn full, RowFn row_only, cudaStream_t st, Ctrl* h) {
-  SPS_TRY(launch_iter_init(pd, L, ws, ic, Q->init_alpha, Q->init_beta, st));
   int launched = 0;
+  if (ic.log_domain) {
+    // the first iteration runs exactly in the log domain and forms the pair (u^1, v^1)
+    SPS_TRY(launch_log_first_iteration(pd, L, ws, ic, Q->init_alpha, Q->init_beta, st));
+    launched = 1;
+    g_iters_enqueued = 1;
+  } else {
+    SPS_TRY(launch_iter_init(pd, L, ws, ic, Q->init_alpha, Q->init_beta, st));
+  }
+  if (launched >= ic.max_iter) {
+    SPS_TRY(read_ctrl(L, ws, h, st));
+  }
   int chunk = Q->check_every > 0 ? Q->check_every : (ic.persistent ? 32 : 4);
   for (;;) {
     const int k = std::min(chunk, ic.max_iter - launched);
+    if (k <= 0) break;
     SPS_TRY(full(pd, L, ws, ic, k, st));
     launched += k;
     g_iters_enqueued = launched;
@@ -321,9 +346,17 @@ static sps_status spar_sink_impl(const sps_problem* P, const sps_params* Q, void
   ic.max_iter = Q->max_iter;
   ic.lpr_rows = lanes_per_row((double)nnz / P->n, P->n);
   ic.lpr_cols = lanes_per_row((double)nnz / P->m, P->m);
-  SPS_TRY(run_iterations(pd, L, ws, ic, Q, launch_sparse_iterations, launch_sparse_row_only, st, &h));
-  ev.rec(2, st);
-  SPS_TRY(launch_sparse_objective(pd, L, ws, ic, alpha_out, beta_out, st));
+  ic.log_domain = Q->log_domain ? 1 : 0;
+  ic.tau = Q->absorb_tau > 0.0 ? Q->absorb_tau : 12.0;
+  if (ic.log_domain) {
+    SPS_TRY(run_iterations(pd, L, ws, ic, Q, launch_log_iterations, launch_log_row_only, st, &h));
+    ev.rec(2, st);
+    SPS_TRY(launch_log_objective(pd, L, ws, ic, alpha_out, beta_out, st));
+  } else {
+    SPS_TRY(run_iterations(pd, L, ws, ic, Q, launch_sparse_iterations, launch_sparse_row_only, st, &h));
+    ev.rec(2, st);
+    SPS_TRY(launch_sparse_objective(pd, L, ws, ic, alpha_out, beta_out, st));
+  }
   ev.rec(3, st);
   DevResult dr;
   SPS_TRY(cuda_fail(cudaMemcpyAsync(&dr, ws + L.res, sizeof(dr), cudaMemcpyDeviceToHost, st), "result read-back"));

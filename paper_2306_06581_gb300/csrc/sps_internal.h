@@ -75,6 +75,8 @@ struct Layout {
   size_t col_idx, val, row_idx, valT, csr_pos, tmp_row, tmp_src;
   size_t u, v, alpha, beta, ahat;   // iterates (u: two buffers)
   size_t qpart, rpart;              // dense: split partial vectors
+  size_t logval, logvalT;           // log-domain: log K~ in CSR / CSC order (binary32)
+  size_t bhat, erow, ecol, pot_a, pot_b;
   size_t part;                      // block partials
   size_t total;
   int64_t cap;                      // sketch capacity (elements)
@@ -132,11 +134,20 @@ struct IterCfg {
   int lpr_rows = 32;   // lanes per row of the row pass (8, 16, 32)
   int lpr_cols = 32;   // lanes per column of the column pass
   int persistent = 1;  // run chunks of iterations in one cooperative launch
+  int log_domain = 0;  // stabilised iterations with absorption
+  double tau = 12.0;   // absorption threshold on max |log u~|, |log v~|
 };
 sps_status launch_iter_init(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                             const void* init_alpha, const void* init_beta, cudaStream_t st);
 sps_status launch_sparse_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                                     int iters, cudaStream_t st);
+sps_status launch_log_first_iteration(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                      const void* init_alpha, const void* init_beta, cudaStream_t st);
+sps_status launch_log_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, int iters,
+                                 cudaStream_t st);
+sps_status launch_log_row_only(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, cudaStream_t st);
+sps_status launch_log_objective(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, void* alpha_out,
+                                void* beta_out, cudaStream_t st);
 sps_status launch_sparse_row_only(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                                   cudaStream_t st);
 sps_status launch_sparse_objective(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,

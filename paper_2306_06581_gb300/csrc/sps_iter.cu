@@ -28,49 +28,16 @@
 #include <algorithm>
 
 #include "sps_internal.h"
+#include "sps_iterdev.cuh"
 
 namespace sps {
 
 namespace {
 
+using namespace iterdev;
+
 constexpr int kThreads = 256;        // objective and set-up kernels
-constexpr int kIterThreads = 1024;   // iteration kernels: one or two blocks per SM
 constexpr int kWarps = kThreads / 32;
-constexpr long long kSpinLimit = 20000000;  // grid-barrier wait limit (about 1-2 s)
-
-// Sparse dot product of one row by a segment of LPR lanes (LPR in 4 .. 32).
-// A lane takes kU elements of the row per batch: all their index and value
-// loads are issued first, then all gathers of x, so a batch costs two memory
-// round trips however long it is; a butterfly reduction closes the segment.
-template <int LPR, typename V, typename T>
-__device__ __forceinline__ T seg_row_dot(const int* __restrict__ idx, const V* __restrict__ val,
-                                         const T* __restrict__ x, int lo, int hi, int sl) {
-  constexpr int kU = sizeof(T) == 8 ? 4 : (LPR >= 32 ? 8 : (LPR == 16 ? 12 : 16));
-  T acc = 0;
-  for (int k0 = lo + sl; k0 < hi; k0 += LPR * kU) {
-    int id[kU];
-    T vv[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int k = k0 + u * LPR;
-      const bool in = k < hi;
-      id[u] = in ? __ldg(idx + k) : -1;
-      vv[u] = in ? load_as<T>(val + k) : (T)0;
-    }
-    T xv[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) xv[u] = id[u] >= 0 ? __ldg(x + id[u]) : (T)0;
-#pragma unroll
-    for (int u = 0; u < kU; ++u) acc += vv[u] * xv[u];
-  }
-#pragma unroll
-  for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  return acc;
-}
-
-template <typename T> __device__ __forceinline__ T powT(T x, T y);
-template <> __device__ __forceinline__ float powT<float>(float x, float y) { return powf(x, y); }
-template <> __device__ __forceinline__ double powT<double>(double x, double y) { return pow(x, y); }
 
 struct IterArgs {
   int n, m;
@@ -86,51 +53,6 @@ struct IterArgs {
   double* part;        // kPartSlots x nblk
   int nblk;
 };
-
-// Sum of NV values over the block with one barrier; result in thread 0.
-// Accumulations inside a phase use the iterate type: on this GPU the FP64
-// pipe is narrow, and only the per-block partials need FP64.
-template <int NV, typename R>
-__device__ __forceinline__ void block_sum_multi(R (&v)[NV], R* sh /* NV x 32 */) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int p = 0; p < NV; ++p) v[p] = warp_sum(v[p]);
-  if (lane == 0) {
-#pragma unroll
-    for (int p = 0; p < NV; ++p) sh[p * 32 + w] = v[p];
-  }
-  __syncthreads();
-  if (w == 0) {
-#pragma unroll
-    for (int p = 0; p < NV; ++p) {
-      const R x = lane < (int)(blockDim.x >> 5) ? sh[p * 32 + lane] : (R)0;
-      v[p] = warp_sum(x);
-    }
-  }
-  __syncthreads();
-}
-
-// Deterministic reduction of NP arrays of block partials (fixed strided
-// subsets per thread, fixed tree); result in out[] (shared), valid after return.
-template <int NP, typename R>
-__device__ void reduce_parts(const double* part, int nblk, double* out) {
-  if (threadIdx.x < 32) {
-    R s[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) s[p] = (R)0;
-#pragma unroll 4
-    for (int b = threadIdx.x; b < nblk; b += 32) {
-#pragma unroll
-      for (int p = 0; p < NP; ++p) s[p] += (R)__ldcg(part + (size_t)p * nblk + b);
-    }
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      s[p] = warp_sum(s[p]);
-      if (threadIdx.x == 0) out[p] = (double)s[p];
-    }
-  }
-  __syncthreads();
-}
 
 // Row phase of iteration t -> t+1 for the rows of this block; returns the
 // block sums (thread 0) of residual, unreachable a-mass and |u^{t+1} - u^t|.
@@ -280,36 +202,6 @@ __device__ __forceinline__ bool publish_and_check_last(unsigned int* counter, do
   }
   __syncthreads();
   return am_last;
-}
-
-// Grid barrier of the cooperative kernel: arrival counter plus generation;
-// the waiting threads spin with a sleep and give up after kSpinLimit polls,
-// recording a failure instead of hanging.
-__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl) {
-  __shared__ int ok_sh;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* gen = &ctrl->bar_gen;
-    const unsigned int g = *gen;
-    __threadfence();
-    int ok = 1;
-    if (atomicAdd(&ctrl->bar_count, 1u) == gridDim.x - 1) {
-      ctrl->bar_count = 0u;
-      __threadfence();
-      atomicAdd(&ctrl->bar_gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*gen == g) {
-        if (spins > 4096) __nanosleep(32);
-        if (++spins > kSpinLimit) { ok = 0; break; }
-      }
-    }
-    __threadfence();
-    if (!ok) { ctrl->wait_timeout = 1; ctrl->done = 1; ctrl->status = SPS_ERR_CUDA; }
-    ok_sh = ok;
-  }
-  __syncthreads();
-  return ok_sh != 0;
 }
 
 template <int LR, int LC, typename V, typename T, bool UOT>
@@ -530,16 +422,6 @@ IterArgs make_args(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& 
   A.phi = ic.phi; A.inv_phi = 1.0 / ic.phi; A.tol = ic.tol; A.stop_rule = ic.stop_rule;
   A.ctrl = at<Ctrl>(ws, L.ctrl); A.part = at<double>(ws, L.part); A.nblk = L.nblk_rows;
   return A;
-}
-
-// Blocks of the iteration kernels: all SMs, as many per SM as fit, never more
-// than the partial arrays hold.
-template <typename K>
-int iter_grid(K fn, int cap) {
-  int dev = 0, nsm = 152, per_sm = 1;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kIterThreads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
-  return std::max(1, std::min(cap, nsm * per_sm));
 }
 
 template <int LPR, typename V, typename T>

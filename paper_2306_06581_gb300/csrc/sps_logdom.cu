@@ -1,0 +1,614 @@
+// sps_logdom.cu -- stabilised iterations for small eps (log_domain = 1).
+//
+// With eps = 0.01 the sketch values K~_ij = exp(-C_ij/eps)/p*_ij span more
+// than the binary32 range, and so do the scalings u, v.  The solve keeps
+//   - absorbed potentials alpha_i, beta_j (binary32),
+//   - stored kernel values K'_ij = K~_ij exp((alpha_i + beta_j)/eps), written
+//     per row (CSR) and per column (CSC) with a power-of-two scale 2^-e so that
+//     the largest stored value of every row / column lies in [1, 2) (this keeps
+//     BF16 and FP16 storage from flushing a whole row or column to zero),
+//   - scalings u~ = u e^{-alpha/eps}, v~ = v e^{-beta/eps} around 1.
+// In these variables Alg. 2 reads u~ = (a^ / (K' v~))^phi with
+// a^_i = a_i e^{-alpha_i/lam} (a^ = a for OT), and the stopping residual of a
+// pair is sum_i (a_i / a^_i) | u~_i^{1/phi} (K' v~)_i - a^_i |.
+// log K~_ij = -C_ij/eps - log p*_ij is the sparse cost C~ = C + eps log p* of
+// the UOT iteration lemma's proof divided by -eps; it is stored in binary32.
+//
+// The first iteration is done exactly in the log domain (log-sum-exp over
+// the support, rows then columns), which gives (alpha, beta) of the pair
+// (u^1, v^1); an absorb pass then writes K' and sets u~ = v~ = 1.  Later
+// iterations run in a persistent cooperative kernel; when max |log u~| or
+// max |log v~| exceeds tau, every block folds its scalings into alpha / beta
+// and rewrites its rows and columns of K' (two extra grid barriers).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "sps_internal.h"
+#include "sps_iterdev.cuh"
+
+namespace sps {
+
+namespace {
+
+using namespace iterdev;
+
+constexpr int kT = 256;
+constexpr float kLog2e = 1.4426950408889634f;
+
+struct LogArgs {
+  int n, m;
+  const int *row_ptr, *col_idx, *col_ptr, *row_idx;
+  void *val, *valT;                // K' storage (scaled)
+  const float *logval, *logvalT;   // log K~ (CSR / CSC order)
+  float *ubuf, *vbuf;              // u~ (2 x n), v~ (2 x m), parity of t
+  float *alpha, *beta;             // absorbed potentials
+  float *ahat, *bhat;
+  float *erow, *ecol;              // power-of-two exponents of stored rows / columns
+  const float *a, *b;
+  float eps, inv_eps, lam, inv_lam, phi, inv_phi, tol, tau;
+  int uot;
+  Ctrl* ctrl;
+  double* part;
+  int nblk;
+};
+
+__device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
+
+// log-sum-exp over one row (or column) by a whole warp: max, then sum.
+__device__ __forceinline__ float warp_lse(const int* idx, const float* logv, const float* pot, float inv_eps,
+                                          int lo, int hi, int lane) {
+  float mx = neg_inf();
+  for (int k = lo + lane; k < hi; k += 32) mx = fmaxf(mx, logv[k] + pot[idx[k]] * inv_eps);
+  mx = warp_max(mx);
+  if (mx == neg_inf()) return mx;
+  float s = 0.0f;
+  for (int k = lo + lane; k < hi; k += 32) s += expf(logv[k] + pot[idx[k]] * inv_eps - mx);
+  s = warp_sum(s);
+  return mx + logf(s);
+}
+
+// One exact log-domain half-iteration: pot_i = phi (eps log marg_i - eps LSE_j(logK~_ij + other_j/eps)).
+__global__ void __launch_bounds__(kT) k_lse_half(int rows, const int* ptr, const int* idx, const float* logv,
+                                                  const float* other, const float* marg, float* pot, float eps,
+                                                  float phi) {
+  const int lane = threadIdx.x & 31;
+  const float inv_eps = 1.0f / eps;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += (gridDim.x * blockDim.x) >> 5) {
+    const float L = warp_lse(idx, logv, other, inv_eps, ptr[i], ptr[i + 1], lane);
+    if (lane == 0) {
+      const float mi = marg[i];
+      pot[i] = (L == neg_inf() || !(mi > 0.0f)) ? neg_inf() : phi * eps * (logf(mi) - L);
+    }
+  }
+}
+
+// Write one row (CSR) or column (CSC) of K' = exp(logK~ + (pot_i + other_j)/eps)
+// scaled by 2^-e, e = floor(log2 of the largest value).
+template <typename V>
+__device__ __forceinline__ void absorb_segment(int lo, int hi, const int* idx, const float* logv, float pot_i,
+                                               const float* other, float inv_eps, V* out, float* e_out, int lane) {
+  float mx = neg_inf();
+  if (pot_i != neg_inf())
+    for (int k = lo + lane; k < hi; k += 32) {
+      const float o = other[idx[k]];
+      if (o != neg_inf()) mx = fmaxf(mx, logv[k] + (pot_i + o) * inv_eps);
+    }
+  mx = warp_max(mx);
+  const float e = (mx == neg_inf()) ? 0.0f : floorf(mx * kLog2e);
+  for (int k = lo + lane; k < hi; k += 32) {
+    const float o = other[idx[k]];
+    float z = neg_inf();
+    if (pot_i != neg_inf() && o != neg_inf()) z = logv[k] + (pot_i + o) * inv_eps;
+    out[k] = from_d<V>((double)exp2f(z * kLog2e - e));
+  }
+  if (lane == 0) *e_out = e;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kT) k_absorb_all(LogArgs A, int t) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = gw; i < A.n; i += nw)
+    absorb_segment<V>(A.row_ptr[i], A.row_ptr[i + 1], A.col_idx, A.logval, A.alpha[i], A.beta, A.inv_eps,
+                      (V*)A.val, A.erow + i, lane);
+  for (int j = gw; j < A.m; j += nw)
+    absorb_segment<V>(A.col_ptr[j], A.col_ptr[j + 1], A.row_idx, A.logvalT, A.beta[j], A.alpha, A.inv_eps,
+                      (V*)A.valT, A.ecol + j, lane);
+  // scalings of the pair t: 1 where the potential is finite, 0 where the row / column is unreachable
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+  float* u = A.ubuf + (size_t)(t & 1) * A.n;
+  float* v = A.vbuf + (size_t)(t & 1) * A.m;
+  for (int i = tid; i < A.n; i += st) {
+    const float al = A.alpha[i];
+    u[i] = al == neg_inf() ? 0.0f : 1.0f;
+    A.ahat[i] = A.uot && al != neg_inf() ? A.a[i] * expf(-al * A.inv_lam) : A.a[i];
+  }
+  for (int j = tid; j < A.m; j += st) {
+    const float be = A.beta[j];
+    v[j] = be == neg_inf() ? 0.0f : 1.0f;
+    A.bhat[j] = A.uot && be != neg_inf() ? A.b[j] * expf(-be * A.inv_lam) : A.b[j];
+  }
+  if (tid == 0) A.ctrl->t = t;
+}
+
+template <typename T>
+__global__ void k_log_init(int n, int m, float* alpha, float* beta, const T* al0, const T* be0, Ctrl* ctrl) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < n; i += stride) alpha[i] = al0 ? (float)al0[i] : 0.0f;
+  for (int64_t j = tid; j < m; j += stride) beta[j] = be0 ? (float)be0[j] : 0.0f;
+  if (tid == 0) {
+    ctrl->t = 0; ctrl->done = 0; ctrl->iters = 0;
+    ctrl->blocks_a = ctrl->blocks_b = ctrl->blocks_c = 0u;
+    ctrl->bar_count = 0u;
+    if (ctrl->status != SPS_OK) ctrl->done = 1;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Phases of the stabilised iteration.
+// ----------------------------------------------------------------------------
+template <int LPR, typename V, bool UOT>
+__device__ __forceinline__ void log_row_phase(const LogArgs& A, int t, float (&o)[3], float* sh) {
+  const float* v = A.vbuf + (size_t)(t & 1) * A.m;
+  const float* uold = A.ubuf + (size_t)(t & 1) * A.n;
+  float* unew = A.ubuf + (size_t)((t + 1) & 1) * A.n;
+  constexpr int RPW = 32 / LPR;
+  const int lane = threadIdx.x & 31, sl = lane & (LPR - 1);
+  float res = 0.0f, unr = 0.0f, mlog = 0.0f;
+  const int nw = blockDim.x >> 5;
+  const int wg = blockIdx.x * nw + (threadIdx.x >> 5);
+  for (int base = wg * RPW; base < A.n; base += gridDim.x * nw * RPW) {
+    const int i = base + lane / LPR;
+    const bool ok = i < A.n;
+    const int lo = ok ? __ldg(A.row_ptr + i) : 0, hi = ok ? __ldg(A.row_ptr + i + 1) : 0;
+    float ah = 0.f, ai = 0.f, uo = 0.f, er = 0.f;
+    if (ok && sl == 0) { ah = A.ahat[i]; ai = A.a[i]; uo = uold[i]; er = A.erow[i]; }
+    const float qs = seg_row_dot<LPR, V, float>(A.col_idx, (const V*)A.val, v, lo, hi, sl);
+    if (ok && sl == 0) {
+      const float q = qs * exp2f(er);
+      float un;
+      if (q > 0.0f) {
+        un = UOT ? powf(ah / q, A.phi) : ah / q;
+        const float lhs = (UOT ? powf(uo, A.inv_phi) : uo) * q;
+        const float w = UOT ? (ah > 0.0f ? ai / ah : 1.0f) : 1.0f;
+        res += w * fabsf(lhs - ah);
+        if (un > 0.0f) mlog = fmaxf(mlog, fabsf(logf(un)));
+      } else {
+        un = 0.0f;
+        unr += ai;
+      }
+      unew[i] = un;
+    }
+  }
+  o[0] = res; o[1] = unr; o[2] = mlog;
+  float s2[2] = {res, unr};
+  block_sum_multi<2, float>(s2, sh);
+  o[0] = s2[0]; o[1] = s2[1];
+  o[2] = warp_max(mlog);
+  if ((threadIdx.x & 31) == 0) sh[64 + (threadIdx.x >> 5)] = o[2];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mm = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, sh[64 + w]);
+    o[2] = mm;
+  }
+  __syncthreads();
+}
+
+template <int LPR, typename V, bool UOT>
+__device__ __forceinline__ void log_col_phase(const LogArgs& A, int t, float (&o)[2], float* sh) {
+  const float* u = A.ubuf + (size_t)((t + 1) & 1) * A.n;
+  float* vnew = A.vbuf + (size_t)((t + 1) & 1) * A.m;
+  constexpr int RPW = 32 / LPR;
+  const int lane = threadIdx.x & 31, sl = lane & (LPR - 1);
+  float unb = 0.0f, mlog = 0.0f;
+  const int nw = blockDim.x >> 5;
+  const int wg = blockIdx.x * nw + (threadIdx.x >> 5);
+  for (int base = wg * RPW; base < A.m; base += gridDim.x * nw * RPW) {
+    const int j = base + lane / LPR;
+    const bool ok = j < A.m;
+    const int lo = ok ? __ldg(A.col_ptr + j) : 0, hi = ok ? __ldg(A.col_ptr + j + 1) : 0;
+    float bh = 0.f, bj = 0.f, ec = 0.f;
+    if (ok && sl == 0) { bh = A.bhat[j]; bj = A.b[j]; ec = A.ecol[j]; }
+    const float rs = seg_row_dot<LPR, V, float>(A.row_idx, (const V*)A.valT, u, lo, hi, sl);
+    if (ok && sl == 0) {
+      const float r = rs * exp2f(ec);
+      float vn;
+      if (r > 0.0f) {
+        vn = UOT ? powf(bh / r, A.phi) : bh / r;
+        if (vn > 0.0f) mlog = fmaxf(mlog, fabsf(logf(vn)));
+      } else {
+        vn = 0.0f;
+        unb += bj;
+      }
+      vnew[j] = vn;
+    }
+  }
+  float s1[1] = {unb};
+  block_sum_multi<1, float>(s1, sh);
+  o[0] = s1[0];
+  const float mw = warp_max(mlog);
+  if ((threadIdx.x & 31) == 0) sh[64 + (threadIdx.x >> 5)] = mw;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mm = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, sh[64 + w]);
+    o[1] = mm;
+  }
+  __syncthreads();
+}
+
+// Fold the scalings of the pair t into the potentials (this block's rows and
+// columns) and reset them to 1.
+__device__ __forceinline__ void fold_scalings(const LogArgs& A, int t) {
+  float* u = A.ubuf + (size_t)(t & 1) * A.n;
+  float* v = A.vbuf + (size_t)(t & 1) * A.m;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+    const float ui = u[i];
+    if (ui > 0.0f) {
+      const float al = A.alpha[i] + A.eps * logf(ui);
+      A.alpha[i] = al;
+      u[i] = 1.0f;
+      A.ahat[i] = A.uot ? A.a[i] * expf(-al * A.inv_lam) : A.a[i];
+    }
+  }
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < A.m; j += gridDim.x * blockDim.x) {
+    const float vj = v[j];
+    if (vj > 0.0f) {
+      const float be = A.beta[j] + A.eps * logf(vj);
+      A.beta[j] = be;
+      v[j] = 1.0f;
+      A.bhat[j] = A.uot ? A.b[j] * expf(-be * A.inv_lam) : A.b[j];
+    }
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ void rewrite_block(const LogArgs& A) {
+  const int lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  const int gw = blockIdx.x * nw + (threadIdx.x >> 5);
+  const int tw = gridDim.x * nw;
+  for (int i = gw; i < A.n; i += tw)
+    absorb_segment<V>(A.row_ptr[i], A.row_ptr[i + 1], A.col_idx, A.logval, A.alpha[i], A.beta, A.inv_eps,
+                      (V*)A.val, A.erow + i, lane);
+  for (int j = gw; j < A.m; j += tw)
+    absorb_segment<V>(A.col_ptr[j], A.col_ptr[j + 1], A.row_idx, A.logvalT, A.beta[j], A.alpha, A.inv_eps,
+                      (V*)A.valT, A.ecol + j, lane);
+}
+
+// Persistent stabilised iterations.  Partial slots: 0 residual, 1 unreachable
+// a-mass, 3 unreachable b-mass, 5 / 7 max |log u~| (by the parity of t: the
+// row phase of the next iteration writes it before any barrier while slower
+// blocks may still read this iteration's values), 6 max |log v~|.
+template <int LR, int LC, typename V, bool UOT>
+__global__ void __launch_bounds__(kIterThreads) k_iterate_log(LogArgs A, int iters, int row_only) {
+  __shared__ float sh[3 * 32 + 64];
+  __shared__ int absorb_now;
+  Ctrl* ctrl = A.ctrl;
+  if (ctrl->done) return;
+  int t = ctrl->t;
+  for (int k = 0; k < iters; ++k) {
+    float r3[3];
+    log_row_phase<LR, V, UOT>(A, t, r3, sh);
+    if (threadIdx.x == 0) {
+      A.part[0 * (size_t)A.nblk + blockIdx.x] = r3[0];
+      A.part[1 * (size_t)A.nblk + blockIdx.x] = r3[1];
+      A.part[(size_t)(5 + 2 * (t & 1)) * A.nblk + blockIdx.x] = r3[2];
+    }
+    if (!grid_barrier(ctrl)) return;
+    if (blockIdx.x == 0) {
+      if (threadIdx.x < 32) {
+        float s0 = 0.f, s1 = 0.f;
+        for (int b = threadIdx.x; b < A.nblk; b += 32) {
+          s0 += (float)__ldcg(A.part + b);
+          s1 += (float)__ldcg(A.part + (size_t)A.nblk + b);
+        }
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+        if (threadIdx.x == 0) {
+          const double res = (double)s0, unr = (double)s1;
+          ctrl->last_residual = res;
+          ctrl->last_unreach_a = unr;
+          if (!ctrl->done) {
+            const int numeric = !isfinite(res);
+            if (numeric || (t >= 1 && res <= A.tol)) {
+              ctrl->iters = t; ctrl->residual = res; ctrl->unreach_a = unr;
+              if (numeric) ctrl->status = SPS_ERR_NUMERIC;
+              __threadfence();
+              ctrl->done = 1;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (row_only) return;
+    float c2[2];
+    log_col_phase<LC, V, UOT>(A, t, c2, sh);
+    if (threadIdx.x == 0) {
+      A.part[3 * (size_t)A.nblk + blockIdx.x] = c2[0];
+      A.part[6 * (size_t)A.nblk + blockIdx.x] = c2[1];
+    }
+    if (!grid_barrier(ctrl)) return;
+    if (*(volatile int*)&ctrl->done) return;
+    // every block takes the same absorption decision from the same partials
+    if (threadIdx.x < 32) {
+      float mu = 0.f, mv = 0.f, ub = 0.f;
+      for (int b = threadIdx.x; b < A.nblk; b += 32) {
+        mu = fmaxf(mu, (float)__ldcg(A.part + (size_t)(5 + 2 * (t & 1)) * A.nblk + b));
+        mv = fmaxf(mv, (float)__ldcg(A.part + 6 * (size_t)A.nblk + b));
+        if (blockIdx.x == 0) ub += (float)__ldcg(A.part + 3 * (size_t)A.nblk + b);
+      }
+      mu = warp_max(mu);
+      mv = warp_max(mv);
+      ub = warp_sum(ub);
+      if (threadIdx.x == 0) {
+        absorb_now = (fmaxf(mu, mv) > A.tau) ? 1 : 0;
+        if (blockIdx.x == 0) {
+          ctrl->unreach_b = (double)ub;
+          ctrl->t = t + 1;
+          ctrl->max_logu = mu;
+          ctrl->max_logv = mv;
+        }
+      }
+    }
+    __syncthreads();
+    if (absorb_now) {
+      fold_scalings(A, t + 1);
+      if (!grid_barrier(ctrl)) return;
+      rewrite_block<V>(A);
+      if (!grid_barrier(ctrl)) return;
+      if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->n_absorb += 1;
+    }
+    ++t;
+  }
+}
+
+template <int LR, int LC, typename V, bool UOT>
+bool coop_log(LogArgs A, int iters, int row_only, cudaStream_t st) {
+  auto fn = k_iterate_log<LR, LC, V, UOT>;
+  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kIterThreads, 0) != cudaSuccess || per_sm < 1) return false;
+  A.nblk = std::min(A.nblk, nsm * per_sm);
+  void* args[] = {(void*)&A, (void*)&iters, (void*)&row_only};
+  if (cudaLaunchCooperativeKernel((const void*)fn, dim3(A.nblk), dim3(kIterThreads), args, 0, st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+template <int LR, typename V, bool UOT>
+bool coop_log_lc(const LogArgs& A, int lc, int iters, int row_only, cudaStream_t st) {
+  if (lc >= 32) return coop_log<LR, 32, V, UOT>(A, iters, row_only, st);
+  if (lc >= 16) return coop_log<LR, 16, V, UOT>(A, iters, row_only, st);
+  return coop_log<LR, 8, V, UOT>(A, iters, row_only, st);
+}
+
+template <typename V, bool UOT>
+bool coop_log_dispatch(const LogArgs& A, int lr, int lc, int iters, int row_only, cudaStream_t st) {
+  if (lr >= 32) return coop_log_lc<32, V, UOT>(A, lc, iters, row_only, st);
+  if (lr >= 16) return coop_log_lc<16, V, UOT>(A, lc, iters, row_only, st);
+  return coop_log_lc<8, V, UOT>(A, lc, iters, row_only, st);
+}
+
+LogArgs make_log_args(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic) {
+  LogArgs A;
+  A.n = pd.n; A.m = pd.m;
+  A.row_ptr = at<int>(ws, L.row_ptr); A.col_idx = at<int>(ws, L.col_idx);
+  A.col_ptr = at<int>(ws, L.col_ptr); A.row_idx = at<int>(ws, L.row_idx);
+  A.val = ws + L.val; A.valT = ws + L.valT;
+  A.logval = at<float>(ws, L.logval); A.logvalT = at<float>(ws, L.logvalT);
+  A.ubuf = at<float>(ws, L.u); A.vbuf = at<float>(ws, L.v);
+  A.alpha = at<float>(ws, L.alpha); A.beta = at<float>(ws, L.beta);
+  A.ahat = at<float>(ws, L.ahat); A.bhat = at<float>(ws, L.bhat);
+  A.erow = at<float>(ws, L.erow); A.ecol = at<float>(ws, L.ecol);
+  A.a = at<float>(ws, L.a_it); A.b = at<float>(ws, L.b_it);
+  A.eps = (float)ic.eps; A.inv_eps = (float)(1.0 / ic.eps);
+  A.lam = ic.uot ? (float)(ic.phi * ic.eps / (1.0 - ic.phi)) : 0.0f;
+  A.inv_lam = ic.uot ? (float)((1.0 - ic.phi) / (ic.phi * ic.eps)) : 0.0f;
+  A.phi = (float)ic.phi; A.inv_phi = (float)(1.0 / ic.phi); A.tol = (float)ic.tol; A.tau = (float)ic.tau;
+  A.uot = ic.uot;
+  A.ctrl = at<Ctrl>(ws, L.ctrl); A.part = at<double>(ws, L.part); A.nblk = L.nblk_rows;
+  return A;
+}
+
+template <typename V>
+void log_iterate_v(const LogArgs& A, const IterCfg& ic, int iters, int row_only, cudaStream_t st, bool* ok) {
+  *ok = ic.uot ? coop_log_dispatch<V, true>(A, ic.lpr_rows, ic.lpr_cols, iters, row_only, st)
+               : coop_log_dispatch<V, false>(A, ic.lpr_rows, ic.lpr_cols, iters, row_only, st);
+}
+
+// ----------------------------------------------------------------------------
+// Objective over the support with T~_ij = exp(logK~_ij + (A_i + B_j)/eps),
+// A = alpha + eps log u~, B = beta + eps log v~ of the returned pair.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double kl_term_d(double x, double y) {
+  if (x == 0.0) return y;
+  if (y == 0.0) return __longlong_as_double(0x7ff0000000000000LL);
+  return x * log(x / y) - x + y;
+}
+
+__global__ void k_log_potentials(LogArgs A, float* al_out, float* be_out) {
+  const Ctrl* ctrl = A.ctrl;
+  const int it = ctrl->done ? ctrl->iters : ctrl->t;
+  const float* u = A.ubuf + (size_t)(it & 1) * A.n;
+  const float* v = A.vbuf + (size_t)(it & 1) * A.m;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+  for (int i = tid; i < A.n; i += st) al_out[i] = u[i] > 0.0f ? A.alpha[i] + A.eps * logf(u[i]) : neg_inf();
+  for (int j = tid; j < A.m; j += st) be_out[j] = v[j] > 0.0f ? A.beta[j] + A.eps * logf(v[j]) : neg_inf();
+}
+
+template <bool UOT>
+__global__ void __launch_bounds__(kT) k_log_obj_rows(ProbDev pd, const SketchScalars* __restrict__ scp, LogArgs A,
+                                                     const float* __restrict__ rowf, const float* __restrict__ colf,
+                                                     const float* Apot, const float* Bpot, double* part, int nblk) {
+  __shared__ double sh[32];
+  const SketchScalars sc = *scp;
+  const int lane = threadIdx.x & 31;
+  double tr = 0.0, ne = 0.0, lp = 0.0, ms = 0.0, kla = 0.0;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < pd.n; i += (gridDim.x * blockDim.x) >> 5) {
+    const float Ai = Apot[i];
+    float rtr = 0.f, rne = 0.f, rlp = 0.f, rs = 0.f;
+    if (Ai != neg_inf()) {
+      const float ri = rowf[i];
+      for (int k = A.row_ptr[i] + lane; k < A.row_ptr[i + 1]; k += 32) {
+        const int j = A.col_idx[k];
+        const float Bj = Bpot[j];
+        if (Bj == neg_inf()) continue;
+        const float z = A.logval[k] + (Ai + Bj) * A.inv_eps;   // log T~_ij
+        const float T = expf(z);
+        if (!(T > 0.0f)) continue;
+        float D = 0.0f;
+        const float p = pstar_raw<UOT>(pd, sc, ri, colf, i, j, &D);
+        const float ps = p < 1.0f ? p : 1.0f;
+        const float C = __fdiv_rn(UOT ? D : raw32(pd.cv, i, j), sc.dn32);
+        rtr += T * C;
+        rne += T * (z - 1.0f);
+        rlp += T * logf(ps);
+        rs += T;
+      }
+    }
+    rtr = warp_sum(rtr); rne = warp_sum(rne); rlp = warp_sum(rlp); rs = warp_sum(rs);
+    if (lane == 0) {
+      tr += rtr; ne += rne; lp += rlp; ms += rs;
+      kla += kl_term_d((double)rs, (double)A.a[i]);
+    }
+  }
+  const double vals[5] = {tr, ne, lp, ms, kla};
+  for (int p = 0; p < 5; ++p) {
+    const double s = block_sum_d(vals[p], sh);
+    if (threadIdx.x == 0) part[(size_t)p * nblk + blockIdx.x] = s;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_log_obj_cols(LogArgs A, const float* Apot, const float* Bpot, double* part,
+                                                     int nblk) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31;
+  double klb = 0.0;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < A.m; j += (gridDim.x * blockDim.x) >> 5) {
+    const float Bj = Bpot[j];
+    float cs = 0.f;
+    if (Bj != neg_inf())
+      for (int k = A.col_ptr[j] + lane; k < A.col_ptr[j + 1]; k += 32) {
+        const float Ai = Apot[A.row_idx[k]];
+        if (Ai != neg_inf()) cs += expf(A.logvalT[k] + (Ai + Bj) * A.inv_eps);
+      }
+    cs = warp_sum(cs);
+    if (lane == 0) klb += kl_term_d((double)cs, (double)A.b[j]);
+  }
+  const double s = block_sum_d(klb, sh);
+  if (threadIdx.x == 0) part[5 * (size_t)nblk + blockIdx.x] = s;
+}
+
+__global__ void k_log_obj_final(const double* part, int nblk, DevResult* out, const Ctrl* ctrl) {
+  __shared__ double sh[32];
+  double r[6];
+  for (int p = 0; p < 6; ++p) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(size_t)p * nblk + b];
+    s = block_sum_d(s, sh);
+    __syncthreads();
+    r[p] = s;
+  }
+  if (threadIdx.x == 0) {
+    out->transport = r[0]; out->neg_entropy = r[1]; out->logp = r[2]; out->mass = r[3];
+    out->kl_a = r[4]; out->kl_b = r[5];
+    out->residual = ctrl->done ? ctrl->residual : ctrl->last_residual;
+    out->unreach_a = ctrl->done ? ctrl->unreach_a : ctrl->last_unreach_a;
+    out->unreach_b = ctrl->unreach_b;
+  }
+}
+
+int grid1(int64_t items, int per_block) {
+  int64_t g = (items + per_block - 1) / per_block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+template <typename V>
+void first_iteration_v(const LogArgs& A, const IterCfg& ic, const void* al0, const void* be0, cudaStream_t st) {
+  k_log_init<float><<<grid1(std::max(A.n, A.m), kT), kT, 0, st>>>(A.n, A.m, A.alpha, A.beta, (const float*)al0,
+                                                                   (const float*)be0, A.ctrl);
+  k_lse_half<<<grid1((int64_t)A.n * 32, kT), kT, 0, st>>>(A.n, A.row_ptr, A.col_idx, A.logval, A.beta, A.a,
+                                                         A.alpha, A.eps, A.phi);
+  k_lse_half<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.col_ptr, A.row_idx, A.logvalT, A.alpha, A.b,
+                                                         A.beta, A.eps, A.phi);
+  k_absorb_all<V><<<grid1((int64_t)std::max(A.n, A.m) * 32, kT), kT, 0, st>>>(A, 1);
+  (void)ic;
+}
+
+}  // namespace
+
+sps_status launch_log_first_iteration(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                      const void* init_alpha, const void* init_beta, cudaStream_t st) {
+  const LogArgs A = make_log_args(pd, L, ws, ic);
+  switch (ic.kd) {
+    case SPS_BF16: first_iteration_v<__nv_bfloat16>(A, ic, init_alpha, init_beta, st); break;
+    case SPS_F16: first_iteration_v<__half>(A, ic, init_alpha, init_beta, st); break;
+    default: first_iteration_v<float>(A, ic, init_alpha, init_beta, st); break;
+  }
+  add_launches(4);
+  return cuda_fail(cudaGetLastError(), "log-domain first iteration");
+}
+
+static sps_status log_coop(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, int iters, int row_only,
+                           cudaStream_t st) {
+  const LogArgs A = make_log_args(pd, L, ws, ic);
+  bool ok = false;
+  switch (ic.kd) {
+    case SPS_BF16: log_iterate_v<__nv_bfloat16>(A, ic, iters, row_only, st, &ok); break;
+    case SPS_F16: log_iterate_v<__half>(A, ic, iters, row_only, st, &ok); break;
+    default: log_iterate_v<float>(A, ic, iters, row_only, st, &ok); break;
+  }
+  if (!ok) {
+    set_error("the device refused the cooperative launch of the stabilised iterations");
+    return SPS_ERR_CUDA;
+  }
+  add_launches(1);
+  return cuda_fail(cudaGetLastError(), "log-domain iterations");
+}
+
+sps_status launch_log_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, int iters,
+                                 cudaStream_t st) {
+  return log_coop(pd, L, ws, ic, iters, 0, st);
+}
+
+sps_status launch_log_row_only(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, cudaStream_t st) {
+  return log_coop(pd, L, ws, ic, 1, 1, st);
+}
+
+sps_status launch_log_objective(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, void* alpha_out,
+                                void* beta_out, cudaStream_t st) {
+  const LogArgs A = make_log_args(pd, L, ws, ic);
+  float* Ap = at<float>(ws, L.pot_a);
+  float* Bp = at<float>(ws, L.pot_b);
+  k_log_potentials<<<grid1(std::max(A.n, A.m), kT), kT, 0, st>>>(A, Ap, Bp);
+  double* part = at<double>(ws, L.part);
+  const int nb = L.nblk_rows;
+  const SketchScalars* sc = at<SketchScalars>(ws, L.scal);
+  if (ic.uot)
+    k_log_obj_rows<true><<<nb, kT, 0, st>>>(pd, sc, A, at<float>(ws, L.rowf), at<float>(ws, L.colf), Ap, Bp, part, nb);
+  else
+    k_log_obj_rows<false><<<nb, kT, 0, st>>>(pd, sc, A, at<float>(ws, L.rowf), at<float>(ws, L.colf), Ap, Bp, part, nb);
+  k_log_obj_cols<<<nb, kT, 0, st>>>(A, Ap, Bp, part, nb);
+  k_log_obj_final<<<1, kT, 0, st>>>(part, nb, at<DevResult>(ws, L.res), A.ctrl);
+  int launches = 4;
+  if (alpha_out && beta_out) {
+    cudaMemcpyAsync(alpha_out, Ap, sizeof(float) * (size_t)pd.n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(beta_out, Bp, sizeof(float) * (size_t)pd.m, cudaMemcpyDeviceToDevice, st);
+  }
+  add_launches(launches);
+  return cuda_fail(cudaGetLastError(), "log-domain objective");
+}
+
+}  // namespace sps

@@ -304,7 +304,7 @@ __device__ __forceinline__ V gather_val(const V* val, int src, long long nnz, Ct
 template <int Q, typename V>
 __device__ __forceinline__ void rank_place(const int* sm, int L, int s0, int lane, const int* tmp_src,
                                            const V* val, int* row_idx, int* csr_pos, V* valT,
-                                           long long nnz, Ctrl* ctrl) {
+                                           long long nnz, Ctrl* ctrl, const float* lv, float* lvT) {
   int r[Q], src[Q], rank[Q];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
@@ -325,6 +325,7 @@ __device__ __forceinline__ void rank_place(const int* sm, int L, int s0, int lan
       row_idx[s0 + rank[k]] = r[k];
       csr_pos[s0 + rank[k]] = src[k];
       valT[s0 + rank[k]] = gather_val(val, src[k], nnz, ctrl);
+      if (lv) lvT[s0 + rank[k]] = gather_val(lv, src[k], nnz, ctrl);
     }
   }
 }
@@ -334,7 +335,8 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_csc_sort(int m, const int* 
                                                               const int* __restrict__ tmp_row,
                                                               const int* __restrict__ tmp_src,
                                                               const V* __restrict__ val, int* row_idx,
-                                                              int* csr_pos, V* valT, Ctrl* ctrl) {
+                                                              int* csr_pos, V* valT, Ctrl* ctrl,
+                                                              const float* lv, float* lvT) {
   if (ctrl->status != SPS_OK || ctrl->sketch_fault) return;
   const long long nnz = ctrl->nnz;
   __shared__ int sm_all[kSortWarps][kSortCap];
@@ -351,9 +353,9 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_csc_sort(int m, const int* 
       __syncwarp();
       for (int e = lane; e < L; e += 32) sm[e] = tmp_row[s0 + e];
       __syncwarp();
-      if (L <= 64) rank_place<2>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl);
-      else if (L <= 256) rank_place<8>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl);
-      else rank_place<32>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl);
+      if (L <= 64) rank_place<2>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl, lv, lvT);
+      else if (L <= 256) rank_place<8>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl, lv, lvT);
+      else rank_place<32>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl, lv, lvT);
     } else {
       for (int e = lane; e < L; e += 32) {
         const int re = tmp_row[s0 + e];
@@ -363,6 +365,7 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_csc_sort(int m, const int* 
         row_idx[s0 + rank] = re;
         csr_pos[s0 + rank] = src;
         valT[s0 + rank] = gather_val(val, src, nnz, ctrl);
+        if (lv) lvT[s0 + rank] = gather_val(lv, src, nnz, ctrl);
       }
     }
   }
@@ -450,7 +453,9 @@ static void csc_sort(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t 
   k_csc_sort<V><<<gs, 32 * kSortWarps, 0, st>>>(pd.m, at<int>(ws, L.col_ptr), at<int>(ws, L.tmp_row),
                                                 at<int>(ws, L.tmp_src), at<V>(ws, L.val),
                                                 at<int>(ws, L.row_idx), at<int>(ws, L.csr_pos),
-                                                at<V>(ws, L.valT), at<Ctrl>(ws, L.ctrl));
+                                                at<V>(ws, L.valT), at<Ctrl>(ws, L.ctrl),
+                                                L.logval ? at<float>(ws, L.logval) : nullptr,
+                                                L.logvalT ? at<float>(ws, L.logvalT) : nullptr);
 }
 
 sps_status launch_sample(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st) {

@@ -42,6 +42,7 @@ struct SweepArgs {
   void* val;
   int* col_cur;
   const int* col_end;   // col_ptr + 1: end of every column segment
+  float* logval;        // log-domain: log K~ of every kept element (or null)
   int* tmp_row;
   int* tmp_src;
   Ctrl* ctrl;
@@ -199,6 +200,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
                   if (pos >= pend[r]) { A.ctrl->sketch_fault = 1; ++pos; continue; }
                   A.col_idx[pos] = jj;
                   val[pos] = from_d<V>(ValMath<V>::value(pd, sc, i, jj, Dd, ps));
+                  if (A.logval) {
+                    // log K~ = -C/eps - log p*, C from the FP64 distance of the binary32 points
+                    const double C64 = raw64(pd.cv, i, jj) / sc.dn64;
+                    A.logval[pos] = (float)(-C64 / pd.eps - (double)logf(ps));
+                  }
                   const int slot = atomicAdd(&A.col_cur[jj], 1);
                   if (slot < A.col_end[jj]) {
                     A.tmp_row[slot] = i;
@@ -315,6 +321,7 @@ static void fill_v(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st
   A.val = ws + L.val;
   A.col_cur = at<int>(ws, L.col_cur);
   A.col_end = at<int>(ws, L.col_ptr) + 1;
+  A.logval = L.logval ? at<float>(ws, L.logval) : nullptr;
   A.tmp_row = at<int>(ws, L.tmp_row);
   A.tmp_src = at<int>(ws, L.tmp_src);
   const SweepGeo g = sweep_geometry(pd.n, pd.m);

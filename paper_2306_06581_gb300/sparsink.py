@@ -195,27 +195,31 @@ def _solve(fn_name, prob: Problem, prm: Params, device, op, workspace=None, rais
 
 def spar_sink_ot(a, b, x=None, y=None, C_=None, *, eps, s, tol=1e-6, max_iter=1000, dtype="f32", kdtype=None,
                  seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL,
-                 check_every=0, init_alpha=None, init_beta=None, workspace=None, device=None, raise_on_error=True):
+                 check_every=0, init_alpha=None, init_beta=None, log_domain=0, absorb_tau=0.0, workspace=None,
+                 device=None, raise_on_error=True):
     """Alg. 3: importance-sparsified Sinkhorn for balanced OT."""
     M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
     dev = M.keep[0].device
     kd = kdtype or dtype
     it = torch.float64 if kd == "f64" else torch.float32
     ia, ib = _dev(init_alpha, it, dev), _dev(init_beta, it, dev)
-    prm = make_params(eps, math.inf, s, tol, max_iter, check_every, stop_rule, seed, problem_id, kd, 0, 0.0, ia, ib)
+    prm = make_params(eps, math.inf, s, tol, max_iter, check_every, stop_rule, seed, problem_id, kd, log_domain,
+                      absorb_tau, ia, ib)
     return _solve("spar_sink_ot", M.prob, prm, dev, OP_SPAR_SINK, workspace, raise_on_error)
 
 
 def spar_sink_uot(a, b, x=None, y=None, C_=None, *, eps, lam, s, tol=1e-6, max_iter=1000, dtype="f32", kdtype=None,
                   seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL,
-                  check_every=0, init_alpha=None, init_beta=None, workspace=None, device=None, raise_on_error=True):
+                  check_every=0, init_alpha=None, init_beta=None, log_domain=0, absorb_tau=0.0, workspace=None,
+                  device=None, raise_on_error=True):
     """Alg. 4: importance-sparsified Sinkhorn for UOT with KL penalty lam."""
     M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
     dev = M.keep[0].device
     kd = kdtype or dtype
     it = torch.float64 if kd == "f64" else torch.float32
     ia, ib = _dev(init_alpha, it, dev), _dev(init_beta, it, dev)
-    prm = make_params(eps, lam, s, tol, max_iter, check_every, stop_rule, seed, problem_id, kd, 0, 0.0, ia, ib)
+    prm = make_params(eps, lam, s, tol, max_iter, check_every, stop_rule, seed, problem_id, kd, log_domain,
+                      absorb_tau, ia, ib)
     return _solve("spar_sink_uot", M.prob, prm, dev, OP_SPAR_SINK, workspace, raise_on_error)
 
 
