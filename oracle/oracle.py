@@ -348,16 +348,28 @@ def spar_sink(prob: OracleProblem, tol=1e-6, max_iter=1000, log_domain=False, st
             "terms": terms, "obj": r1, "obj_sparse": r2}
 
 
-def dense_sinkhorn(prob: OracleProblem, tol=1e-6, max_iter=1000, stop_rule=STOP_RESIDUAL):
-    """Alg. 1 / Alg. 2 on the dense kernel, with the same objective terms."""
+def dense_sinkhorn(prob: OracleProblem, tol=1e-6, max_iter=1000, stop_rule=STOP_RESIDUAL, log_domain=False):
+    """Alg. 1 / Alg. 2 on the dense kernel, with the same objective terms.
+    log_domain=True runs the log-sum-exp iterations over the full support
+    (log K = -C/eps), for the small eps at which K underflows."""
     K, Cn = prob.dense_kernel()
-    u, v, info = sinkhorn_dense(K, prob.a, prob.b, prob.eps, prob.lam, tol, max_iter, stop_rule)
     n, m = K.shape
+    row_ptr = (np.arange(n + 1) * m).astype(np.int32)
+    col_idx = np.tile(np.arange(m, dtype=np.int32), n)
+    if log_domain:
+        lk = -Cn / prob.eps
+        full = {"n": n, "m": m, "row_ptr": row_ptr, "col_idx": col_idx, "logval": lk.ravel(),
+                "col_ptr": (np.arange(m + 1) * n).astype(np.int32),
+                "row_idx": np.tile(np.arange(n, dtype=np.int32), m), "logvalT": lk.T.ravel()}
+        al, be, info = sinkhorn_log_sparse(full, prob.a, prob.b, prob.eps, prob.lam, tol, max_iter, stop_rule)
+        logT = ((al[:, None] + be[None, :]) / prob.eps + lk).ravel()
+        terms = objective_terms(row_ptr, col_idx, logT, Cn.ravel(), np.ones(n * m, np.float32), prob.a, prob.b)
+        r1, _ = _objective(terms, prob.eps, prob.lam)
+        return {"alpha": al, "beta": be, "info": info, "terms": terms, "obj": r1, "K": K, "C": Cn}
+    u, v, info = sinkhorn_dense(K, prob.a, prob.b, prob.eps, prob.lam, tol, max_iter, stop_rule)
     logu, logv = _log_or_neginf(u), _log_or_neginf(v)
     with np.errstate(divide="ignore"):
         logT = (logu[:, None] + np.log(K) + logv[None, :]).ravel()
-    row_ptr = (np.arange(n + 1) * m).astype(np.int32)
-    col_idx = np.tile(np.arange(m, dtype=np.int32), n)
     terms = objective_terms(row_ptr, col_idx, logT, Cn.ravel(), np.ones(n * m, np.float32),
                             prob.a, prob.b)
     r1, _ = _objective(terms, prob.eps, prob.lam)

@@ -101,8 +101,10 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
   if (op == SPS_OP_DENSE) {
     nb = (int)std::min<int64_t>(152 * 8, std::max<int64_t>(1, ((int64_t)std::max(n, m) + 255) / 256));
     part_blocks = std::max(nb, dense_pass_blocks(n, m));
-    L->qpart = take(dense_qpart_elems(n, m) * ib);
-    L->rpart = take(dense_rpart_elems(n, m) * ib);
+    // log_domain: a running maximum and a scaled sum per element
+    const size_t lf = Q->log_domain ? 2 : 1;
+    L->qpart = take(dense_qpart_elems(n, m) * ib * lf);
+    L->rpart = take(dense_rpart_elems(n, m) * ib * lf);
   }
   if (op == SPS_OP_SPAR_SINK || op == SPS_OP_DENSE) {
     L->u = take((size_t)2 * n * ib);
@@ -147,7 +149,7 @@ static sps_status validate(const sps_problem* P, const sps_params* Q, int op) {
   if (!valid_dtype(Q->kdtype)) { set_error("bad kdtype"); return SPS_ERR_INVALID_ARG; }
   if (op == SPS_OP_DENSE && Q->kdtype != SPS_F64 && Q->kdtype != SPS_F32) { set_error("dense Sinkhorn iterates in F64 or F32"); return SPS_ERR_INVALID_ARG; }
   if (op == SPS_OP_DENSE && !P->C && P->d > 16) { set_error("dense Sinkhorn on points supports d <= 16 (d=%d)", P->d); return SPS_ERR_INVALID_ARG; }
-  if (Q->log_domain && op == SPS_OP_DENSE) { set_error("log_domain applies to the sparse solvers"); return SPS_ERR_INVALID_ARG; }
+  if (Q->log_domain && op == SPS_OP_DENSE && Q->kdtype != SPS_F32) { set_error("dense log_domain iterates in F32"); return SPS_ERR_INVALID_ARG; }
   if (Q->log_domain && Q->kdtype == SPS_F64) { set_error("log_domain stores K' in F32, BF16 or F16"); return SPS_ERR_INVALID_ARG; }
   if (Q->log_domain && Q->stop_rule != SPS_STOP_RESIDUAL) { set_error("log_domain stops on the residual rule"); return SPS_ERR_INVALID_ARG; }
   if (Q->log_domain && Q->absorb_tau < 0.0) { set_error("absorb_tau must be >= 0"); return SPS_ERR_INVALID_ARG; }
@@ -252,7 +254,9 @@ static thread_local int g_iters_enqueued = 0;
 static sps_status run_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, const sps_params* Q,
                                  IterFn full, RowFn row_only, cudaStream_t st, Ctrl* h) {
   int launched = 0;
-  if (ic.log_domain) {
+  if (ic.log_domain && ic.dense) {
+    SPS_TRY(launch_dense_lse_init(pd, L, ws, Q->init_alpha, Q->init_beta, st));
+  } else if (ic.log_domain) {
     // the first iteration runs exactly in the log domain and forms the pair (u^1, v^1)
     SPS_TRY(launch_log_first_iteration(pd, L, ws, ic, Q->init_alpha, Q->init_beta, st));
     launched = 1;
@@ -459,9 +463,17 @@ sps_status sinkhorn_dense(const sps_problem* prob, const sps_params* prm, void* 
   ic.max_iter = prm->max_iter;
   Ctrl h;
   ic.persistent = 0;
-  SPS_TRY(run_iterations(pd, L, ws, ic, prm, launch_dense_iterations, launch_dense_row_only, st, &h));
-  ev.rec(2, st);
-  SPS_TRY(launch_dense_objective(pd, L, ws, ic, alpha_out, beta_out, st));
+  ic.dense = 1;
+  ic.log_domain = prm->log_domain ? 1 : 0;
+  if (ic.log_domain) {
+    SPS_TRY(run_iterations(pd, L, ws, ic, prm, launch_dense_lse_iterations, launch_dense_lse_row_only, st, &h));
+    ev.rec(2, st);
+    SPS_TRY(launch_dense_lse_objective(pd, L, ws, ic, alpha_out, beta_out, st));
+  } else {
+    SPS_TRY(run_iterations(pd, L, ws, ic, prm, launch_dense_iterations, launch_dense_row_only, st, &h));
+    ev.rec(2, st);
+    SPS_TRY(launch_dense_objective(pd, L, ws, ic, alpha_out, beta_out, st));
+  }
   ev.rec(3, st);
   DevResult dr;
   SPS_TRY(cuda_fail(cudaMemcpyAsync(&dr, ws + L.res, sizeof(dr), cudaMemcpyDeviceToHost, st), "result read-back"));

@@ -14,23 +14,14 @@
 
 #include <algorithm>
 
+#include "sps_dense.cuh"
 #include "sps_internal.h"
 
 namespace sps {
 
 namespace {
 
-constexpr int kTI = 128;   // threads per block
-constexpr int kRPT = 2;    // rows per thread
-constexpr int kTJ = 128;   // columns per shared-memory tile
-
-struct DenseView {
-  const float* P32; const float* Q32;      // row / column points (binary32)
-  const double* P64; const double* Q64;    // FP64 points (FP64 problems)
-  const float* C32; const double* C64;     // dense raw cost, original orientation n x m
-  int transposed;                          // 1: pass rows are the original columns
-  int np, nq, d, m_orig;
-};
+using namespace dense;
 
 struct PassArgs {
   DenseView V;
@@ -55,12 +46,6 @@ template <typename T> __device__ __forceinline__ T gibbs(T D, T k2);
 // exp(-D / (dn eps)) = exp2(-D * k2), k2 = log2(e) / (dn eps)
 template <> __device__ __forceinline__ float gibbs<float>(float D, float k2) { return exp2f(-D * k2); }
 template <> __device__ __forceinline__ double gibbs<double>(double D, double k2) { return exp(-D * k2); }
-
-template <typename T>
-__device__ __forceinline__ T ldpt(const float* p32, const double* p64, int64_t off) {
-  if (sizeof(T) == 8) return (T)(p64 ? p64[off] : (double)p32[off]);
-  return (T)p32[off];
-}
 
 // mode 0: out[split][p] = sum_{q in range} K_pq w_q
 // mode 1: block partials of transport, neg_entropy, mass over the range
@@ -166,25 +151,6 @@ __global__ void __launch_bounds__(kTI) k_dense_pass(PassArgs A) {
       if (threadIdx.x == 0) A.part[(size_t)k * A.nblk_total + b] = s;
       __syncthreads();
     }
-  }
-}
-
-__device__ __forceinline__ bool last_block_d(unsigned int* counter) {
-  __shared__ bool am_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  return am_last;
-}
-
-__device__ void reduce_parts_d(const double* part, int nblk, int nparts, double* out, double* sh) {
-  for (int p = 0; p < nparts; ++p) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(part + (size_t)p * nblk + b);
-    s = block_sum_d(s, sh);
-    if (threadIdx.x == 0) out[p] = s;
-    __syncthreads();
   }
 }
 
@@ -335,34 +301,6 @@ __global__ void k_dense_potentials(int n, int m, const T* ubuf, const T* v, doub
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = tid; i < n; i += stride) al[i] = (T)(eps * log((double)u[i]));
   for (int64_t j = tid; j < m; j += stride) be[j] = (T)(eps * log((double)v[j]));
-}
-
-struct Geo {
-  dim3 grid;
-  int qchunk;
-  int nsplit;
-};
-
-Geo geometry(int np, int nq) {
-  const int gi = (np + kTI * kRPT - 1) / (kTI * kRPT);
-  int gs = std::max(1, (152 * 4 + gi - 1) / gi);
-  int qchunk = std::max(kTJ, (nq + gs - 1) / gs);
-  qchunk = ((qchunk + kTJ - 1) / kTJ) * kTJ;
-  gs = (nq + qchunk - 1) / qchunk;
-  return Geo{dim3(gi, gs), qchunk, gs};
-}
-
-DenseView view_rows(const ProbDev& pd) {
-  DenseView V;
-  V.P32 = pd.cv.x32; V.Q32 = pd.cv.y32; V.P64 = pd.cv.x64; V.Q64 = pd.cv.y64;
-  V.C32 = pd.cv.C32; V.C64 = pd.cv.C64; V.transposed = 0; V.np = pd.n; V.nq = pd.m; V.d = pd.d; V.m_orig = pd.m;
-  return V;
-}
-DenseView view_cols(const ProbDev& pd) {
-  DenseView V = view_rows(pd);
-  V.P32 = pd.cv.y32; V.Q32 = pd.cv.x32; V.P64 = pd.cv.y64; V.Q64 = pd.cv.x64;
-  V.transposed = 1; V.np = pd.m; V.nq = pd.n;
-  return V;
 }
 
 PassArgs base_args(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic) {

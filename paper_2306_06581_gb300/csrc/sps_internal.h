@@ -136,6 +136,7 @@ struct IterCfg {
   int persistent = 1;  // run chunks of iterations in one cooperative launch
   int log_domain = 0;  // stabilised iterations with absorption
   double tau = 12.0;   // absorption threshold on max |log u~|, |log v~|
+  int dense = 0;       // dense Sinkhorn (log_domain: log-sum-exp form)
 };
 sps_status launch_iter_init(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                             const void* init_alpha, const void* init_beta, cudaStream_t st);
@@ -163,6 +164,15 @@ size_t dense_rpart_elems(int n, int m);
 int dense_pass_blocks(int n, int m);
 sps_status launch_dense_objective(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                                   void* alpha_out, void* beta_out, cudaStream_t st);
+// Dense log-sum-exp form (sps_dense_lse.cu)
+sps_status launch_dense_lse_init(const ProbDev& pd, const Layout& L, char* ws, const void* init_alpha,
+                                 const void* init_beta, cudaStream_t st);
+sps_status launch_dense_lse_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, int iters,
+                                       cudaStream_t st);
+sps_status launch_dense_lse_row_only(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                     cudaStream_t st);
+sps_status launch_dense_lse_objective(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
+                                      void* alpha_out, void* beta_out, cudaStream_t st);
 
 template <typename T> T* at(char* ws, size_t off) { return reinterpret_cast<T*>(ws + off); }
 

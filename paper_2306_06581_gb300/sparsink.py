@@ -224,12 +224,15 @@ def spar_sink_uot(a, b, x=None, y=None, C_=None, *, eps, lam, s, tol=1e-6, max_i
 
 
 def sinkhorn_dense(a, b, x=None, y=None, C_=None, *, eps, lam=math.inf, tol=1e-6, max_iter=1000, dtype="f32",
-                   cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL, check_every=0, workspace=None,
-                   device=None, raise_on_error=True):
-    """Alg. 1 (lam = inf) / Alg. 2 with K = exp(-C/eps) recomputed on the fly."""
+                   cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL, check_every=0, log_domain=0,
+                   init_alpha=None, init_beta=None, workspace=None, device=None, raise_on_error=True):
+    """Alg. 1 (lam = inf) / Alg. 2 with K = exp(-C/eps) recomputed on the fly;
+    log_domain=1 iterates the potentials in log-sum-exp form (binary32)."""
     M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
     dev = M.keep[0].device
-    prm = make_params(eps, lam, 1.0, tol, max_iter, check_every, stop_rule, 0, 0, dtype)
+    it = torch.float64 if dtype == "f64" else torch.float32
+    ia, ib = _dev(init_alpha, it, dev), _dev(init_beta, it, dev)
+    prm = make_params(eps, lam, 1.0, tol, max_iter, check_every, stop_rule, 0, 0, dtype, log_domain, 0.0, ia, ib)
     return _solve("sinkhorn_dense", M.prob, prm, dev, OP_DENSE, workspace, raise_on_error)
 
 

@@ -255,3 +255,37 @@ def test_empty_row_is_unreachable_not_nan(orc):
     assert empty_c[3] and r["info"]["status"] == 0
     assert np.isneginf(r["beta"][empty_c]).all() and np.isfinite(r["obj"])
     assert abs(r["info"]["unreach_b"] - P.b[empty_c].sum()) < 1e-15
+
+
+@pytest.mark.parametrize("lam", [math.inf, 1.0])
+def test_dense_log_domain_equals_plain(orc, lam):
+    w = inputs.small_problem(n=60, m=50, d=3, seed=17, eps=0.1, mass_b=1.0 if math.isinf(lam) else 1.5)
+    P = orc.OracleProblem(w.a, w.b, 0.1, 1.0, lam, x=w.x, y=w.y)
+    pl = orc.dense_sinkhorn(P, tol=1e-11, max_iter=20000)
+    lg = orc.dense_sinkhorn(P, tol=1e-11, max_iter=20000, log_domain=True)
+    assert pl["info"]["iters"] == lg["info"]["iters"]
+    assert np.abs(pl["alpha"] - lg["alpha"]).max() < 1e-12
+    assert abs(pl["obj"] - lg["obj"]) < 1e-12
+
+
+def test_dense_log_domain_small_eps_lp_sandwich(orc):
+    # eps = 1e-3 on a cost normalised to [0, 1]: exp(-C/eps) underflows binary64
+    # for C > 0.745, so only the log form is usable.  Uniform weights, n = 7:
+    # OT is the best permutation (Birkhoff), and OT - eps(1 + 2 log n) <= OT_eps <= OT - eps.
+    rng = np.random.default_rng(21)
+    n = 7
+    # a permuted, slightly moved copy of x: one best matching with a clear margin
+    x = rng.uniform(0, 1, (n, 2)); y = x[rng.permutation(n)] + 0.02 * rng.standard_normal((n, 2))
+    a = np.full(n, 1.0 / n); b = np.full(n, 1.0 / n)
+    C = ((x[:, None] - y[None]) ** 2).sum(-1)
+    C = C / C.max()
+    assert (np.exp(-C / 1e-3) == 0).any()
+    ot = min(sum(C[i, p[i]] for i in range(n)) / n for p in itertools.permutations(range(n)))
+    eps = 1e-3
+    P = orc.OracleProblem(a, b, eps, 1.0, math.inf, C_=C, cost_norm=0)
+    r = orc.dense_sinkhorn(P, tol=1e-12, max_iter=500000, log_domain=True)
+    assert r["info"]["status"] == 0
+    assert ot - eps * (1 + 2 * math.log(n)) - 1e-9 <= r["obj"] <= ot - eps + 1e-9
+    assert abs(r["terms"]["transport"] - ot) < 5e-3
+    T = np.exp((r["alpha"][:, None] + r["beta"][None]) / eps - C / eps)
+    assert np.abs(T.sum(1) - a).sum() < 1e-11 and np.abs(T.sum(0) - b).sum() < 1e-11
