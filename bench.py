@@ -48,20 +48,36 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+WORKLOADS = ("uot_n20000", "ot_n1000", "ot_n200000", "ot_n1000000")
+
+
 def _workload(name):
     from paper_2306_06581_gb300 import inputs
     if name == "uot_n20000":
         return inputs.uot_n20000()
     if name == "ot_n1000":
         return inputs.ot_n1000()
+    if name == "ot_n200000":
+        return inputs.ot_n200000()
+    if name == "ot_n1000000":
+        return inputs.ot_n1000000()
     raise SystemExit(f"unknown workload {name}")
 
 
-def _config(w, flush):
+def _log_domain(w):
+    """The stabilised iterations run for eps < 0.05 (K~ leaves the binary32 range)."""
+    return 1 if w.eps < 0.05 else 0
+
+
+def _problem_dtype(w):
+    return "f64" if w.dtype == "f64" else "f32"
+
+
+def _config(w, flush, kdtype=None):
     return {"workload": w.name, "n": w.n, "m": w.m, "d": w.d, "eps": w.eps,
             "lambda": None if math.isinf(w.lam) else w.lam, "s": round(w.s, 1), "tol": TOL,
-            "value_dtype": w.dtype, "cost": "squared Euclidean / max", "l2": flush,
-            "parallelism": "replicas (one independent solve per GPU)"}
+            "value_dtype": kdtype or w.dtype, "log_domain": _log_domain(w), "cost": "squared Euclidean / max",
+            "l2": flush, "parallelism": "replicas (one independent solve per GPU)"}
 
 
 class ClockSampler:
@@ -106,15 +122,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _spmv_bytes(res, n, m):
+_VB = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
+
+
+def _spmv_bytes(res, n, m, kdtype="f32", log_domain=0):
     """Algorithmic HBM bytes of one iteration (row pass + column pass): every
-    stored element once (int32 index + value), the pointer arrays, the marginal,
-    the old and new scaling vectors, and the gathered vector once."""
+    stored element once (int32 index + value), the pointer arrays, the per-row
+    vectors (plain: marginal, old and new scaling; stabilised: also the
+    absorbed marginal and the row exponent), and the gathered vector once."""
     nnz = res["nnz"]
-    vb = 4
-    row = nnz * (4 + vb) + 4 * (n + 1) + 4 * n * 3 + 4 * m
-    col = nnz * (4 + vb) + 4 * (m + 1) + 4 * m * 3 + 4 * n
+    vb = _VB[kdtype]
+    ib = 8 if kdtype == "f64" else 4
+    kr = 5 if log_domain else 3
+    kc = 4 if log_domain else 3
+    row = nnz * (4 + vb) + 4 * (n + 1) + ib * n * kr + ib * m
+    col = nnz * (4 + vb) + 4 * (m + 1) + ib * m * kc + ib * n
     return row, col
+
+
+def _golden(w):
+    """FP64 oracle result of the workload stored by tests/golden (None if absent)."""
+    p = os.path.join(ROOT, "tests", "golden", f"{w.name.split('_d')[0]}_oracle.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            g = json.load(f)
+        if g.get("workload") == w.name:
+            return g
+    return None
 
 
 def run_ours(args):
@@ -134,14 +168,23 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     w = _workload(args.workload)
     uot = not math.isinf(w.lam)
-    dt = torch.float64 if w.dtype == "f64" else torch.float32
+    pdt = _problem_dtype(w)
+    kd = args.kdtype or w.dtype
+    logd = _log_domain(w)
+    dt = torch.float64 if pdt == "f64" else torch.float32
     x = torch.tensor(w.x, dtype=dt, device=dev)
     y = torch.tensor(w.y, dtype=dt, device=dev)
     a = torch.tensor(w.a, dtype=dt, device=dev)
     b = torch.tensor(w.b, dtype=dt, device=dev)
-    kw = dict(eps=w.eps, s=w.s, tol=TOL, max_iter=20000, dtype=w.dtype, seed=w.seed, problem_id=rank)
-    solve = (lambda **extra: S.spar_sink_uot(a, b, x, y, lam=w.lam, **kw, **extra)) if uot else \
-        (lambda **extra: S.spar_sink_ot(a, b, x, y, **kw, **extra))
+    kw = dict(eps=w.eps, s=w.s, tol=TOL, max_iter=20000, dtype=pdt, seed=w.seed, problem_id=rank)
+
+    def solve(**extra):
+        k = dict(kw, kdtype=kd, log_domain=logd)
+        k.update(extra)
+        if uot:
+            return S.spar_sink_uot(k.pop("a", a), k.pop("b", b), k.pop("x", x), k.pop("y", y), lam=w.lam, **k)
+        return S.spar_sink_ot(k.pop("a", a), k.pop("b", b), k.pop("x", x), k.pop("y", y), **k)
+
     first = solve()
     ws = first["workspace"]
     flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -177,12 +220,8 @@ def run_ours(args):
     # Roofline of the SpMV half-iterations: a fixed-length run (tol = 0, one
     # chunk, no read-back inside) timed by the library's CUDA events.
     fixed_iters = 200
-    kw_fixed = dict(kw, tol=0.0, max_iter=fixed_iters, check_every=fixed_iters)
-    if uot:
-        rf = S.spar_sink_uot(a, b, x, y, lam=w.lam, **kw_fixed, workspace=ws)
-    else:
-        rf = S.spar_sink_ot(a, b, x, y, **kw_fixed, workspace=ws)
-    row_b, col_b = _spmv_bytes(rf, w.n, w.m)
+    rf = solve(tol=0.0, max_iter=fixed_iters, check_every=fixed_iters, workspace=ws)
+    row_b, col_b = _spmv_bytes(rf, w.n, w.m, kd, logd)
     per_iter_ms = rf["ms_iter"] / max(rf["iters_enqueued"], 1)
     peak, peak_kind = _peaks()
     achieved = (row_b + col_b) / (per_iter_ms * 1e-3) / 1e9
@@ -192,11 +231,40 @@ def run_ours(args):
         with open(tpath) as f:
             traffic = json.load(f).get("bytes_per_iteration")
 
-    # dense Sinkhorn on the same GPU, same tolerance
-    dense = S.sinkhorn_dense(a, b, x, y, eps=w.eps, lam=w.lam, tol=TOL, max_iter=20000, dtype=w.dtype)
-    dense = S.sinkhorn_dense(a, b, x, y, eps=w.eps, lam=w.lam, tol=TOL, max_iter=20000, dtype=w.dtype,
-                             workspace=dense["workspace"])
+    # dense Sinkhorn on the same GPU, same tolerance (log-sum-exp form for small
+    # eps); with --dense-cap the run stops after that many iterations and the
+    # time to tolerance is extrapolated at Spar-Sink's iteration count
+    cap = args.dense_cap if args.dense_cap > 0 else 20000
+    dkw = dict(eps=w.eps, lam=w.lam, tol=TOL, max_iter=cap, dtype=pdt, log_domain=logd, raise_on_error=False)
+    dense = S.sinkhorn_dense(a, b, x, y, **dkw)
+    dense = S.sinkhorn_dense(a, b, x, y, **dkw, workspace=dense["workspace"])
     dense_ms = dense["ms_sketch"] + dense["ms_iter"] + dense["ms_obj"]
+    dense_line = {"ms": round(dense_ms, 4), "iters": dense["iters"], "obj": dense["obj"],
+                  "residual": dense["residual"], "log_domain": logd}
+    if dense["status"] == 0:
+        dense_line["speedup_of_spar_sink"] = round(dense_ms / ms, 2)
+        dense_line["rel_obj_gap_sparse_value"] = abs(last["obj_sparse"] - dense["obj"]) / abs(dense["obj"])
+    else:
+        per = dense["ms_iter"] / max(dense["iters_enqueued"], 1)
+        est = dense["ms_sketch"] + per * last["iters"] + dense["ms_obj"]
+        dense_line.update({"capped_at_iters": cap, "ms_per_iteration": round(per, 4),
+                           "extrapolated_ms_at_spar_sink_iters": round(est, 1),
+                           "speedup_of_spar_sink_extrapolated": round(est / ms, 2)})
+
+    # storage precision forms of the stabilised path against the stored FP64 oracle value
+    precision = None
+    gold = _golden(w)
+    if logd and rank == 0:
+        precision = {}
+        for k2 in ("f32", "bf16", "f16"):
+            rr = solve(kdtype=k2)
+            rr = solve(kdtype=k2, workspace=rr["workspace"])
+            ent = {"ms": round(rr["ms_sketch"] + rr["ms_iter"] + rr["ms_obj"], 3), "iters": rr["iters"],
+                   "obj": rr["obj"], "n_absorb": rr["n_absorb"]}
+            if gold is not None:
+                ent["rel_err_vs_fp64_oracle"] = abs(rr["obj"] - gold["obj"]) / abs(gold["obj"])
+                ent["oracle_iters"] = gold["iters"]
+            precision[k2] = ent
 
     # end to end through the public API with host buffers (pinned), copies inside
     hx, hy = torch.tensor(w.x, dtype=dt).pin_memory(), torch.tensor(w.y, dtype=dt).pin_memory()
@@ -206,10 +274,7 @@ def run_ours(args):
         flush_buf.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        if uot:
-            r = S.spar_sink_uot(ha, hb, hx, hy, lam=w.lam, **kw, workspace=ws, device=dev)
-        else:
-            r = S.spar_sink_ot(ha, hb, hx, hy, **kw, workspace=ws, device=dev)
+        r = solve(a=ha, b=hb, x=hx, y=hy, workspace=ws, device=dev)
         al, be = r["alpha"].cpu(), r["beta"].cpu()
         obj = float(r["obj"])
         torch.cuda.synchronize()
@@ -220,15 +285,13 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(ms, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if w.dtype == "f32" else "f64", "data": "synthetic (seeded)",
-        "config": _config(w, "flushed between steps (512 MB write)"),
+        "vs_baseline": None, "dtype": kd, "data": "synthetic (seeded)",
+        "config": _config(w, "flushed between steps (512 MB write)", kd),
         "phases_ms": {"sketch": round(last["ms_sketch"], 4), "iterations": round(last["ms_iter"], 4),
                       "objective": round(last["ms_obj"], 4)},
         "iters": last["iters"], "nnz": last["nnz"], "residual": last["residual"], "obj": last["obj"],
-        "obj_sparse": last["obj_sparse"],
-        "dense_sinkhorn": {"ms": round(dense_ms, 4), "iters": dense["iters"], "obj": dense["obj"],
-                           "residual": dense["residual"], "speedup_of_spar_sink": round(dense_ms / ms, 2),
-                           "rel_obj_gap_sparse_value": abs(last["obj_sparse"] - dense["obj"]) / abs(dense["obj"])},
+        "obj_sparse": last["obj_sparse"], "n_absorb": last["n_absorb"],
+        "dense_sinkhorn": dense_line,
         "roofline": {"bound": "hbm", "kernel": "spmv half-iterations (row pass + column pass)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
@@ -239,6 +302,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if precision is not None:
+        line["precision_forms"] = precision
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
@@ -247,15 +312,54 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _oracle_solve(w):
+def _f32(z):
     import numpy as np
+    return np.asarray(z, np.float32).astype(np.float64)
 
+
+def _oracle_problem(w, rows=None):
     import oracle
-    f = (lambda z: np.asarray(z, np.float32).astype(np.float64)) if w.dtype == "f32" else (lambda z: np.asarray(z))
-    P = oracle.OracleProblem(f(w.a), f(w.b), w.eps, w.s, w.lam, x=f(w.x), y=f(w.y), seed=w.seed)
+    f = _f32 if w.dtype != "f64" else (lambda z: z)
+    x = w.x if rows is None else w.x[:rows]
+    a = w.a if rows is None else w.a[:rows]
+    # a row subset keeps the per-element probabilities of the whole problem with s scaled by rows/n
+    s = w.s if rows is None else w.s * rows / w.n
+    return oracle.OracleProblem(f(a), f(w.b), w.eps, s, w.lam, x=f(x), y=f(w.y), seed=w.seed)
+
+
+def _oracle_solve(w):
+    import oracle
+    P = _oracle_problem(w)
     t0 = time.perf_counter()
-    r = oracle.spar_sink(P, tol=TOL, max_iter=20000)
+    r = oracle.spar_sink(P, tol=TOL, max_iter=20000, log_domain=bool(_log_domain(w)))
     return (time.perf_counter() - t0) * 1e3, r
+
+
+# a full oracle solve above this many decisions (n m) is replaced by a bounded sample
+FULL_ORACLE_MAX_PAIRS = 1.0e9
+
+
+def _oracle_sampled(w, rows, iters, gold_iters):
+    """Bounded oracle sample of a large workload: the sketch (cost maximum,
+    count and fill passes) of the first `rows` rows against all m columns,
+    `iters` iterations and the objective on that partial sketch.  Returns the
+    whole-solve estimate (sketch scaled by n/rows, iterations and objective by
+    the nnz ratio and the iteration count) in ms, and a description."""
+    import oracle
+    P = _oracle_problem(w, rows)
+    t0 = time.perf_counter()
+    sk = P.sparsify()
+    t1 = time.perf_counter()
+    it = oracle.spar_sink(P, tol=0.0, max_iter=iters, log_domain=bool(_log_domain(w)), sketch=sk)
+    t2 = time.perf_counter()
+    nnz_full = w.s  # expected nnz of the whole sketch (no clipping at these budgets)
+    scale = nnz_full / max(sk["nnz"], 1)
+    per_iter = (t2 - t1) / max(iters, 1)   # includes the objective pass once per `iters` iterations
+    est = ((t1 - t0) * w.n / rows + per_iter * scale * gold_iters) * 1e3
+    desc = (f"FP64 oracle on the first {rows} of {w.n} rows against all {w.m} columns: sketch "
+            f"{(t1 - t0):.1f} s scaled by n/rows, then {iters} iterations + objective on that partial sketch "
+            f"({sk['nnz']} of ~{int(nnz_full)} elements) scaled by the element count to {gold_iters} iterations")
+    return est, desc
 
 
 def _threads():
@@ -265,14 +369,23 @@ def _threads():
         return os.cpu_count() or 1
 
 
+def _baseline_sample(w):
+    if float(w.n) * w.m <= FULL_ORACLE_MAX_PAIRS:
+        ms, r = _oracle_solve(w)
+        return ms, (f"one complete FP64 oracle solve of {w.name} (sketch, {r['info']['iters']} iterations to "
+                    f"1e-5, objective) on the host cores, OpenMP over rows")
+    gold = _golden(w)
+    gi = gold["iters"] if gold else 200
+    rows = max(256, int(4.0e8 / w.m))
+    return _oracle_sampled(w, rows, 5, gi)
+
+
 def cpu_baseline(w):
     import oracle
     oracle.build_oracle()
-    ms, r = _oracle_solve(w)
+    ms, desc = _baseline_sample(w)
     return {"value": round(ms, 1), "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", _threads())),
-            "kind": "oracle",
-            "sample": f"one complete FP64 oracle solve of {w.name} (sketch, {r['info']['iters']} iterations to "
-                      f"1e-5, objective) on the host cores, OpenMP over rows"}
+            "kind": "oracle", "sample": desc}
 
 
 def run_reference(args):
@@ -286,22 +399,24 @@ def run_reference(args):
     small = inputs.uot_n20000(n=2000) if not math.isinf(w.lam) else inputs.ot_n1000()
     for _ in range(max(args.warmup, 0)):
         _oracle_solve(small)
-    times = []
+    times, descs = [], []
     budget_s = 200.0
     t_start = time.perf_counter()
     for k in range(args.steps):
-        ms, r = _oracle_solve(w)
+        t0 = time.perf_counter()
+        ms, desc = _baseline_sample(w)
         times.append(ms)
-        if (time.perf_counter() - t_start) + ms / 1e3 > budget_s:
+        descs.append(desc)
+        if (time.perf_counter() - t_start) + (time.perf_counter() - t0) > budget_s:
             break
     val = sum(times) / len(times)
     cores = int(os.environ.get("OMP_NUM_THREADS", _threads()))
-    sample = (f"each step one complete FP64 oracle solve of {w.name} (sketch, iterations to 1e-5, objective); "
-              f"{len(times)} of {args.steps} requested steps run within the {budget_s:.0f} s bound; warm-up on n=2000")
+    sample = (f"each step: {descs[-1]}; {len(times)} of {args.steps} requested steps run within the "
+              f"{budget_s:.0f} s bound; warm-up on a small instance")
     line = {"metric": METRIC, "value": round(val, 1), "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
             "steps": len(times), "warmup": args.warmup, "ms_per_step": round(val, 1), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-            "config": _config(w, "n/a (CPU)"), "impl": "reference",
+            "config": _config(w, "n/a (CPU)", args.kdtype or w.dtype), "impl": "reference",
             "cpu_baseline": {"value": round(val, 1), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": round(val, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -313,7 +428,11 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="uot_n20000")
+    ap.add_argument("--workload", default="uot_n20000", choices=WORKLOADS)
+    ap.add_argument("--kdtype", default=None, choices=["f64", "f32", "bf16", "f16"],
+                    help="storage type of the sketch values (default: the workload's)")
+    ap.add_argument("--dense-cap", type=int, default=0,
+                    help="stop dense Sinkhorn after this many iterations and extrapolate (0: run to tolerance)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
