@@ -92,7 +92,17 @@ typedef struct {
   double absorb_tau;   /* absorb when max |log u~| or |log v~| exceeds this (0 = default 12) */
   const void* init_alpha; /* optional device warm start (n), iterate type, or NULL */
   const void* init_beta;  /* optional device warm start (m), iterate type, or NULL */
+  int32_t gather_mode; /* stabilised iterations only: how the sparse products read the
+                          gathered scaling vector.  SPS_GATHER_AUTO (0) stages it through
+                          shared memory in column chunks when n and m are both >= 65536,
+                          SPS_GATHER_DIRECT (1) never does, SPS_GATHER_STAGED (2) always does
+                          (with at least four chunks when n or m exceeds 3072).
+                          The results agree to rounding; the choice is a performance one. */
 } sps_params;
+
+#define SPS_GATHER_AUTO 0
+#define SPS_GATHER_DIRECT 1
+#define SPS_GATHER_STAGED 2
 
 /* Results of a solve (host struct). */
 typedef struct {

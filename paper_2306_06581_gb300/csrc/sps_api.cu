@@ -48,6 +48,40 @@ static int64_t sketch_capacity(const sps_problem* P, const sps_params* Q) {
   return (int64_t)cap;
 }
 
+// Staged gathers for the stabilised iterations: when both scaling vectors are
+// too long to stay in L1 (2^16 entries and more), every block streams the
+// gathered vector through shared memory in chunks of W entries, one block per
+// SM.  W is the largest multiple of 1024 (at most 48K entries) that leaves room
+// for the block's own row sums, balanced over the chunks.
+constexpr int kStageMin = 1 << 16;
+constexpr int kStageWMax = 48 * 1024;
+constexpr size_t kStageSmem = 227 * 1024 - 1024;   // dynamic shared memory of one block
+
+template <typename Take>
+static void plan_staging(int n, int m, int mode, Layout* L, Take& take) {
+  if (mode == SPS_GATHER_DIRECT) return;
+  if (mode == SPS_GATHER_AUTO && (n < kStageMin || m < kStageMin)) return;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      nsm < 1) {
+    cudaGetLastError();
+    return;
+  }
+  const int big = std::max(n, m);
+  const size_t acc = (size_t)((big + nsm - 1) / nsm);
+  if (acc * 4 + 8192 * 4 > kStageSmem) return;
+  const int wcap = std::min<int>(kStageWMax, (int)(((kStageSmem - acc * 4) / 4) / 1024 * 1024));
+  int J = (big + wcap - 1) / wcap;
+  if (mode == SPS_GATHER_STAGED) J = std::max(J, std::min(4, (big + 1023) / 1024));   // forced: several chunks
+  const int W = (int)(((big + J - 1) / J + 1023) / 1024 * 1024);
+  L->stage_w = W;
+  L->stage_jr = (m + W - 1) / W;
+  L->stage_jc = (n + W - 1) / W;
+  L->stage_nsm = nsm;
+  L->seg_r = take((size_t)(L->stage_jr + 1) * n * 4);
+  L->seg_c = take((size_t)(L->stage_jc + 1) * m * 4);
+}
+
 bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
   memset(L, 0, sizeof(*L));
   const int n = P->n, m = P->m, d = P->d;
@@ -118,6 +152,7 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
       L->ecol = take((size_t)m * 4);
       L->pot_a = take((size_t)n * 4);
       L->pot_b = take((size_t)m * 4);
+      if (op == SPS_OP_SPAR_SINK) plan_staging(n, m, Q->gather_mode, L, take);
     }
   }
   L->nblk_rows = nb;
@@ -153,6 +188,7 @@ static sps_status validate(const sps_problem* P, const sps_params* Q, int op) {
   if (Q->log_domain && Q->kdtype == SPS_F64) { set_error("log_domain stores K' in F32, BF16 or F16"); return SPS_ERR_INVALID_ARG; }
   if (Q->log_domain && Q->stop_rule != SPS_STOP_RESIDUAL) { set_error("log_domain stops on the residual rule"); return SPS_ERR_INVALID_ARG; }
   if (Q->log_domain && Q->absorb_tau < 0.0) { set_error("absorb_tau must be >= 0"); return SPS_ERR_INVALID_ARG; }
+  if (Q->gather_mode < SPS_GATHER_AUTO || Q->gather_mode > SPS_GATHER_STAGED) { set_error("unknown gather_mode %d", Q->gather_mode); return SPS_ERR_INVALID_ARG; }
   if (op != SPS_OP_DENSE && (double)Q->s + 8.0 * sqrt(Q->s) + 1024.0 > 2147483647.0 &&
       (double)P->n * (double)P->m > 2147483647.0) {
     set_error("sample budget too large for int32 indices"); return SPS_ERR_CAPACITY;
@@ -352,6 +388,11 @@ static sps_status spar_sink_impl(const sps_problem* P, const sps_params* Q, void
   ic.lpr_cols = lanes_per_row((double)nnz / P->m, P->m);
   ic.log_domain = Q->log_domain ? 1 : 0;
   ic.tau = Q->absorb_tau > 0.0 ? Q->absorb_tau : 12.0;
+  if (ic.log_domain && L.stage_w > 0) {
+    // staged passes work on a row's share of one chunk
+    ic.lpr_rows = lanes_per_row((double)nnz / ((double)P->n * L.stage_jr), P->n);
+    ic.lpr_cols = ic.lpr_rows;
+  }
   if (ic.log_domain) {
     SPS_TRY(run_iterations(pd, L, ws, ic, Q, launch_log_iterations, launch_log_row_only, st, &h));
     ev.rec(2, st);

@@ -77,6 +77,9 @@ struct Layout {
   size_t qpart, rpart;              // dense: split partial vectors
   size_t logval, logvalT;           // log-domain: log K~ in CSR / CSC order (binary32)
   size_t bhat, erow, ecol, pot_a, pot_b;
+  size_t seg_r, seg_c;              // staged gathers: chunk pointers of the CSR rows / CSC columns
+  int stage_w, stage_jr, stage_jc;  // staged gathers: chunk width, chunks over columns / rows (0: off)
+  int stage_nsm;                    // SM count the staging was planned for
   size_t part;                      // block partials
   size_t total;
   int64_t cap;                      // sketch capacity (elements)

@@ -18,9 +18,12 @@ constexpr long long kSpinLimit = 20000000;  // grid-barrier wait limit (about 1-
 // A lane takes kU elements of the row per batch: all their index and value
 // loads are issued first, then all gathers of x, so a batch costs two memory
 // round trips however long it is; a butterfly reduction closes the segment.
+// Only the index array is read through the read-only path: the values (which
+// the stabilised kernel rewrites) and x (written by other blocks before the
+// last grid barrier) use coherent loads.
 template <int LPR, typename V, typename T>
-__device__ __forceinline__ T seg_row_dot(const int* __restrict__ idx, const V* __restrict__ val,
-                                         const T* __restrict__ x, int lo, int hi, int sl) {
+__device__ __forceinline__ T seg_row_dot(const int* __restrict__ idx, const V* val, const T* x, int lo, int hi,
+                                         int sl) {
   constexpr int kU = sizeof(T) == 8 ? 4 : (LPR >= 32 ? 8 : (LPR == 16 ? 12 : 16));
   T acc = 0;
   for (int k0 = lo + sl; k0 < hi; k0 += LPR * kU) {
@@ -35,9 +38,34 @@ __device__ __forceinline__ T seg_row_dot(const int* __restrict__ idx, const V* _
     }
     T xv[kU];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) xv[u] = id[u] >= 0 ? __ldg(x + id[u]) : (T)0;
+    for (int u = 0; u < kU; ++u) xv[u] = id[u] >= 0 ? x[id[u]] : (T)0;
 #pragma unroll
     for (int u = 0; u < kU; ++u) acc += vv[u] * xv[u];
+  }
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
+// The same product with x staged in shared memory: xs holds x[j0 .. j0 + W);
+// an index outside the chunk (which a correct segment never holds) adds nothing.
+template <int LPR, typename V>
+__device__ __forceinline__ float seg_dot_smem(const int* __restrict__ idx, const V* val, const float* xs, int j0,
+                                              int W, int lo, int hi, int sl) {
+  constexpr int kU = LPR >= 8 ? 8 : 16;
+  float acc = 0.0f;
+  for (int k0 = lo + sl; k0 < hi; k0 += LPR * kU) {
+    int id[kU];
+    float vv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int k = k0 + u * LPR;
+      const bool in = k < hi;
+      id[u] = in ? __ldg(idx + k) - j0 : -1;
+      vv[u] = in ? load_as<float>(val + k) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) acc += (unsigned)id[u] < (unsigned)W ? vv[u] * xs[id[u]] : 0.0f;
   }
 #pragma unroll
   for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

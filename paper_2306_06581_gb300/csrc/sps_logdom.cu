@@ -52,6 +52,12 @@ struct LogArgs {
   Ctrl* ctrl;
   double* part;
   int nblk;
+  // staged gathers (large problems): the gathered vector passes through shared
+  // memory in chunks of W entries; block b owns rows [b rows_pb, (b+1) rows_pb)
+  // and columns [b cols_pb, (b+1) cols_pb); seg_r[c n + i] is the first CSR
+  // position of row i with column >= c W (c = 0 .. Jr), seg_c likewise for CSC.
+  int stage, W, Jr, Jc, rows_pb, cols_pb;
+  const int *seg_r, *seg_c;
 };
 
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
@@ -151,6 +157,55 @@ __global__ void k_log_init(int n, int m, float* alpha, float* beta, const T* al0
 // ----------------------------------------------------------------------------
 // Phases of the stabilised iteration.
 // ----------------------------------------------------------------------------
+
+// Row update from q' = (K' v~)_i (scale applied): u~ = (a^/q')^phi; residual
+// term (a/a^)|u~_old^{1/phi} q' - a^|; an empty row is unreachable (u~ = 0).
+template <bool UOT>
+__device__ __forceinline__ float row_math(const LogArgs& A, float q, float ah, float ai, float uo, float& res,
+                                          float& unr, float& mlog) {
+  float un;
+  if (q > 0.0f) {
+    un = UOT ? powf(ah / q, A.phi) : ah / q;
+    const float lhs = (UOT ? powf(uo, A.inv_phi) : uo) * q;
+    const float w = UOT ? (ah > 0.0f ? ai / ah : 1.0f) : 1.0f;
+    res += w * fabsf(lhs - ah);
+    if (un > 0.0f) mlog = fmaxf(mlog, fabsf(logf(un)));
+  } else {
+    un = 0.0f;
+    unr += ai;
+  }
+  return un;
+}
+
+// Column update from r' = (K'^T u~)_j: v~ = (b^/r')^phi.
+template <bool UOT>
+__device__ __forceinline__ float col_math(const LogArgs& A, float r, float bh, float bj, float& unb, float& mlog) {
+  float vn;
+  if (r > 0.0f) {
+    vn = UOT ? powf(bh / r, A.phi) : bh / r;
+    if (vn > 0.0f) mlog = fmaxf(mlog, fabsf(logf(vn)));
+  } else {
+    vn = 0.0f;
+    unb += bj;
+  }
+  return vn;
+}
+
+// Block totals of a phase: sums of NV values (thread 0) and the block maximum
+// of mlog (thread 0).
+template <int NV>
+__device__ __forceinline__ float finish_phase(float (&s)[NV], float mlog, float* sh) {
+  block_sum_multi<NV, float>(s, sh);
+  const float mw = warp_max(mlog);
+  if ((threadIdx.x & 31) == 0) sh[64 + (threadIdx.x >> 5)] = mw;
+  __syncthreads();
+  float mm = 0.0f;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, sh[64 + w]);
+  __syncthreads();
+  return mm;
+}
+
 template <int LPR, typename V, bool UOT>
 __device__ __forceinline__ void log_row_phase(const LogArgs& A, int t, float (&o)[3], float* sh) {
   const float* v = A.vbuf + (size_t)(t & 1) * A.m;
@@ -168,35 +223,11 @@ __device__ __forceinline__ void log_row_phase(const LogArgs& A, int t, float (&o
     float ah = 0.f, ai = 0.f, uo = 0.f, er = 0.f;
     if (ok && sl == 0) { ah = A.ahat[i]; ai = A.a[i]; uo = uold[i]; er = A.erow[i]; }
     const float qs = seg_row_dot<LPR, V, float>(A.col_idx, (const V*)A.val, v, lo, hi, sl);
-    if (ok && sl == 0) {
-      const float q = qs * exp2f(er);
-      float un;
-      if (q > 0.0f) {
-        un = UOT ? powf(ah / q, A.phi) : ah / q;
-        const float lhs = (UOT ? powf(uo, A.inv_phi) : uo) * q;
-        const float w = UOT ? (ah > 0.0f ? ai / ah : 1.0f) : 1.0f;
-        res += w * fabsf(lhs - ah);
-        if (un > 0.0f) mlog = fmaxf(mlog, fabsf(logf(un)));
-      } else {
-        un = 0.0f;
-        unr += ai;
-      }
-      unew[i] = un;
-    }
+    if (ok && sl == 0) unew[i] = row_math<UOT>(A, qs * exp2f(er), ah, ai, uo, res, unr, mlog);
   }
-  o[0] = res; o[1] = unr; o[2] = mlog;
   float s2[2] = {res, unr};
-  block_sum_multi<2, float>(s2, sh);
+  o[2] = finish_phase<2>(s2, mlog, sh);
   o[0] = s2[0]; o[1] = s2[1];
-  o[2] = warp_max(mlog);
-  if ((threadIdx.x & 31) == 0) sh[64 + (threadIdx.x >> 5)] = o[2];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float mm = 0.0f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, sh[64 + w]);
-    o[2] = mm;
-  }
-  __syncthreads();
 }
 
 template <int LPR, typename V, bool UOT>
@@ -215,31 +246,113 @@ __device__ __forceinline__ void log_col_phase(const LogArgs& A, int t, float (&o
     float bh = 0.f, bj = 0.f, ec = 0.f;
     if (ok && sl == 0) { bh = A.bhat[j]; bj = A.b[j]; ec = A.ecol[j]; }
     const float rs = seg_row_dot<LPR, V, float>(A.row_idx, (const V*)A.valT, u, lo, hi, sl);
-    if (ok && sl == 0) {
-      const float r = rs * exp2f(ec);
-      float vn;
-      if (r > 0.0f) {
-        vn = UOT ? powf(bh / r, A.phi) : bh / r;
-        if (vn > 0.0f) mlog = fmaxf(mlog, fabsf(logf(vn)));
-      } else {
-        vn = 0.0f;
-        unb += bj;
-      }
-      vnew[j] = vn;
-    }
+    if (ok && sl == 0) vnew[j] = col_math<UOT>(A, rs * exp2f(ec), bh, bj, unb, mlog);
   }
   float s1[1] = {unb};
-  block_sum_multi<1, float>(s1, sh);
+  o[1] = finish_phase<1>(s1, mlog, sh);
   o[0] = s1[0];
-  const float mw = warp_max(mlog);
-  if ((threadIdx.x & 31) == 0) sh[64 + (threadIdx.x >> 5)] = mw;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float mm = 0.0f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, sh[64 + w]);
-    o[1] = mm;
+}
+
+// The sparse products of one block's rows [r0, r0 + nr) with x staged in
+// shared memory chunk by chunk (J chunks of W entries of x, x of length nx):
+// acc[k] += sum over the elements of row r0 + k whose column lies in the chunk.
+// seg[c * ldseg + i] is the first position of row i in chunk c.
+template <int LPR, typename V>
+__device__ __forceinline__ void staged_pass(const int* __restrict__ idx, const V* val, const float* x, int nx,
+                                            const int* __restrict__ seg, int ldseg, int r0, int nr, int W, int J,
+                                            float* xs, float* acc) {
+  constexpr int RPW = 32 / LPR;
+  const int lane = threadIdx.x & 31, sl = lane & (LPR - 1);
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  for (int c = 0; c < J; ++c) {
+    const int j0 = c * W;
+    const int jn = min(W, nx - j0);
+    __syncthreads();   // the previous chunk is no longer read (and acc is initialised)
+    if ((((uintptr_t)(x + j0)) & 15) == 0) {
+      const int n4 = jn >> 2;
+      const float4* src = reinterpret_cast<const float4*>(x + j0);
+      for (int k = threadIdx.x; k < n4; k += blockDim.x) reinterpret_cast<float4*>(xs)[k] = __ldcg(src + k);
+      for (int k = 4 * n4 + threadIdx.x; k < jn; k += blockDim.x) xs[k] = __ldcg(x + j0 + k);
+    } else {
+      for (int k = threadIdx.x; k < jn; k += blockDim.x) xs[k] = __ldcg(x + j0 + k);
+    }
+    __syncthreads();
+    const int* s0 = seg + (size_t)c * ldseg;
+    const int* s1 = seg + (size_t)(c + 1) * ldseg;
+    for (int base = warp * RPW; base < nr; base += nw * RPW) {
+      const int k = base + lane / LPR;
+      const bool ok = k < nr;
+      const int lo = ok ? __ldg(s0 + r0 + k) : 0, hi = ok ? __ldg(s1 + r0 + k) : 0;
+      const float dot = seg_dot_smem<LPR, V>(idx, val, xs, j0, jn, lo, hi, sl);
+      if (ok && sl == 0) acc[k] += dot;
+    }
   }
   __syncthreads();
+}
+
+// Staged row pass: v passes through shared memory chunk by chunk; the partial
+// products of this block's rows accumulate in shared memory.
+template <int LPR, typename V, bool UOT>
+__device__ __forceinline__ void log_row_phase_staged(const LogArgs& A, int t, float (&o)[3], float* sh, float* dsm) {
+  const float* v = A.vbuf + (size_t)(t & 1) * A.m;
+  const float* uold = A.ubuf + (size_t)(t & 1) * A.n;
+  float* unew = A.ubuf + (size_t)((t + 1) & 1) * A.n;
+  const int r0 = blockIdx.x * A.rows_pb;
+  const int nr = max(0, min(A.n, r0 + A.rows_pb) - r0);
+  float* acc = dsm + A.W;
+  for (int k = threadIdx.x; k < nr; k += blockDim.x) acc[k] = 0.0f;
+  staged_pass<LPR, V>(A.col_idx, (const V*)A.val, v, A.m, A.seg_r, A.n, r0, nr, A.W, A.Jr, dsm, acc);
+  float res = 0.0f, unr = 0.0f, mlog = 0.0f;
+  for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+    const int i = r0 + k;
+    unew[i] = row_math<UOT>(A, acc[k] * exp2f(A.erow[i]), A.ahat[i], A.a[i], uold[i], res, unr, mlog);
+  }
+  float s2[2] = {res, unr};
+  o[2] = finish_phase<2>(s2, mlog, sh);
+  o[0] = s2[0]; o[1] = s2[1];
+}
+
+template <int LPR, typename V, bool UOT>
+__device__ __forceinline__ void log_col_phase_staged(const LogArgs& A, int t, float (&o)[2], float* sh, float* dsm) {
+  const float* u = A.ubuf + (size_t)((t + 1) & 1) * A.n;
+  float* vnew = A.vbuf + (size_t)((t + 1) & 1) * A.m;
+  const int c0 = blockIdx.x * A.cols_pb;
+  const int nc = max(0, min(A.m, c0 + A.cols_pb) - c0);
+  float* acc = dsm + A.W;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) acc[k] = 0.0f;
+  staged_pass<LPR, V>(A.row_idx, (const V*)A.valT, u, A.n, A.seg_c, A.m, c0, nc, A.W, A.Jc, dsm, acc);
+  float unb = 0.0f, mlog = 0.0f;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const int j = c0 + k;
+    vnew[j] = col_math<UOT>(A, acc[k] * exp2f(A.ecol[j]), A.bhat[j], A.b[j], unb, mlog);
+  }
+  float s1[1] = {unb};
+  o[1] = finish_phase<1>(s1, mlog, sh);
+  o[0] = s1[0];
+}
+
+// seg[c * ld + i] for c = 0 .. J: the first position of segment i (a CSR row
+// or a CSC column) whose index is >= c W; lane c of the segment's warp finds it
+// by binary search over the sorted indices.
+__global__ void k_chunk_ptrs(int rows, const int* __restrict__ ptr, const int* __restrict__ idx, int W, int J,
+                             int* __restrict__ seg) {
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += (gridDim.x * blockDim.x) >> 5) {
+    const int lo0 = ptr[i], hi0 = ptr[i + 1];
+    for (int c = lane; c <= J; c += 32) {
+      int lo = lo0, hi = hi0;
+      if (c == 0) hi = lo0;
+      else if (c == J) lo = hi0;
+      else {
+        const int key = c * W;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (idx[mid] < key) lo = mid + 1; else hi = mid;
+        }
+      }
+      seg[(size_t)c * rows + i] = lo;
+    }
+  }
 }
 
 // Fold the scalings of the pair t into the potentials (this block's rows and
@@ -285,16 +398,18 @@ __device__ __forceinline__ void rewrite_block(const LogArgs& A) {
 // a-mass, 3 unreachable b-mass, 5 / 7 max |log u~| (by the parity of t: the
 // row phase of the next iteration writes it before any barrier while slower
 // blocks may still read this iteration's values), 6 max |log v~|.
-template <int LR, int LC, typename V, bool UOT>
+template <int LR, int LC, typename V, bool UOT, bool STG>
 __global__ void __launch_bounds__(kIterThreads) k_iterate_log(LogArgs A, int iters, int row_only) {
   __shared__ float sh[3 * 32 + 64];
   __shared__ int absorb_now;
+  extern __shared__ __align__(16) float dsm[];   // staged chunk of the gathered vector, then row sums
   Ctrl* ctrl = A.ctrl;
   if (ctrl->done) return;
   int t = ctrl->t;
   for (int k = 0; k < iters; ++k) {
     float r3[3];
-    log_row_phase<LR, V, UOT>(A, t, r3, sh);
+    if constexpr (STG) log_row_phase_staged<LR, V, UOT>(A, t, r3, sh, dsm);
+    else log_row_phase<LR, V, UOT>(A, t, r3, sh);
     if (threadIdx.x == 0) {
       A.part[0 * (size_t)A.nblk + blockIdx.x] = r3[0];
       A.part[1 * (size_t)A.nblk + blockIdx.x] = r3[1];
@@ -329,7 +444,8 @@ __global__ void __launch_bounds__(kIterThreads) k_iterate_log(LogArgs A, int ite
     }
     if (row_only) return;
     float c2[2];
-    log_col_phase<LC, V, UOT>(A, t, c2, sh);
+    if constexpr (STG) log_col_phase_staged<LC, V, UOT>(A, t, c2, sh, dsm);
+    else log_col_phase<LC, V, UOT>(A, t, c2, sh);
     if (threadIdx.x == 0) {
       A.part[3 * (size_t)A.nblk + blockIdx.x] = c2[0];
       A.part[6 * (size_t)A.nblk + blockIdx.x] = c2[1];
@@ -369,17 +485,34 @@ __global__ void __launch_bounds__(kIterThreads) k_iterate_log(LogArgs A, int ite
   }
 }
 
-template <int LR, int LC, typename V, bool UOT>
+template <int LR, int LC, typename V, bool UOT, bool STG>
 bool coop_log(LogArgs A, int iters, int row_only, cudaStream_t st) {
-  auto fn = k_iterate_log<LR, LC, V, UOT>;
+  auto fn = k_iterate_log<LR, LC, V, UOT, STG>;
   int dev = 0, nsm = 0, per_sm = 0, coop = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kIterThreads, 0) != cudaSuccess || per_sm < 1) return false;
-  A.nblk = std::min(A.nblk, nsm * per_sm);
+  size_t smem = 0;
+  if (STG) {
+    // one block per SM owns a fixed row range and column range
+    smem = sizeof(float) * ((size_t)A.W + (size_t)std::max(A.rows_pb, A.cols_pb));
+    if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kIterThreads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  if (STG) {
+    if ((int64_t)A.rows_pb * nsm < A.n || (int64_t)A.cols_pb * nsm < A.m || A.nblk < nsm) return false;
+    A.nblk = nsm;
+  } else {
+    A.nblk = std::min(A.nblk, nsm * per_sm);
+  }
   void* args[] = {(void*)&A, (void*)&iters, (void*)&row_only};
-  if (cudaLaunchCooperativeKernel((const void*)fn, dim3(A.nblk), dim3(kIterThreads), args, 0, st) != cudaSuccess) {
+  if (cudaLaunchCooperativeKernel((const void*)fn, dim3(A.nblk), dim3(kIterThreads), args, smem, st) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -388,13 +521,20 @@ bool coop_log(LogArgs A, int iters, int row_only, cudaStream_t st) {
 
 template <int LR, typename V, bool UOT>
 bool coop_log_lc(const LogArgs& A, int lc, int iters, int row_only, cudaStream_t st) {
-  if (lc >= 32) return coop_log<LR, 32, V, UOT>(A, iters, row_only, st);
-  if (lc >= 16) return coop_log<LR, 16, V, UOT>(A, iters, row_only, st);
-  return coop_log<LR, 8, V, UOT>(A, iters, row_only, st);
+  if (lc >= 32) return coop_log<LR, 32, V, UOT, false>(A, iters, row_only, st);
+  if (lc >= 16) return coop_log<LR, 16, V, UOT, false>(A, iters, row_only, st);
+  return coop_log<LR, 8, V, UOT, false>(A, iters, row_only, st);
 }
 
 template <typename V, bool UOT>
 bool coop_log_dispatch(const LogArgs& A, int lr, int lc, int iters, int row_only, cudaStream_t st) {
+  if (A.stage) {
+    // staged segments are a row's share of one chunk: one lane count for both passes
+    if (lr >= 32) return coop_log<32, 32, V, UOT, true>(A, iters, row_only, st);
+    if (lr >= 16) return coop_log<16, 16, V, UOT, true>(A, iters, row_only, st);
+    if (lr >= 8) return coop_log<8, 8, V, UOT, true>(A, iters, row_only, st);
+    return coop_log<4, 4, V, UOT, true>(A, iters, row_only, st);
+  }
   if (lr >= 32) return coop_log_lc<32, V, UOT>(A, lc, iters, row_only, st);
   if (lr >= 16) return coop_log_lc<16, V, UOT>(A, lc, iters, row_only, st);
   return coop_log_lc<8, V, UOT>(A, lc, iters, row_only, st);
@@ -418,6 +558,12 @@ LogArgs make_log_args(const ProbDev& pd, const Layout& L, char* ws, const IterCf
   A.phi = (float)ic.phi; A.inv_phi = (float)(1.0 / ic.phi); A.tol = (float)ic.tol; A.tau = (float)ic.tau;
   A.uot = ic.uot;
   A.ctrl = at<Ctrl>(ws, L.ctrl); A.part = at<double>(ws, L.part); A.nblk = L.nblk_rows;
+  A.stage = L.stage_w > 0 ? 1 : 0;
+  A.W = L.stage_w; A.Jr = L.stage_jr; A.Jc = L.stage_jc;
+  A.rows_pb = L.stage_nsm > 0 ? (pd.n + L.stage_nsm - 1) / L.stage_nsm : 0;
+  A.cols_pb = L.stage_nsm > 0 ? (pd.m + L.stage_nsm - 1) / L.stage_nsm : 0;
+  A.seg_r = A.stage ? at<int>(ws, L.seg_r) : nullptr;
+  A.seg_c = A.stage ? at<int>(ws, L.seg_c) : nullptr;
   return A;
 }
 
@@ -544,6 +690,10 @@ void first_iteration_v(const LogArgs& A, const IterCfg& ic, const void* al0, con
   k_lse_half<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.col_ptr, A.row_idx, A.logvalT, A.alpha, A.b,
                                                          A.beta, A.eps, A.phi);
   k_absorb_all<V><<<grid1((int64_t)std::max(A.n, A.m) * 32, kT), kT, 0, st>>>(A, 1);
+  if (A.stage) {
+    k_chunk_ptrs<<<grid1((int64_t)A.n * 32, kT), kT, 0, st>>>(A.n, A.row_ptr, A.col_idx, A.W, A.Jr, (int*)A.seg_r);
+    k_chunk_ptrs<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.col_ptr, A.row_idx, A.W, A.Jc, (int*)A.seg_c);
+  }
   (void)ic;
 }
 
@@ -557,7 +707,7 @@ sps_status launch_log_first_iteration(const ProbDev& pd, const Layout& L, char* 
     case SPS_F16: first_iteration_v<__half>(A, ic, init_alpha, init_beta, st); break;
     default: first_iteration_v<float>(A, ic, init_alpha, init_beta, st); break;
   }
-  add_launches(4);
+  add_launches(A.stage ? 6 : 4);
   return cuda_fail(cudaGetLastError(), "log-domain first iteration");
 }
 

@@ -94,3 +94,30 @@ def test_log_domain_equals_plain_at_moderate_eps(S, lam):
     assert abs(pl["iters"] - lg["iters"]) <= max(2, 0.05 * pl["iters"])
     assert abs(pl["obj"] - lg["obj"]) <= 2e-6 * abs(pl["obj"])
     assert torch.allclose(pl["alpha"], lg["alpha"], rtol=0, atol=2e-5)
+
+
+@pytest.mark.parametrize("kd", ["f32", "bf16"])
+def test_staged_gathers_match_direct(S, ot_case, kd):
+    """Shared-memory staged gathers (several column chunks) against direct gathers
+    and, in FP32, against the oracle."""
+    w, (x, y, a, b), o = ot_case
+    kw = dict(eps=w.eps, s=w.s, tol=1e-5, max_iter=20000, dtype="f32", kdtype=kd, seed=w.seed, log_domain=1)
+    d = S.spar_sink_ot(a, b, x, y, gather_mode=S.GATHER_DIRECT, **kw)
+    g = S.spar_sink_ot(a, b, x, y, gather_mode=S.GATHER_STAGED, **kw)
+    assert g["status"] == 0 and g["nnz"] == d["nnz"]
+    assert abs(g["iters"] - d["iters"]) <= 1
+    assert abs(g["obj"] - d["obj"]) <= 2e-6 * abs(d["obj"])
+    if kd == "f32":
+        assert abs(g["obj"] - o["obj"]) <= 1e-5 * abs(o["obj"])
+
+
+def test_staged_gathers_uot(S, orc):
+    w = inputs.uot_n20000(n=3000)
+    x, y, a, b = _r32(w)
+    P = orc.OracleProblem(a, b, 0.01, w.s, 1.0, x=x, y=y, seed=w.seed)
+    o = orc.spar_sink(P, tol=1e-5, max_iter=20000, log_domain=True)
+    g = S.spar_sink_uot(a, b, x, y, eps=0.01, lam=1.0, s=w.s, tol=1e-5, max_iter=20000, dtype="f32", seed=w.seed,
+                        log_domain=1, gather_mode=S.GATHER_STAGED)
+    assert g["status"] == 0 and o["info"]["status"] == 0
+    assert abs(g["iters"] - o["info"]["iters"]) <= max(3, 0.05 * o["info"]["iters"])
+    assert abs(g["obj"] - o["obj"]) <= 1e-5 * abs(o["obj"])
