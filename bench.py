@@ -51,16 +51,18 @@ def _peaks():
 WORKLOADS = ("uot_n20000", "ot_n1000", "ot_n200000", "ot_n1000000")
 
 
-def _workload(name):
+def _workload(name, n=None):
+    """The named workload; n (profiling) re-draws the same family at another size."""
     from paper_2306_06581_gb300 import inputs
+    kw = {} if n is None else {"n": n}
     if name == "uot_n20000":
-        return inputs.uot_n20000()
+        return inputs.uot_n20000(**kw)
     if name == "ot_n1000":
-        return inputs.ot_n1000()
+        return inputs.ot_n1000(**kw)
     if name == "ot_n200000":
-        return inputs.ot_n200000()
+        return inputs.ot_n200000(**kw)
     if name == "ot_n1000000":
-        return inputs.ot_n1000000()
+        return inputs.ot_n1000000(**kw)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -166,7 +168,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = _workload(args.workload)
+    w = _workload(args.workload, args.n)
     uot = not math.isinf(w.lam)
     pdt = _problem_dtype(w)
     kd = args.kdtype or w.dtype
@@ -187,6 +189,13 @@ def run_ours(args):
 
     first = solve()
     ws = first["workspace"]
+    if args.solve_only:
+        # one more solve in the same workspace, for profilers; no timing loop
+        r = solve(workspace=ws)
+        if rank == 0:
+            print(json.dumps({"workload": w.name, "iters": r["iters"], "nnz": r["nnz"], "obj": r["obj"],
+                              "ms": r["ms_sketch"] + r["ms_iter"] + r["ms_obj"]}), flush=True)
+        return
     flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(max(args.warmup, 0)):
         solve(workspace=ws)
@@ -434,6 +443,8 @@ def main():
     ap.add_argument("--dense-cap", type=int, default=0,
                     help="stop dense Sinkhorn after this many iterations and extrapolate (0: run to tolerance)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="profiling: the workload's family at another size")
+    ap.add_argument("--solve-only", action="store_true", help="profiling: two solves, no timing loop")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -205,6 +205,73 @@ sps_status spar_sink_ot_noalloc(const sps_problem* prob, const sps_params* prm, 
                                 void* beta_out, sps_result* res, sps_stream stream);
 
 /* Thread-local message describing the last error on this thread. */
+/* ---------------- batches of problems over shared point sets ----------------
+ * Many independent problems whose points come from a few shared sets, e.g.
+ * all pairs of frames of an image sequence: pair p transports set src[p]
+ * (weights a = mass of that set) to set dst[p] (b = its mass), with its own
+ * budget s[p] and its own sampling stream (Philox problem id
+ * prm->problem_id + p).  Every pair is sketched as in Eq. (pois) with
+ * Eq. (pij-ot) or Eq. (pij-uot) and solved by Alg. 3 (lambda = +inf) or
+ * Alg. 4 with the stabilised iterations (log-domain first iteration and
+ * absorption, the form used for small eps), then its objective terms.
+ * There is no batched counterpart in the paper: the batch is a throughput
+ * form of the same per-pair computation, and each pair's pattern, iteration
+ * count and objective equal those of a single spar_sink_ot / spar_sink_uot
+ * call with log_domain = 1 and the same problem id (to rounding).
+ *
+ * The sketches of all pairs live in one block-diagonal CSR / CSC in the
+ * workspace; the iterations of all pairs run in ONE persistent launch whose
+ * blocks take pairs from a queue (largest first) and iterate each pair to its
+ * own stopping rule with block-local barriers only, the scaling vectors in
+ * shared memory.  Hence a support limit: 2 n_p + m_p <= SPS_BATCH_MAX_SMEM_ENTRIES
+ * for every pair.
+ */
+typedef struct {
+  int32_t n_sets;          /* number of point sets */
+  int32_t d;               /* dimension of the points, 1 .. 16 */
+  const int64_t* set_off;  /* HOST, n_sets + 1 offsets: set k holds points set_off[k] .. set_off[k+1]-1 */
+  const void* pts;         /* DEVICE, set_off[n_sets] x d row-major, dtype */
+  const void* mass;        /* DEVICE, set_off[n_sets] weights >= 0, dtype */
+  int32_t n_pairs;         /* number of problems */
+  const int32_t* src;      /* HOST, n_pairs source set indices */
+  const int32_t* dst;      /* HOST, n_pairs target set indices */
+  const double* s;         /* HOST, n_pairs sample budgets (> 0) */
+  int32_t cost_norm;       /* SPS_COST_RAW, SPS_COST_MAXNORM (max over the pair) or SPS_COST_SCALE */
+  double cost_scale;       /* divisor for SPS_COST_SCALE */
+  sps_dtype dtype;         /* F32 or F64 points and weights */
+} sps_batch;
+
+#define SPS_BATCH_MAX_SMEM_ENTRIES 49152
+
+/* Launch shape of the persistent iteration kernel.  Zero fields are chosen
+ * by the library's autotuner: it times every candidate (lanes per row 4, 8,
+ * 16, 32 x block threads 256, 512, 1024) on the batch itself for a few
+ * iterations and caches the winner per batch shape for the process. */
+typedef struct {
+  int32_t lanes_per_row;   /* lanes sharing one row / column segment: 4, 8, 16, 32, or 0 */
+  int32_t block_threads;   /* 256, 512, 1024, or 0 */
+  int32_t use_graph;       /* 1: capture the enqueued device work in a CUDA graph on the first
+                              call with this workspace and batch shape, and replay it after
+                              (needs a stream other than the legacy default stream) */
+  int32_t chosen_lanes;    /* out: the shape used */
+  int32_t chosen_threads;  /* out */
+  float tune_ms;           /* out: time spent autotuning in this call (0 if cached or fixed) */
+} sps_batch_opts;
+
+/* Workspace bytes for spar_sink_batched, or 0 on invalid arguments. */
+size_t sps_batch_workspace_bytes(const sps_batch* batch, const sps_params* prm);
+
+/* Solves every pair.  alpha_out: DEVICE, sum_p n_p floats (pair p's source
+ * potentials at offset sum_{q<p} n_q); beta_out likewise with m_p.  res:
+ * HOST array of n_pairs results (ms_* fields hold the whole batch's phase
+ * times).  Returns SPS_OK when every pair converged, SPS_NOT_CONVERGED if
+ * any did not (see res[p].status), or an error.  prm: eps, lambda, tol,
+ * max_iter, seed, problem_id, kdtype (F32, BF16 or F16), absorb_tau;
+ * init_alpha / init_beta (DEVICE, same layout as the outputs) may be given. */
+sps_status spar_sink_batched(const sps_batch* batch, const sps_params* prm, sps_batch_opts* opts, void* ws,
+                             size_t ws_bytes, void* alpha_out, void* beta_out, sps_result* res,
+                             sps_stream stream);
+
 const char* sps_last_error(void);
 
 /* Library version string. */

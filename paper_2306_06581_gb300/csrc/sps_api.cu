@@ -389,8 +389,10 @@ static sps_status spar_sink_impl(const sps_problem* P, const sps_params* Q, void
   ic.log_domain = Q->log_domain ? 1 : 0;
   ic.tau = Q->absorb_tau > 0.0 ? Q->absorb_tau : 12.0;
   if (ic.log_domain && L.stage_w > 0) {
-    // staged passes work on a row's share of one chunk
-    ic.lpr_rows = lanes_per_row((double)nnz / ((double)P->n * L.stage_jr), P->n);
+    // staged passes work on a row's share of one chunk: lanes x 16 (4 lanes) or
+    // x 8 (more lanes) elements per load batch, sized to the mean share
+    const double seg = (double)nnz / ((double)P->n * L.stage_jr);
+    ic.lpr_rows = seg <= 64.0 ? 4 : seg <= 128.0 ? 8 : seg <= 256.0 ? 16 : 32;
     ic.lpr_cols = ic.lpr_rows;
   }
   if (ic.log_domain) {

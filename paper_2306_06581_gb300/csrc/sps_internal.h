@@ -177,6 +177,12 @@ sps_status launch_dense_lse_row_only(const ProbDev& pd, const Layout& L, char* w
 sps_status launch_dense_lse_objective(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                                       void* alpha_out, void* beta_out, cudaStream_t st);
 
+// Shared with the batched path (sps_sketch.cu)
+void launch_scan_counts(const int* row_cnt, int* row_ptr, int n, const int* col_cnt, int* col_ptr, int* col_cur,
+                        int m, long long cap, Ctrl* ctrl, cudaStream_t st);
+void launch_csc_sort_f32(int m, const int* col_ptr, const int* tmp_row, const int* tmp_src, const float* val,
+                         int* row_idx, int* csr_pos, float* valT, Ctrl* ctrl, cudaStream_t st);
+
 template <typename T> T* at(char* ws, size_t off) { return reinterpret_cast<T*>(ws + off); }
 
 // p*_ij before clipping at 1, in the binary32 decision spec.

@@ -277,14 +277,23 @@ __device__ __forceinline__ void staged_pass(const int* __restrict__ idx, const V
       for (int k = threadIdx.x; k < jn; k += blockDim.x) xs[k] = __ldcg(x + j0 + k);
     }
     __syncthreads();
-    const int* s0 = seg + (size_t)c * ldseg;
-    const int* s1 = seg + (size_t)(c + 1) * ldseg;
-    for (int base = warp * RPW; base < nr; base += nw * RPW) {
-      const int k = base + lane / LPR;
-      const bool ok = k < nr;
-      const int lo = ok ? __ldg(s0 + r0 + k) : 0, hi = ok ? __ldg(s1 + r0 + k) : 0;
-      const float dot = seg_dot_smem<LPR, V>(idx, val, xs, j0, jn, lo, hi, sl);
-      if (ok && sl == 0) acc[k] += dot;
+    const int* s0 = seg + (size_t)c * ldseg + r0;
+    const int* s1 = seg + (size_t)(c + 1) * ldseg + r0;
+    // each warp owns a contiguous share of the rows; the segment bounds of 32
+    // rows arrive in one coalesced load and are handed out by shuffles
+    const int q = (nr + nw - 1) / nw;
+    const int wb = warp * q, we = min(nr, wb + q);
+    for (int g = wb; g < we; g += 32) {
+      const int gl = min(32, we - g);
+      const int lo_l = lane < gl ? __ldg(s0 + g + lane) : 0;
+      const int hi_l = lane < gl ? __ldg(s1 + g + lane) : 0;
+      for (int sub = 0; sub < gl; sub += RPW) {
+        const int rl = sub + lane / LPR;
+        const int lo = __shfl_sync(0xffffffffu, lo_l, rl & 31), hi = __shfl_sync(0xffffffffu, hi_l, rl & 31);
+        const bool ok = rl < gl;
+        const float dot = seg_dot_smem<LPR, V>(idx, val, xs, j0, jn, ok ? lo : 0, ok ? hi : 0, sl);
+        if (ok && sl == 0) acc[g + rl] += dot;
+      }
     }
   }
   __syncthreads();

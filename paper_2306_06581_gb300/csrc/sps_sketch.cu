@@ -458,6 +458,19 @@ static void csc_sort(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t 
                                                 L.logvalT ? at<float>(ws, L.logvalT) : nullptr);
 }
 
+// Shared with the batched sketch (one block-diagonal CSR / CSC for all pairs).
+void launch_scan_counts(const int* row_cnt, int* row_ptr, int n, const int* col_cnt, int* col_ptr, int* col_cur,
+                        int m, long long cap, Ctrl* ctrl, cudaStream_t st) {
+  k_scan2<<<2, 1024, 0, st>>>(row_cnt, row_ptr, n, col_cnt, col_ptr, col_cur, m, cap, ctrl);
+}
+
+void launch_csc_sort_f32(int m, const int* col_ptr, const int* tmp_row, const int* tmp_src, const float* val,
+                         int* row_idx, int* csr_pos, float* valT, Ctrl* ctrl, cudaStream_t st) {
+  const int gs = grid_for((int64_t)m * 32, 32 * kSortWarps);
+  k_csc_sort<float><<<gs, 32 * kSortWarps, 0, st>>>(m, col_ptr, tmp_row, tmp_src, val, row_idx, csr_pos, valT, ctrl,
+                                                    nullptr, nullptr);
+}
+
 sps_status launch_sample(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st) {
   Ctrl* ctrl = at<Ctrl>(ws, L.ctrl);
   int* row_cnt = at<int>(ws, L.row_cnt);

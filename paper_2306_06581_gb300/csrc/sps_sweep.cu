@@ -64,6 +64,35 @@ template <typename V> struct ValMath {
   }
 };
 
+// C_ij / eps for log K~ without the FP64 pipe (narrow on this GPU): the
+// squared distance of the binary32 points in double-float arithmetic (exact
+// differences by TwoSum, squares by an FMA error term), times 1/(dn eps) held
+// as a binary32 pair.  The result is within about one binary32 ulp of the
+// FP64 value.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ float cost_over_eps_df(const float* xi, const float* yj, int d, float k_hi, float k_lo) {
+  float hi = 0.0f, lo = 0.0f;
+  for (int k = 0; k < d; ++k) {
+    float t, te;
+    two_sum(xi[k], -yj[k], t, te);
+    const float p = __fmul_rn(t, t);
+    const float pe = __fmaf_rn(t, t, -p);                 // exact error of t*t
+    const float q = __fmaf_rn(__fmul_rn(2.0f, t), te, pe);  // 2 t te + error (te^2 below ulp)
+    float s, se;
+    two_sum(hi, p, s, se);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(se, q));
+  }
+  const float ph = __fmul_rn(hi, k_hi);
+  const float pe = __fmaf_rn(hi, k_hi, -ph);
+  return __fadd_rn(ph, __fmaf_rn(hi, k_lo, __fmaf_rn(lo, k_hi, pe)));
+}
+
 template <int MODE, bool UOT, int D, typename V>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
   if (A.ctrl->status != SPS_OK) return;
@@ -87,6 +116,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
   }
   constexpr int DR = D > 0 ? D : kMaxDSmem;
   if (blockDim.x != kSweepThreads) return;  // the row mapping assumes 8 warps
+  // log K~ in binary32 arithmetic when the points are binary32 (no FP64 copy, no dense cost)
+  const bool lv32 = MODE == SW_FILL && A.logval && !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64;
+  float k_hi = 0.0f, k_lo = 0.0f;
+  if (lv32) {
+    const double k64 = 1.0 / (A.sc->dn64 * pd.eps);
+    k_hi = __double2float_rn(k64);
+    k_lo = __double2float_rn(k64 - (double)k_hi);
+  }
   for (int rb = blockIdx.x * kRB; rb < n; rb += gridDim.x * kRB) {
     // rows rb + warp*kRW + r, r < kRW, handled one after the other on each tile
     int cnt[kRW], pos0[kRW], pend[kRW];
@@ -178,15 +215,16 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
             for (int e = 0; e < 4; ++e)
               if (mask & (1u << e)) atomicAdd(&A.col_cnt[j + e], 1);
           } else if (MODE == SW_FILL) {
+            // most steps keep nothing anywhere in the warp
+            if (__ballot_sync(0xffffffffu, mask != 0u) == 0u) continue;
+            // warp prefix of the per-lane counts (0 .. 4) from three bit ballots
             const int cnum = __popc(mask);
-            int incl = cnum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const int y = __shfl_up_sync(0xffffffffu, incl, o);
-              if (lane >= o) incl += y;
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            int pos = pos0[r] + incl - cnum;
+            const unsigned c0 = __ballot_sync(0xffffffffu, cnum & 1), c1 = __ballot_sync(0xffffffffu, cnum & 2),
+                           c2 = __ballot_sync(0xffffffffu, cnum & 4);
+            const unsigned lt = (1u << lane) - 1u;
+            const int excl = __popc(c0 & lt) + 2 * __popc(c1 & lt) + 4 * __popc(c2 & lt);
+            const int total = __popc(c0) + 2 * __popc(c1) + 4 * __popc(c2);
+            int pos = pos0[r] + excl;
             if (mask) {
               const SketchScalars& sc = *A.sc;
               V* val = (V*)A.val;
@@ -195,15 +233,22 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
                 if (mask & (1u << e)) {
                   const int jj = j + e;
                   const float ps = pe[e] < 1.0f ? pe[e] : 1.0f;
-                  const float Dd = UOT ? Dv[e] : raw32(pd.cv, i, jj);
                   // bounds checks: a count/fill mismatch is recorded, never written out of range
                   if (pos >= pend[r]) { A.ctrl->sketch_fault = 1; ++pos; continue; }
                   A.col_idx[pos] = jj;
-                  val[pos] = from_d<V>(ValMath<V>::value(pd, sc, i, jj, Dd, ps));
-                  if (A.logval) {
-                    // log K~ = -C/eps - log p*, C from the FP64 distance of the binary32 points
-                    const double C64 = raw64(pd.cv, i, jj) / sc.dn64;
-                    A.logval[pos] = (float)(-C64 / pd.eps - (double)logf(ps));
+                  if (lv32) {
+                    // stabilised iterations: the absorption writes K' later; only log K~ = -C/eps - log p*
+                    const float ce = cost_over_eps_df(pd.cv.x32 + (int64_t)i * d, pd.cv.y32 + (int64_t)jj * d, d,
+                                                      k_hi, k_lo);
+                    A.logval[pos] = __fsub_rn(-ce, logf(ps));
+                  } else {
+                    const float Dd = UOT ? Dv[e] : raw32(pd.cv, i, jj);
+                    val[pos] = from_d<V>(ValMath<V>::value(pd, sc, i, jj, Dd, ps));
+                    if (A.logval) {
+                      // log K~ = -C/eps - log p*, C from the FP64 distance of the points
+                      const double C64 = raw64(pd.cv, i, jj) / sc.dn64;
+                      A.logval[pos] = (float)(-C64 / pd.eps - (double)logf(ps));
+                    }
                   }
                   const int slot = atomicAdd(&A.col_cur[jj], 1);
                   if (slot < A.col_end[jj]) {

@@ -92,14 +92,13 @@ def small_problem(n=64, m=None, d=3, seed=0, eps=0.1, lam=math.inf, s_factor=8.0
                     1e-6, dtype, seed=0x5EED + seed)
 
 
-def ot_n1000(seed=1):
+def ot_n1000(seed=1, n=1000):
     rng = np.random.default_rng(seed)
-    n = 1000
     x = rng.standard_normal((n, 5))
     y = rng.standard_normal((n, 5)) + 1.0
     a = _uniform_weights(rng, n)
     b = _uniform_weights(rng, n)
-    return Workload("ot_n1000_d5_eps0.1_f64", x, y, a, b, 0.1, math.inf, s_budget(n, 8.0), 1e-6,
+    return Workload(f"ot_n{n}_d5_eps0.1_f64", x, y, a, b, 0.1, math.inf, s_budget(n, 8.0), 1e-6,
                     "f64")
 
 
@@ -151,8 +150,8 @@ def frames(seed=4, n_frames=64, size=96, period=20.0, noise=0.05):
     raw = []
     for t in range(n_frames):
         ph = 2.0 * math.pi * t / period
-        r0 = 9.0 * (1.0 + 0.4 * math.sin(ph))
-        r1 = 7.0 * (1.0 + 0.4 * math.cos(ph))
+        r0 = 18.0 * (1.0 + 0.5 * math.sin(ph))
+        r1 = 12.0 * (1.0 + 0.5 * math.cos(ph))
         c0 = (32.0 + 10.0 * math.sin(ph), 40.0 + 6.0 * math.cos(ph))
         c1 = (64.0 + 8.0 * math.cos(ph), 56.0 + 10.0 * math.sin(ph))
         img = np.exp(-((xx - c0[0]) ** 2 + (yy - c0[1]) ** 2) / (2 * r0 ** 2))
