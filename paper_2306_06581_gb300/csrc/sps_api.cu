@@ -32,14 +32,6 @@ sps_status cuda_fail(cudaError_t e, const char* what) {
   return SPS_ERR_CUDA;
 }
 
-static size_t dtype_bytes(sps_dtype t) {
-  switch (t) {
-    case SPS_F64: return 8;
-    case SPS_F32: return 4;
-    default: return 2;
-  }
-}
-
 static int64_t sketch_capacity(const sps_problem* P, const sps_params* Q) {
   const double nm = (double)P->n * (double)P->m;
   double cap = ceil(Q->s + 8.0 * sqrt(Q->s) + 1024.0);
@@ -226,11 +218,6 @@ static sps_status read_ctrl(const Layout& L, char* ws, Ctrl* h, cudaStream_t st)
   return cuda_fail(cudaStreamSynchronize(st), "stream synchronize");
 }
 
-#define SPS_TRY(x)                     \
-  do {                                 \
-    sps_status _s = (x);               \
-    if (_s != SPS_OK) return _s;       \
-  } while (0)
 
 struct Events {
   cudaEvent_t e[4];

@@ -355,4 +355,33 @@ __device__ __forceinline__ int exact_floor_for(float bound) {
   return B < -149 ? -149 : B;
 }
 
+// C_ij / eps for log K~ without the FP64 pipe (narrow on this GPU): the
+// squared distance of the binary32 points in double-float arithmetic (exact
+// differences by TwoSum, squares by an FMA error term), times 1/(dn eps) held
+// as a binary32 pair.  The result is within about one binary32 ulp of the
+// FP64 value.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ float cost_over_eps_df(const float* xi, const float* yj, int d, float k_hi, float k_lo) {
+  float hi = 0.0f, lo = 0.0f;
+  for (int k = 0; k < d; ++k) {
+    float t, te;
+    two_sum(xi[k], -yj[k], t, te);
+    const float p = __fmul_rn(t, t);
+    const float pe = __fmaf_rn(t, t, -p);                 // exact error of t*t
+    const float q = __fmaf_rn(__fmul_rn(2.0f, t), te, pe);  // 2 t te + error (te^2 below ulp)
+    float s, se;
+    two_sum(hi, p, s, se);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(se, q));
+  }
+  const float ph = __fmul_rn(hi, k_hi);
+  const float pe = __fmaf_rn(hi, k_hi, -ph);
+  return __fadd_rn(ph, __fmaf_rn(hi, k_lo, __fmaf_rn(lo, k_hi, pe)));
+}
+
 }  // namespace sps

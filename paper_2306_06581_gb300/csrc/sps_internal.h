@@ -92,6 +92,20 @@ constexpr int kMaxBlocks = 4096;
 
 bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L);
 
+inline size_t dtype_bytes(sps_dtype t) {
+  switch (t) {
+    case SPS_F64: return 8;
+    case SPS_F32: return 4;
+    default: return 2;
+  }
+}
+
+#define SPS_TRY(x)                     \
+  do {                                 \
+    sps_status _s = (x);               \
+    if (_s != SPS_OK) return _s;       \
+  } while (0)
+
 // ---- error reporting and launch accounting ----
 void add_launches(int k);
 void set_error(const char* fmt, ...);

@@ -17,6 +17,8 @@ import os
 import threading
 from dataclasses import dataclass
 
+import numpy as np
+
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -301,3 +303,89 @@ def spar_sink_ot_noalloc(a, b, x=None, y=None, C_=None, *, eps, s, tol=1e-6, max
 
 def version() -> str:
     return lib().sps_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# batches of problems over shared point sets
+# ---------------------------------------------------------------------------
+
+_side_streams = {}
+
+
+def _side_stream(dev):
+    if dev not in _side_streams:
+        _side_streams[dev] = torch.cuda.Stream(dev)
+    return _side_streams[dev]
+
+
+class Batch(C.Structure):
+    _fields_ = [("n_sets", C.c_int32), ("d", C.c_int32), ("set_off", C.c_void_p), ("pts", C.c_void_p),
+                ("mass", C.c_void_p), ("n_pairs", C.c_int32), ("src", C.c_void_p), ("dst", C.c_void_p),
+                ("s", C.c_void_p), ("cost_norm", C.c_int32), ("cost_scale", C.c_double), ("dtype", C.c_int32)]
+
+
+class BatchOpts(C.Structure):
+    _fields_ = [("lanes_per_row", C.c_int32), ("block_threads", C.c_int32), ("use_graph", C.c_int32),
+                ("chosen_lanes", C.c_int32), ("chosen_threads", C.c_int32), ("tune_ms", C.c_float)]
+
+
+def spar_sink_batched(sets, pairs, s, *, eps, lam=math.inf, tol=1e-5, max_iter=1000, dtype="f32", kdtype=None,
+                      seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, absorb_tau=0.0,
+                      lanes_per_row=0, block_threads=0, use_graph=0, init_alpha=None, init_beta=None,
+                      workspace=None, device=None, raise_on_error=True):
+    """Every pair (src, dst) of `pairs` solved as Alg. 3 (lam = inf) or Alg. 4
+    on the sets `sets` = [(points k x d, masses k), ...] with budget s[p] and
+    Philox problem id problem_id + p.  Returns the per-pair results, the
+    potentials split per pair, and the launch shape the library used."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    dt = torch.float64 if dtype == "f64" else torch.float32
+    pts = torch.cat([torch.as_tensor(p, dtype=dt).reshape(len(m), -1) for p, m in sets]).to(dev).contiguous()
+    mass = torch.cat([torch.as_tensor(m, dtype=dt).reshape(-1) for _, m in sets]).to(dev).contiguous()
+    d = int(pts.shape[1])
+    set_off = np.zeros(len(sets) + 1, np.int64)
+    set_off[1:] = np.cumsum([len(m) for _, m in sets])
+    src = np.ascontiguousarray([p[0] for p in pairs], np.int32)
+    dst = np.ascontiguousarray([p[1] for p in pairs], np.int32)
+    sv = np.ascontiguousarray(np.broadcast_to(np.asarray(s, np.float64), (len(pairs),)))
+    bt = Batch(len(sets), d, set_off.ctypes.data, _ptr(pts), _ptr(mass), len(pairs), src.ctypes.data,
+               dst.ctypes.data, sv.ctypes.data, int(cost_norm), float(cost_scale), DTYPE_CODES[dtype])
+    kd = kdtype or ("f32" if dtype == "f64" else dtype)
+    ia, ib = _dev(init_alpha, torch.float32, dev), _dev(init_beta, torch.float32, dev)
+    prm = make_params(eps, lam, 1.0, tol, max_iter, 0, STOP_RESIDUAL, seed, problem_id, kd, 1, absorb_tau, ia, ib)
+    L = lib()
+    L.sps_batch_workspace_bytes.argtypes = [C.c_void_p, C.c_void_p]
+    L.sps_batch_workspace_bytes.restype = C.c_size_t
+    L.spar_sink_batched.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]
+    L.spar_sink_batched.restype = C.c_int
+    nbytes = L.sps_batch_workspace_bytes(C.byref(bt), C.byref(prm))
+    if nbytes == 0:
+        raise SpsError(SPS_ERR_INVALID_ARG, last_error())
+    ws = _workspace(nbytes, dev, workspace)
+    sizes = np.diff(set_off)
+    n_tot = int(sum(sizes[p[0]] for p in pairs))
+    m_tot = int(sum(sizes[p[1]] for p in pairs))
+    alpha = torch.empty(n_tot, dtype=torch.float32, device=dev)
+    beta = torch.empty(m_tot, dtype=torch.float32, device=dev)
+    opts = BatchOpts(int(lanes_per_row), int(block_threads), int(use_graph), 0, 0, 0.0)
+    res = (Result * len(pairs))()
+    cur = torch.cuda.current_stream(dev)
+    side = None
+    if use_graph and cur.cuda_stream == 0:
+        # graph capture needs a stream other than the legacy default stream
+        side = _side_stream(dev)
+        side.wait_stream(cur)
+    stream = C.c_void_p((side or cur).cuda_stream)
+    st = L.spar_sink_batched(C.byref(bt), C.byref(prm), C.byref(opts), _ptr(ws), nbytes, _ptr(alpha), _ptr(beta),
+                             C.byref(res), stream)
+    if side is not None:
+        cur.wait_stream(side)
+    if raise_on_error:
+        _check(st)
+    ro = np.concatenate([[0], np.cumsum([sizes[p[0]] for p in pairs])])
+    co = np.concatenate([[0], np.cumsum([sizes[p[1]] for p in pairs])])
+    return {"status_code": st, "results": [r.as_dict() for r in res],
+            "alpha": [alpha[ro[k]:ro[k + 1]] for k in range(len(pairs))],
+            "beta": [beta[co[k]:co[k + 1]] for k in range(len(pairs))],
+            "lanes_per_row": opts.chosen_lanes, "block_threads": opts.chosen_threads, "tune_ms": opts.tune_ms,
+            "workspace": ws, "alpha_flat": alpha, "beta_flat": beta}
