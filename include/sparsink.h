@@ -272,6 +272,63 @@ sps_status spar_sink_batched(const sps_batch* batch, const sps_params* prm, sps_
                              size_t ws_bytes, void* alpha_out, void* beta_out, sps_result* res,
                              sps_stream stream);
 
+/* ---------------- learned warm start ----------------
+ * The paper starts the scaling iterations from u = v = 1 (Alg. 1, Alg. 2).
+ * These entry points predict starting potentials instead, with one small
+ * network per side: for source point i,
+ *   f_i = [x_i / sqrt(cost_max), n a_i],  P = sum_j b_j relu(We [y_j / sqrt(cost_max), m b_j] + ce) / sum_j b_j,
+ *   alpha^_i = w3 . relu(W2 relu(W1 [f_i, P] + b1) + b2) + b3
+ * (hidden width SPS_MLP_HIDDEN, embedding SPS_MLP_EMB), and symmetrically
+ * beta^_j.  Potentials are in units of the normalised cost C = D / cost_max,
+ * ready for sps_params.init_alpha / init_beta with
+ * cost_norm = SPS_COST_SCALE, cost_scale = cost_max (which reproduces
+ * SPS_COST_MAXNORM exactly when cost_max comes from sps_cost_max).  The
+ * forward pass reads BF16 weights and accumulates in FP32; training keeps
+ * FP32 master weights and Adam moments.  The fixed point, stopping rule and
+ * result of the solve do not depend on the start; only the iteration count
+ * does.
+ *
+ * Parameter vectors: FP32 (sps_mlp_param_count(d) floats) and a BF16 copy of
+ * the same length; layout per side: We (EMB x (d+1)), ce, W1 (HIDDEN x
+ * (d+1+EMB)), b1, W2 (HIDDEN x HIDDEN), b2, w3, b3; the source side first.
+ * All pointers are DEVICE pointers; ws holds sps_mlp_workspace_bytes(). */
+#define SPS_MLP_HIDDEN 128
+#define SPS_MLP_EMB 16
+
+typedef struct {
+  const float* x; const float* y;   /* DEVICE points, n x d and m x d, binary32 */
+  const float* a; const float* b;   /* DEVICE weights */
+  int32_t n, m, d;                  /* 1 <= d <= 16 */
+  double cost_max;                  /* the cost divisor (sps_cost_max) */
+  double eps;                       /* training loss scale: errors are measured in units of eps */
+} sps_mlp_instance;
+
+size_t sps_mlp_param_count(int32_t d);
+size_t sps_mlp_workspace_bytes(void);
+/* He-uniform initialisation from the Philox stream of `seed`; fills both copies. */
+sps_status sps_mlp_init(float* params, void* params_bf16, int32_t d, uint64_t seed, sps_stream stream);
+sps_status sps_mlp_sync_bf16(const float* params, void* params_bf16, int32_t d, sps_stream stream);
+/* Exact maximum over all pairs of the binary32 squared distance (the divisor
+ * of SPS_COST_MAXNORM), read back to the host. */
+sps_status sps_cost_max(const float* x, int32_t n, const float* y, int32_t m, int32_t d, double* cost_max,
+                        void* ws, sps_stream stream);
+/* Predicted potentials alpha^ (n) and beta^ (m). */
+sps_status sps_mlp_infer(const void* params_bf16, const sps_mlp_instance* inst, float* alpha_out,
+                         float* beta_out, void* ws, sps_stream stream);
+/* Shift a potential pair (in place) so that sum a alpha = sum b beta over the
+ * finite entries (the OT gauge: (alpha + c, beta - c) is the same plan). */
+sps_status sps_mlp_gauge_fix(const sps_mlp_instance* inst, float* alpha, float* beta, void* ws,
+                             sps_stream stream);
+/* Gradient of the loss sum_i a_i ((alpha^_i - alpha_i)/eps)^2 / sum a + (same for beta)
+ * with respect to the BF16 forward's weights, into grad (param count floats);
+ * the loss value goes to *loss_out (HOST, may be NULL; non-NULL synchronises). */
+sps_status sps_mlp_grad(const float* params, const void* params_bf16, const sps_mlp_instance* inst,
+                        const float* alpha_target, const float* beta_target, float* grad, float* loss_out,
+                        void* ws, sps_stream stream);
+/* One Adam step (bias-corrected, step >= 1) on the FP32 master weights; refreshes the BF16 copy. */
+sps_status sps_mlp_adam(float* params, void* params_bf16, float* m1, float* m2, const float* grad, int32_t d,
+                        int32_t step, float lr, float beta1, float beta2, float eps, sps_stream stream);
+
 const char* sps_last_error(void);
 
 /* Library version string. */

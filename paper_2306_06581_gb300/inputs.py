@@ -190,3 +190,26 @@ WORKLOADS = {
     "ot_n200000": ot_n200000,
     "ot_n1000000": ot_n1000000,
 }
+
+
+def mlp_weights(d, seed, scale=1.0):
+    """Seeded warm-start network weights that are exact in BF16 (k / 2^10 with
+    |k| <= 255, times a power-of-two scale), for checks that feed the same
+    weights to the GPU and to the CPU reference.  Both sides, source first."""
+    rng = np.random.default_rng(seed)
+    F, E, H = d + 1, 16, 128
+    D0 = F + E
+    sizes = [E * F, E, H * D0, H, H * H, H, H, 1]
+    fans = [F, 0, D0, 0, H, 0, H, 0]
+    out = []
+    for _ in range(2):
+        for sz, fan in zip(sizes, fans):
+            lim = math.sqrt(6.0 / fan) if fan else 0.05
+            k = np.clip(np.rint(rng.uniform(-lim, lim, sz) * 1024.0 * scale), -255, 255)
+            out.append(k / 1024.0)
+    return np.concatenate(out)
+
+
+def ot_gmm16(n, seed, eps=0.01):
+    """The 16-component mixture family in R^3 (balanced OT, s = 16 n ln n)."""
+    return ot_gmm(n, 3, 16, seed, eps, 16.0, 1e-5, "f32", name=f"ot_n{n}_d3_gmm16_seed{seed}")

@@ -389,3 +389,95 @@ def spar_sink_batched(sets, pairs, s, *, eps, lam=math.inf, tol=1e-5, max_iter=1
             "beta": [beta[co[k]:co[k + 1]] for k in range(len(pairs))],
             "lanes_per_row": opts.chosen_lanes, "block_threads": opts.chosen_threads, "tune_ms": opts.tune_ms,
             "workspace": ws, "alpha_flat": alpha, "beta_flat": beta}
+
+
+# ---------------------------------------------------------------------------
+# learned warm start
+# ---------------------------------------------------------------------------
+
+class MlpInstance(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p), ("n", C.c_int32),
+                ("m", C.c_int32), ("d", C.c_int32), ("cost_max", C.c_double), ("eps", C.c_double)]
+
+
+def _mlp_lib():
+    L = lib()
+    if not getattr(L, "_mlp_ready", False):
+        V, S_ = C.c_void_p, C.c_size_t
+        L.sps_mlp_param_count.argtypes = [C.c_int32]
+        L.sps_mlp_param_count.restype = S_
+        L.sps_mlp_workspace_bytes.argtypes = []
+        L.sps_mlp_workspace_bytes.restype = S_
+        L.sps_mlp_init.argtypes = [V, V, C.c_int32, C.c_uint64, V]
+        L.sps_mlp_sync_bf16.argtypes = [V, V, C.c_int32, V]
+        L.sps_cost_max.argtypes = [V, C.c_int32, V, C.c_int32, C.c_int32, V, V, V]
+        L.sps_mlp_infer.argtypes = [V, V, V, V, V, V]
+        L.sps_mlp_gauge_fix.argtypes = [V, V, V, V, V]
+        L.sps_mlp_grad.argtypes = [V, V, V, V, V, V, V, V, V]
+        L.sps_mlp_adam.argtypes = [V, V, V, V, V, C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float, V]
+        for f in ("sps_mlp_init", "sps_mlp_sync_bf16", "sps_cost_max", "sps_mlp_infer", "sps_mlp_gauge_fix",
+                  "sps_mlp_grad", "sps_mlp_adam"):
+            getattr(L, f).restype = C.c_int
+        L._mlp_ready = True
+    return L
+
+
+def mlp_param_count(d):
+    return int(_mlp_lib().sps_mlp_param_count(int(d)))
+
+
+def _mlp_ws(device):
+    return torch.empty(int(_mlp_lib().sps_mlp_workspace_bytes()) + 256, dtype=torch.uint8, device=device)
+
+
+def cost_max(x, y, device=None):
+    """Exact maximum of the binary32 squared distances (the SPS_COST_MAXNORM divisor)."""
+    dev = torch.device(device) if device is not None else (x.device if isinstance(x, torch.Tensor) and x.is_cuda
+                                                           else torch.device("cuda"))
+    xd = _dev(x, torch.float32, dev).contiguous()
+    yd = _dev(y, torch.float32, dev).contiguous()
+    out = C.c_double(0.0)
+    st = _mlp_lib().sps_cost_max(_ptr(xd), xd.shape[0], _ptr(yd), yd.shape[0], xd.shape[1], C.byref(out),
+                                 _ptr(_mlp_ws(dev)), _stream())
+    _check(st, allow_not_converged=False)
+    return out.value
+
+
+def mlp_instance(x, a, y, b, cost_max_value, eps=1.0):
+    """Device tensors and the C struct of one instance (kept alive together)."""
+    inst = MlpInstance(_ptr(x), _ptr(y), _ptr(a), _ptr(b), x.shape[0], y.shape[0], x.shape[1],
+                       float(cost_max_value), float(eps))
+    inst.keep = (x, a, y, b)
+    return inst
+
+
+def mlp_init(params, params_bf16, d, seed):
+    _check(_mlp_lib().sps_mlp_init(_ptr(params), _ptr(params_bf16), int(d), int(seed), _stream()), False)
+
+
+def mlp_sync_bf16(params, params_bf16, d):
+    _check(_mlp_lib().sps_mlp_sync_bf16(_ptr(params), _ptr(params_bf16), int(d), _stream()), False)
+
+
+def mlp_infer(params_bf16, inst, alpha_out, beta_out, ws=None):
+    ws = ws if ws is not None else _mlp_ws(alpha_out.device)
+    _check(_mlp_lib().sps_mlp_infer(_ptr(params_bf16), C.byref(inst), _ptr(alpha_out), _ptr(beta_out), _ptr(ws),
+                                    _stream()), False)
+
+
+def mlp_gauge_fix(inst, alpha, beta, ws=None):
+    ws = ws if ws is not None else _mlp_ws(alpha.device)
+    _check(_mlp_lib().sps_mlp_gauge_fix(C.byref(inst), _ptr(alpha), _ptr(beta), _ptr(ws), _stream()), False)
+
+
+def mlp_grad(params, params_bf16, inst, alpha_t, beta_t, grad, ws=None, want_loss=True):
+    ws = ws if ws is not None else _mlp_ws(grad.device)
+    loss = C.c_float(0.0)
+    _check(_mlp_lib().sps_mlp_grad(_ptr(params), _ptr(params_bf16), C.byref(inst), _ptr(alpha_t), _ptr(beta_t),
+                                   _ptr(grad), C.byref(loss) if want_loss else None, _ptr(ws), _stream()), False)
+    return loss.value if want_loss else None
+
+
+def mlp_adam(params, params_bf16, m1, m2, grad, d, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(_mlp_lib().sps_mlp_adam(_ptr(params), _ptr(params_bf16), _ptr(m1), _ptr(m2), _ptr(grad), int(d),
+                                   int(step), float(lr), float(beta1), float(beta2), float(eps), _stream()), False)
