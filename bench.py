@@ -113,9 +113,7 @@ def run_batch(args):
         split = S.spar_sink_batched(dsets, pairs, s, workspace=ws, **kw)
     ms = sum(times) / len(times)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = _max_over_ranks(ms, dist, dev)
     res = last["results"]
     iters = np.array([r["iters"] for r in res])
     nnz = np.array([r["nnz"] for r in res], np.float64)
@@ -288,6 +286,14 @@ class ClockSampler:
 _VB = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
 
 
+def _max_over_ranks(x, dist, device):
+    """The slowest rank's value (replicas: every rank times its own solve)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _spmv_bytes(res, n, m, kdtype="f32", log_domain=0):
     """Algorithmic HBM bytes of one iteration (row pass + column pass): every
     stored element once (int32 index + value), the pointer arrays, the per-row
@@ -381,9 +387,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = sum(times) / len(times)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = _max_over_ranks(ms, dist, dev)
     last = results[-1]
     launches = int(sum(r["launches"] for r in results))
 
