@@ -428,7 +428,7 @@ def run_ours(args):
     # storage precision forms of the stabilised path against the stored FP64 oracle value
     precision = None
     gold = _golden(w)
-    if logd and rank == 0:
+    if logd and rank == 0 and gold is not None:
         precision = {}
         for k2 in ("f32", "bf16", "f16"):
             rr = solve(kdtype=k2)
@@ -478,12 +478,56 @@ def run_ours(args):
     }
     if precision is not None:
         line["precision_forms"] = precision
+    if args.warm_start:
+        line["warm_start"] = _warm_start_leg(args, w, S, x, y, a, b, kd, logd, last)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _warm_start_leg(args, w, S, x, y, a, b, kd, logd, cold):
+    """Train the warm-start network on seeded smaller instances of the same
+    family (targets from the solver), then time warm-started Spar-Sink on the
+    workload: exact cost divisor + inference + solve, against the cold solve."""
+    import torch
+
+    from paper_2306_06581_gb300 import inputs
+    from paper_2306_06581_gb300 import warmstart as WS
+    t0 = time.perf_counter()
+    data = []
+    for k in range(args.ws_instances):
+        wk = inputs.ot_gmm16(args.ws_n, seed=1000 + k)
+        inst, al, be, _ = WS.solve_targets(wk, w.eps, wk.s, seed=wk.seed, kdtype=kd)
+        data.append((inst, al, be))
+    t1 = time.perf_counter()
+    net = WS.WarmStart(w.d, seed=5)
+    losses = WS.train(net, data, args.ws_steps, lr=2e-3, lr_end=2e-4)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    st = torch.cuda.current_stream()
+    kw = dict(eps=w.eps, s=w.s, tol=TOL, max_iter=20000, dtype="f32", kdtype=kd, seed=w.seed, log_domain=logd)
+    runs = []
+    for rep in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        cm = S.cost_max(x, y)
+        al, be = net.predict(net.instance(x, a, y, b, cm))
+        r = S.spar_sink_ot(a, b, x, y, init_alpha=al, init_beta=be, cost_norm=S.COST_SCALE, cost_scale=cm, **kw)
+        e1.record(st)
+        e1.synchronize()
+        runs.append((e0.elapsed_time(e1), r))
+    ms, r = runs[-1]
+    return {"ms": round(ms, 3), "iters": r["iters"], "cold_iters": cold["iters"],
+            "obj_rel_diff_vs_cold": abs(r["obj"] - cold["obj"]) / abs(cold["obj"]),
+            "ms_iterations": round(r["ms_iter"], 3), "cold_ms_iterations": round(cold["ms_iter"], 3),
+            "training": {"instances": args.ws_instances, "n": args.ws_n, "steps": args.ws_steps,
+                         "targets_s": round(t1 - t0, 1), "train_s": round(t2 - t1, 1),
+                         "loss_first": float(sum(losses[:64]) / len(losses[:64])),
+                         "loss_last": float(sum(losses[-64:]) / len(losses[-64:]))},
+            "includes": "exact cost divisor, network inference and the solve (cold: the solve, which finds the divisor itself)"}
 
 
 def _f32(z):
@@ -629,6 +673,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="profiling: the workload's family at another size")
     ap.add_argument("--solve-only", action="store_true", help="profiling: two solves, no timing loop")
+    ap.add_argument("--warm-start", action="store_true", help="also train and time the learned warm start")
+    ap.add_argument("--ws-instances", type=int, default=512)
+    ap.add_argument("--ws-n", type=int, default=50000)
+    ap.add_argument("--ws-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -305,11 +305,12 @@ int orc_factors(const orc_problem* P, float* rowf, float* colf, orc_scalars* S) 
   if (check_problem(P)) return -1;
   const int32_t n = P->n, m = P->m;
   memset(S, 0, sizeof(*S));
-  /* maximum raw cost over all pairs, in both precisions (max is exact) */
+  /* maximum raw cost over all pairs, in both precisions (max is exact); it is
+     the divisor of the max-normalised cost only, so other normalisations skip it */
   float dmax32 = 0.0f;
   double dmax64 = 0.0;
 #pragma omp parallel for reduction(max : dmax32, dmax64) schedule(static)
-  for (int32_t i = 0; i < n; ++i) {
+  for (int32_t i = 0; i < (P->cost_norm == 1 ? n : 0); ++i) {
     for (int32_t j = 0; j < m; ++j) {
       float d32 = raw_cost32(P, i, j);
       double d64 = raw_cost64(P, i, j);

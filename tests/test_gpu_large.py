@@ -76,3 +76,22 @@ def test_ot_n200000_objective_vs_fp64_oracle(S, W, gold, kd, bound):
           f"absorptions {g['n_absorb']}")
     assert rel <= bound
     assert abs(g["iters"] - gold["iters"]) <= max(3, 0.05 * gold["iters"])
+
+
+def test_ot_n1000000_rows_bit_exact(S, orc):
+    """The 10^6-point workload: sampled rows of the GPU pattern equal the
+    oracle's rows (the OT decision does not involve the cost, so both sides
+    run with the raw cost and the oracle needs no 10^12-pair maximum)."""
+    w = inputs.ot_n1000000()
+    f = lambda z: np.asarray(z, np.float32).astype(np.float64)
+    x, y, a, b = f(w.x), f(w.y), f(w.a), f(w.b)
+    g = S.sparsify_kernel(a, b, x, y, eps=w.eps, s=w.s, dtype="f32", kdtype="f32", seed=w.seed,
+                          cost_norm=S.COST_RAW)
+    assert abs(g["nnz"] - w.s) < 6 * math.sqrt(w.s)
+    rp = g["row_ptr"].cpu().numpy()
+    ci = g["col_idx"].cpu().numpy()
+    P = orc.OracleProblem(a, b, w.eps, w.s, math.inf, x=x, y=y, seed=w.seed, cost_norm=0)
+    rng = np.random.default_rng(2)
+    for i in np.concatenate([[0, w.n - 1], rng.choice(w.n, 10, replace=False)]):
+        r = P.sample_row(int(i))
+        assert np.array_equal(ci[rp[i]:rp[i + 1]], r["cols"]), i
