@@ -98,7 +98,16 @@ typedef struct {
                           SPS_GATHER_DIRECT (1) never does, SPS_GATHER_STAGED (2) always does
                           (with at least four chunks when n or m exceeds 3072).
                           The results agree to rounding; the choice is a performance one. */
+  int32_t sketch_mode; /* SPS_SKETCH_SINGLE (0): one n x m sweep writes every kept element
+                          into a padded slot per (row, column chunk) sized from its expected
+                          count, then a compaction places it; if a slot overflows (a count
+                          about 8 standard deviations above its mean) the two passes run
+                          instead.  SPS_SKETCH_TWO_PASS (1): count, then fill.  Both give the
+                          same sketch bit for bit. */
 } sps_params;
+
+#define SPS_SKETCH_SINGLE 0
+#define SPS_SKETCH_TWO_PASS 1
 
 #define SPS_GATHER_AUTO 0
 #define SPS_GATHER_DIRECT 1

@@ -122,6 +122,22 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
       L->logval = take((size_t)cap * 4);
       L->logvalT = take((size_t)cap * 4);
     }
+    // single-pass sketch: padded slots of ceil(mu + 8 sqrt(mu) + 16) per (row, chunk); by Cauchy-Schwarz
+    // their total is at most s + 8 sqrt(cells s) + 17 cells (cells = n x chunks; one more per cell for
+    // the rounding up), plus a margin for the binary32 sums behind mu
+    const SweepGeo g = sweep_geometry(n, m);
+    const double cells = (double)n * g.nchunk;
+    double pcap = ceil(1.001 * Q->s + 8.0 * sqrt(cells * Q->s) + 17.0 * cells + 1024.0);
+    pcap = std::min(pcap, (double)n * (double)m);
+    if (Q->sketch_mode == SPS_SKETCH_SINGLE && pcap < 2147483000.0 && cells * 2.0 + 1.0 < 2147483000.0) {
+      L->pad_cap = (int64_t)pcap;
+      L->pad_ofs = take((size_t)(2 * cells + 1) * 4);
+      L->pad_col = take((size_t)pcap * 4);
+      L->pad_val = take((size_t)pcap * vb);   // written unless log K~ is formed in binary32
+      if (Q->log_domain) L->pad_lv = take((size_t)pcap * 4);
+      if (!isinf(Q->lambda)) L->zsum = take((size_t)cells * 4);
+      L->csum = take((size_t)g.nchunk * 4);
+    }
   }
   int part_blocks = nb;
   if (op == SPS_OP_DENSE) {
@@ -181,6 +197,7 @@ static sps_status validate(const sps_problem* P, const sps_params* Q, int op) {
   if (Q->log_domain && Q->stop_rule != SPS_STOP_RESIDUAL) { set_error("log_domain stops on the residual rule"); return SPS_ERR_INVALID_ARG; }
   if (Q->log_domain && Q->absorb_tau < 0.0) { set_error("absorb_tau must be >= 0"); return SPS_ERR_INVALID_ARG; }
   if (Q->gather_mode < SPS_GATHER_AUTO || Q->gather_mode > SPS_GATHER_STAGED) { set_error("unknown gather_mode %d", Q->gather_mode); return SPS_ERR_INVALID_ARG; }
+  if (Q->sketch_mode != SPS_SKETCH_SINGLE && Q->sketch_mode != SPS_SKETCH_TWO_PASS) { set_error("unknown sketch_mode %d", Q->sketch_mode); return SPS_ERR_INVALID_ARG; }
   if (op != SPS_OP_DENSE && (double)Q->s + 8.0 * sqrt(Q->s) + 1024.0 > 2147483647.0 &&
       (double)P->n * (double)P->m > 2147483647.0) {
     set_error("sample budget too large for int32 indices"); return SPS_ERR_CAPACITY;

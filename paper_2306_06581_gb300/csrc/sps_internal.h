@@ -40,6 +40,7 @@ struct Ctrl {
   unsigned int bar_gen;   //   and generation
   int wait_timeout;       // a bounded device wait gave up
   int sketch_fault;       // fill disagreed with count (write skipped instead of out of range)
+  int pad_overflow;       // single-pass sketch: a padded (row, chunk) slot was too small
 };
 
 // Scalars of the sampling decision, computed on the device.
@@ -78,6 +79,8 @@ struct Layout {
   size_t logval, logvalT;           // log-domain: log K~ in CSR / CSC order (binary32)
   size_t bhat, erow, ecol, pot_a, pot_b;
   size_t seg_r, seg_c;              // staged gathers: chunk pointers of the CSR rows / CSC columns
+  size_t pad_ofs, pad_col, pad_val, pad_lv, zsum, csum;   // single-pass sketch (0: two passes)
+  int64_t pad_cap;
   int stage_w, stage_jr, stage_jc;  // staged gathers: chunk width, chunks over columns / rows (0: off)
   int stage_nsm;                    // SM count the staging was planned for
   size_t part;                      // block partials
@@ -132,6 +135,12 @@ SweepGeo sweep_geometry(int n, int m);
 void launch_uot_Z(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st);
 void launch_count(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st);
 void launch_fill(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st);
+// Single pass: padded slots from the expected counts, then the sweep (counts and
+// entries together); the caller reads pad_overflow and either compacts or
+// falls back to launch_count / launch_fill.
+void launch_fused(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st);
+void launch_compact(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st);
+void launch_sum_chunks(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st);
 
 // Host launchers (sps_sketch.cu)
 sps_status launch_prepare(const ProbDev& pd, const Layout& L, char* ws, int it64, cudaStream_t st);

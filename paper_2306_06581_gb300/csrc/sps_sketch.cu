@@ -475,6 +475,32 @@ sps_status launch_sample(const ProbDev& pd, const Layout& L, char* ws, sps_dtype
   Ctrl* ctrl = at<Ctrl>(ws, L.ctrl);
   int* row_cnt = at<int>(ws, L.row_cnt);
   int* col_cnt = at<int>(ws, L.col_cnt);
+  if (L.pad_ofs) {
+    // one sweep into padded (row, chunk) slots; compaction gives the two-pass positions
+    cudaMemsetAsync(col_cnt, 0, sizeof(int) * (size_t)pd.m, st);
+    launch_fused(pd, L, ws, kd, st);
+    Ctrl h;
+    cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "single-pass sketch");
+    if (h.status == SPS_OK && !h.pad_overflow) {
+      launch_sum_chunks(pd, L, ws, st);
+      k_scan2<<<2, 1024, 0, st>>>(row_cnt, at<int>(ws, L.row_ptr), pd.n, col_cnt, at<int>(ws, L.col_ptr),
+                                  at<int>(ws, L.col_cur), pd.m, (long long)L.cap, ctrl);
+      launch_compact(pd, L, ws, kd, st);
+      switch (kd) {
+        case SPS_F64: csc_sort<double>(pd, L, ws, st); break;
+        case SPS_F32: csc_sort<float>(pd, L, ws, st); break;
+        case SPS_BF16: csc_sort<__nv_bfloat16>(pd, L, ws, st); break;
+        case SPS_F16: csc_sort<__half>(pd, L, ws, st); break;
+      }
+      add_launches(7);
+      return cuda_fail(cudaGetLastError(), "single-pass sketch");
+    }
+    if (h.status != SPS_OK) return SPS_OK;   // the caller reports the status
+    // a slot was too small: clear the flag and run the two passes
+    cudaMemsetAsync(&ctrl->pad_overflow, 0, sizeof(int), st);
+  }
   cudaMemsetAsync(col_cnt, 0, sizeof(int) * (size_t)pd.m, st);
   launch_count(pd, L, ws, st);
   k_scan2<<<2, 1024, 0, st>>>(row_cnt, at<int>(ws, L.row_ptr), pd.n, col_cnt, at<int>(ws, L.col_ptr),

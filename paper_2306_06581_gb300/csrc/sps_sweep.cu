@@ -28,7 +28,7 @@ constexpr int kTJ = 512;        // columns per shared-memory tile
 constexpr int kSteps = kTJ / 128;
 constexpr int kMaxDSmem = 16;   // coordinates staged for d <= 16; larger d reads global memory
 
-enum { SW_Z = 0, SW_COUNT = 1, SW_FILL = 2 };
+enum { SW_Z = 0, SW_COUNT = 1, SW_FILL = 2, SW_FUSED = 3 };
 
 struct SweepArgs {
   ProbDev pd;
@@ -48,6 +48,12 @@ struct SweepArgs {
   Ctrl* ctrl;
   int chunk;          // columns per chunk (multiple of kTJ)
   int nchunk;
+  // single-pass sketch: padded slots per (row, chunk), row-major [i * nchunk + c]
+  const int* pad_ofs;   // n * nchunk + 1 offsets
+  int* pad_col;
+  void* pad_val;
+  float* pad_lv;
+  float* zsum;          // UOT Z sweep: [nchunk][n] sums of w per (row, chunk) (or null)
 };
 
 template <typename V> struct ValMath;
@@ -67,6 +73,7 @@ template <typename V> struct ValMath {
 template <int MODE, bool UOT, int D, typename V>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
   if (A.ctrl->status != SPS_OK) return;
+  if (MODE == SW_FUSED && A.ctrl->pad_overflow) return;   // the slots were not laid out: two passes follow
   extern __shared__ __align__(16) float smem[];
   const ProbDev& pd = A.pd;
   const int n = pd.n, m = pd.m;
@@ -88,20 +95,23 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
   constexpr int DR = D > 0 ? D : kMaxDSmem;
   if (blockDim.x != kSweepThreads) return;  // the row mapping assumes 8 warps
   // log K~ in binary32 arithmetic when the points are binary32 (no FP64 copy, no dense cost)
-  const bool lv32 = MODE == SW_FILL && A.logval && !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64;
+  const bool lv32 = (MODE == SW_FILL ? A.logval != nullptr : MODE == SW_FUSED ? A.pad_lv != nullptr : false) &&
+                    !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64;
   float k_hi = 0.0f, k_lo = 0.0f;
   if (lv32) {
-    const double k64 = 1.0 / (A.sc->dn64 * pd.eps);
+    const double k64 = 1.0 / (A.sc->dn64 * pd.eps);   // one division per block
     k_hi = __double2float_rn(k64);
     k_lo = __double2float_rn(k64 - (double)k_hi);
   }
   for (int rb = blockIdx.x * kRB; rb < n; rb += gridDim.x * kRB) {
     // rows rb + warp*kRW + r, r < kRW, handled one after the other on each tile
     int cnt[kRW], pos0[kRW], pend[kRW];
+    float zr[kRW];
 #pragma unroll
     for (int r = 0; r < kRW; ++r) {
       const int i = rb + warp * kRW + r;
       cnt[r] = 0;
+      zr[r] = 0.0f;
       pos0[r] = 0;
       pend[r] = 0;
       if (MODE == SW_FILL && i < n) pend[r] = A.row_ptr[i + 1];
@@ -109,6 +119,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
         int p = A.row_ptr[i];
         for (int cc = 0; cc < c; ++cc) p += A.cnt2[(size_t)cc * n + i];
         pos0[r] = p;
+      }
+      if (MODE == SW_FUSED && i < n) {
+        pos0[r] = A.pad_ofs[(size_t)i * A.nchunk + c];
+        pend[r] = A.pad_ofs[(size_t)i * A.nchunk + c + 1];
       }
     }
     for (int j0 = jc0; j0 < jc1; j0 += kTJ) {
@@ -170,7 +184,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
                 float p;
                 if (UOT) {
                   const float w = __fmul_rn(__fmul_rn(ri, cv[e]), spec_exp(-__fmul_rn(Dv[e], kappa)));
-                  if (MODE == SW_Z) { exact_add(acc, &A.sc->acc1, Bz, w); continue; }
+                  if (MODE == SW_Z) { exact_add(acc, &A.sc->acc1, Bz, w); zr[r] += w; continue; }
                   p = __fmul_rn(scale, w);
                 } else {
                   p = __fmul_rn(ri, cv[e]);
@@ -180,12 +194,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
               }
             }
           }
-          if (MODE == SW_COUNT) {
+          if (MODE == SW_COUNT || MODE == SW_FUSED) {
             cnt[r] += __popc(mask);
 #pragma unroll
             for (int e = 0; e < 4; ++e)
               if (mask & (1u << e)) atomicAdd(&A.col_cnt[j + e], 1);
-          } else if (MODE == SW_FILL) {
+          }
+          if (MODE == SW_FILL || MODE == SW_FUSED) {
             // most steps keep nothing anywhere in the warp
             if (__ballot_sync(0xffffffffu, mask != 0u) == 0u) continue;
             // warp prefix of the per-lane counts (0 .. 4) from three bit ballots
@@ -198,35 +213,45 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
             int pos = pos0[r] + excl;
             if (mask) {
               const SketchScalars& sc = *A.sc;
-              V* val = (V*)A.val;
+              V* val = (V*)(MODE == SW_FUSED ? A.pad_val : A.val);
+              int* cidx = MODE == SW_FUSED ? A.pad_col : A.col_idx;
+              float* lvo = MODE == SW_FUSED ? A.pad_lv : A.logval;
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 if (mask & (1u << e)) {
                   const int jj = j + e;
                   const float ps = pe[e] < 1.0f ? pe[e] : 1.0f;
-                  // bounds checks: a count/fill mismatch is recorded, never written out of range
-                  if (pos >= pend[r]) { A.ctrl->sketch_fault = 1; ++pos; continue; }
-                  A.col_idx[pos] = jj;
+                  // bounds checks: never written out of range.  FILL: a count/fill mismatch
+                  // (a fault); FUSED: the padded slot was too small (the two-pass sweep reruns).
+                  if (pos >= pend[r]) {
+                    if (MODE == SW_FUSED) A.ctrl->pad_overflow = 1;
+                    else A.ctrl->sketch_fault = 1;
+                    ++pos;
+                    continue;
+                  }
+                  cidx[pos] = jj;
                   if (lv32) {
                     // stabilised iterations: the absorption writes K' later; only log K~ = -C/eps - log p*
                     const float ce = cost_over_eps_df(pd.cv.x32 + (int64_t)i * d, pd.cv.y32 + (int64_t)jj * d, d,
                                                       k_hi, k_lo);
-                    A.logval[pos] = __fsub_rn(-ce, logf(ps));
+                    lvo[pos] = __fsub_rn(-ce, logf(ps));
                   } else {
                     const float Dd = UOT ? Dv[e] : raw32(pd.cv, i, jj);
                     val[pos] = from_d<V>(ValMath<V>::value(pd, sc, i, jj, Dd, ps));
-                    if (A.logval) {
+                    if (lvo) {
                       // log K~ = -C/eps - log p*, C from the FP64 distance of the points
                       const double C64 = raw64(pd.cv, i, jj) / sc.dn64;
-                      A.logval[pos] = (float)(-C64 / pd.eps - (double)logf(ps));
+                      lvo[pos] = (float)(-C64 / pd.eps - (double)logf(ps));
                     }
                   }
-                  const int slot = atomicAdd(&A.col_cur[jj], 1);
-                  if (slot < A.col_end[jj]) {
-                    A.tmp_row[slot] = i;
-                    A.tmp_src[slot] = pos;
-                  } else {
-                    A.ctrl->sketch_fault = 1;
+                  if (MODE == SW_FILL) {
+                    const int slot = atomicAdd(&A.col_cur[jj], 1);
+                    if (slot < A.col_end[jj]) {
+                      A.tmp_row[slot] = i;
+                      A.tmp_src[slot] = pos;
+                    } else {
+                      A.ctrl->sketch_fault = 1;
+                    }
                   }
                   ++pos;
                 }
@@ -237,12 +262,20 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
         }
       }
     }
-    if (MODE == SW_COUNT) {
+    if (MODE == SW_COUNT || MODE == SW_FUSED) {
 #pragma unroll
       for (int r = 0; r < kRW; ++r) {
         const int i = rb + warp * kRW + r;
         const int cs = warp_sum(cnt[r]);
         if (lane == 0 && i < n) A.cnt2[(size_t)c * n + i] = cs;
+      }
+    }
+    if (MODE == SW_Z && A.zsum) {
+#pragma unroll
+      for (int r = 0; r < kRW; ++r) {
+        const int i = rb + warp * kRW + r;
+        const float zs = warp_sum(zr[r]);
+        if (lane == 0 && i < n) A.zsum[(size_t)c * n + i] = zs;
       }
     }
   }
@@ -256,6 +289,113 @@ __global__ void k_sum_chunks(int n, int nchunk, const int* cnt2, int* row_cnt, c
     int s = 0;
     for (int c = 0; c < nchunk; ++c) s += cnt2[(size_t)c * n + i];
     row_cnt[i] = s;
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Single-pass sketch.  The expected number of kept elements of (row i, chunk
+// c) is bounded by mu = sum_j p_ij before clipping: OT r_i sum_{j in c} c_j,
+// UOT fl32(s/Z) sum_{j in c} w_ij (from the Z sweep).  A slot of
+// mu + 8 sqrt(mu) + 16 entries (at most the chunk's width) holds the pair's
+// elements unless the count lies ~8 standard deviations above its mean; then
+// the two-pass sweep runs instead, so the result never depends on the slots.
+// ---------------------------------------------------------------------------
+__global__ void k_chunk_csum(int m, int chunk, int nchunk, const float* colf, float* csum) {
+  __shared__ float sh[32];
+  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    const int j0 = c * chunk, j1 = min(m, j0 + chunk);
+    float s = 0.0f;
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) s += colf[j];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.0f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+      csum[c] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_pad_caps(int n, int m, int chunk, int nchunk, int uot, const float* rowf, const float* csum,
+                           const float* zsum, const SketchScalars* sc, int* caps) {
+  const float scale = sc->scale32;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < (long long)n * nchunk;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(k / nchunk), c = (int)(k % nchunk);
+    const float mu = uot ? scale * zsum[(size_t)c * n + i] : rowf[i] * csum[c];
+    const int width = min(m, (c + 1) * chunk) - c * chunk;
+    float cap = mu + 8.0f * sqrtf(fmaxf(mu, 0.0f)) + 16.0f;
+    if (!(cap < (float)width)) cap = (float)width;   // also catches NaN
+    caps[k] = (int)ceilf(cap);
+  }
+}
+
+// Exclusive scan of len counts into ofs[0 .. len] by one block; a total above
+// limit sets the overflow flag (the two-pass sweep then runs).
+__global__ void __launch_bounds__(1024) k_pad_scan(const int* caps, int* ofs, long long len, long long limit,
+                                                   Ctrl* ctrl) {
+  __shared__ long long sh[1024];
+  const int T = blockDim.x, t = threadIdx.x;
+  const long long per = (len + T - 1) / T;
+  const long long lo = min(len, (long long)t * per), hi = min(len, lo + per);
+  long long s = 0;
+  for (long long k = lo; k < hi; ++k) s += caps[k];
+  sh[t] = s;
+  __syncthreads();
+  for (int o = 1; o < T; o <<= 1) {
+    const long long v = t >= o ? sh[t - o] : 0;
+    __syncthreads();
+    sh[t] += v;
+    __syncthreads();
+  }
+  const long long total = sh[T - 1];
+  const bool over = total > limit;
+  if (over && t == 0) ctrl->pad_overflow = 1;
+  // offsets are always written (all zero when the slots do not fit), so that no
+  // kernel can read an undefined value; the fused sweep skips on the flag
+  long long run = sh[t] - s;
+  for (long long k = lo; k < hi; ++k) {
+    ofs[k] = over ? 0 : (int)run;
+    run += caps[k];
+  }
+  if (t == T - 1) ofs[len] = over ? 0 : (int)total;
+}
+
+// Copy every (row, chunk) slot to its CSR position (row_ptr[i] plus the earlier
+// chunks' counts: the positions of the two-pass fill) and scatter the CSC.
+template <typename V>
+__global__ void k_compact(int n, int nchunk, const int* pad_ofs, const int* cnt2, const int* row_ptr,
+                          const int* pad_col, const V* pad_val, const float* pad_lv, int* col_idx, V* val,
+                          float* logval, int* col_cur, const int* col_end, int* tmp_row, int* tmp_src, Ctrl* ctrl) {
+  // pad_val is null when the sweep formed only log K~ (the absorption writes K' later)
+  if (ctrl->status != SPS_OK || ctrl->pad_overflow) return;
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+    int dst = row_ptr[i];
+    const int end = row_ptr[i + 1];
+    for (int c = 0; c < nchunk; ++c) {
+      const int src = pad_ofs[(size_t)i * nchunk + c];
+      const int len = cnt2[(size_t)c * n + i];
+      for (int e = lane; e < len; e += 32) {
+        const int q = dst + e;
+        if (q >= end) { ctrl->sketch_fault = 1; continue; }
+        const int j = pad_col[src + e];
+        col_idx[q] = j;
+        if (pad_val) val[q] = pad_val[src + e];
+        if (pad_lv) logval[q] = pad_lv[src + e];
+        const int slot = atomicAdd(&col_cur[j], 1);
+        if (slot < col_end[j]) {
+          tmp_row[slot] = i;
+          tmp_src[slot] = q;
+        } else {
+          ctrl->sketch_fault = 1;
+        }
+      }
+      dst += len;
+    }
   }
 }
 
@@ -314,6 +454,7 @@ static SweepArgs base_args(const ProbDev& pd, const Layout& L, char* ws) {
 
 void launch_uot_Z(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st) {
   SweepArgs A = base_args(pd, L, ws);
+  A.zsum = L.zsum ? at<float>(ws, L.zsum) : nullptr;
   const SweepGeo g = sweep_geometry(pd.n, pd.m);
   launch_sweep<SW_Z, true, float>(A, dim3(g.row_blocks, g.nchunk), st);
 }
@@ -352,6 +493,65 @@ void launch_fill(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cud
     case SPS_F32: fill_v<float>(pd, L, ws, st); break;
     case SPS_BF16: fill_v<__nv_bfloat16>(pd, L, ws, st); break;
     case SPS_F16: fill_v<__half>(pd, L, ws, st); break;
+  }
+}
+
+template <typename V>
+static void fused_v(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st) {
+  SweepArgs A = base_args(pd, L, ws);
+  const SweepGeo g = sweep_geometry(pd.n, pd.m);
+  const long long len = (long long)pd.n * g.nchunk;
+  int* caps = at<int>(ws, L.pad_ofs) + len + 1;   // scratch after the offsets
+  if (pd.is_ot)
+    k_chunk_csum<<<std::min(g.nchunk, 1024), 256, 0, st>>>(pd.m, g.chunk, g.nchunk, A.colf, at<float>(ws, L.csum));
+  const int gc = (int)std::max<long long>(1, std::min<long long>(4096, (len + 255) / 256));
+  k_pad_caps<<<gc, 256, 0, st>>>(pd.n, pd.m, g.chunk, g.nchunk, pd.is_ot ? 0 : 1, A.rowf, at<float>(ws, L.csum),
+                                 L.zsum ? at<float>(ws, L.zsum) : nullptr, A.sc, caps);
+  k_pad_scan<<<1, 1024, 0, st>>>(caps, at<int>(ws, L.pad_ofs), len, (long long)L.pad_cap, A.ctrl);
+  A.col_cnt = at<int>(ws, L.col_cnt);
+  A.pad_ofs = at<int>(ws, L.pad_ofs);
+  A.pad_col = at<int>(ws, L.pad_col);
+  A.pad_val = ws + L.pad_val;
+  A.pad_lv = L.pad_lv ? at<float>(ws, L.pad_lv) : nullptr;
+  const dim3 grid(g.row_blocks, g.nchunk);
+  if (pd.is_ot) launch_sweep<SW_FUSED, false, V>(A, grid, st);
+  else launch_sweep<SW_FUSED, true, V>(A, grid, st);
+}
+
+void launch_fused(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st) {
+  switch (kd) {
+    case SPS_F64: fused_v<double>(pd, L, ws, st); break;
+    case SPS_F32: fused_v<float>(pd, L, ws, st); break;
+    case SPS_BF16: fused_v<__nv_bfloat16>(pd, L, ws, st); break;
+    case SPS_F16: fused_v<__half>(pd, L, ws, st); break;
+  }
+}
+
+template <typename V>
+static void compact_v(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st) {
+  const SweepGeo g = sweep_geometry(pd.n, pd.m);
+  const int gb = std::max(1, std::min(152 * 32, (pd.n * 32 + 255) / 256));
+  // the same condition as the sweep's binary32 log K~ (then no plain values were written)
+  const bool lv32 = L.pad_lv && !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64;
+  k_compact<V><<<gb, 256, 0, st>>>(pd.n, g.nchunk, at<int>(ws, L.pad_ofs), at<int>(ws, L.cnt2), at<int>(ws, L.row_ptr),
+                                   at<int>(ws, L.pad_col), lv32 ? nullptr : at<V>(ws, L.pad_val),
+                                   L.pad_lv ? at<float>(ws, L.pad_lv) : nullptr, at<int>(ws, L.col_idx),
+                                   at<V>(ws, L.val), L.logval ? at<float>(ws, L.logval) : nullptr,
+                                   at<int>(ws, L.col_cur), at<int>(ws, L.col_ptr) + 1, at<int>(ws, L.tmp_row),
+                                   at<int>(ws, L.tmp_src), at<Ctrl>(ws, L.ctrl));
+}
+
+void launch_sum_chunks(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st) {
+  k_sum_chunks<<<std::max(1, std::min(1216, (pd.n + 255) / 256)), 256, 0, st>>>(
+      pd.n, sweep_geometry(pd.n, pd.m).nchunk, at<int>(ws, L.cnt2), at<int>(ws, L.row_cnt), at<Ctrl>(ws, L.ctrl));
+}
+
+void launch_compact(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st) {
+  switch (kd) {
+    case SPS_F64: compact_v<double>(pd, L, ws, st); break;
+    case SPS_F32: compact_v<float>(pd, L, ws, st); break;
+    case SPS_BF16: compact_v<__nv_bfloat16>(pd, L, ws, st); break;
+    case SPS_F16: compact_v<__half>(pd, L, ws, st); break;
   }
 }
 

@@ -205,3 +205,32 @@ def test_full_size_uot_rows_bit_exact(S, orc):
         assert np.allclose(vals[rp[i]:rp[i + 1]], r["val"], rtol=2e-6)
     # nnz is consistent with E nnz = sum p* <= s
     assert abs(g["nnz"] - w.s) < 6 * math.sqrt(w.s)
+
+
+@pytest.mark.parametrize("lam,n,m,kd", [(math.inf, 3000, 2500, "f32"), (1.0, 3000, 2800, "f32"),
+                                          (math.inf, 20000, 20000, "bf16"), (1.0, 900, 700, "f64")])
+def test_single_pass_sketch_equals_two_pass(S, lam, n, m, kd):
+    """The single-pass sketch (padded slots, then compaction) gives the
+    two-pass sketch bit for bit: CSR, CSC, values and the CSR positions."""
+    w = inputs.small_problem(n=n, m=m, d=3, seed=91, eps=0.1, mass_b=1.0 if math.isinf(lam) else 1.5)
+    x, y, a, b = _round32(w)
+    kw = dict(eps=0.1, s=w.s, lam=lam, dtype="f64" if kd == "f64" else "f32", kdtype=kd, seed=17)
+    one = S.sparsify_kernel(a, b, x, y, sketch_mode=0, **kw)
+    two = S.sparsify_kernel(a, b, x, y, sketch_mode=1, **kw)
+    assert one["nnz"] == two["nnz"]
+    for k in ("row_ptr", "col_idx", "col_ptr", "row_idx", "csr_pos"):
+        assert torch.equal(one[k], two[k]), k
+    assert torch.equal(one["val"].view(torch.uint8), two["val"].view(torch.uint8))
+    assert torch.equal(one["valT"].view(torch.uint8), two["valT"].view(torch.uint8))
+
+
+@pytest.mark.parametrize("lam", [math.inf, 1.0])
+def test_single_pass_log_domain_solve_equals_two_pass(S, lam):
+    w = inputs.small_problem(n=2500, m=2200, d=3, seed=92, eps=0.01, mass_b=1.0 if math.isinf(lam) else 1.5)
+    x, y, a, b = _round32(w)
+    f = S.spar_sink_ot if math.isinf(lam) else (lambda *z, **k: S.spar_sink_uot(*z, lam=lam, **k))
+    kw = dict(eps=0.01, s=w.s, tol=1e-5, max_iter=5000, dtype="f32", seed=3, log_domain=1)
+    r1 = f(a, b, x, y, sketch_mode=0, **kw)
+    r2 = f(a, b, x, y, sketch_mode=1, **kw)
+    assert r1["nnz"] == r2["nnz"] and r1["iters"] == r2["iters"] and r1["obj"] == r2["obj"]
+    assert torch.equal(r1["alpha"], r2["alpha"])
