@@ -53,6 +53,7 @@ template <typename Take>
 static void plan_staging(int n, int m, int mode, Layout* L, Take& take) {
   if (mode == SPS_GATHER_DIRECT) return;
   if (mode == SPS_GATHER_AUTO && (n < kStageMin || m < kStageMin)) return;
+  if (L->cap <= 0) return;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       nsm < 1) {
@@ -60,9 +61,9 @@ static void plan_staging(int n, int m, int mode, Layout* L, Take& take) {
     return;
   }
   const int big = std::max(n, m);
-  const size_t acc = (size_t)((big + nsm - 1) / nsm);
-  if (acc * 4 + 8192 * 4 > kStageSmem) return;
-  const int wcap = std::min<int>(kStageWMax, (int)(((kStageSmem - acc * 4) / 4) / 1024 * 1024));
+  const size_t acc = (size_t)((big + nsm - 1) / nsm);   // row sums and segment bounds of one block
+  if (acc * 8 + 16 + 8192 * 4 > kStageSmem) return;
+  const int wcap = std::min<int>(kStageWMax, (int)(((kStageSmem - acc * 8 - 16) / 4) / 1024 * 1024));
   int J = (big + wcap - 1) / wcap;
   if (mode == SPS_GATHER_STAGED) J = std::max(J, std::min(4, (big + 1023) / 1024));   // forced: several chunks
   const int W = (int)(((big + J - 1) / J + 1023) / 1024 * 1024);
@@ -72,6 +73,15 @@ static void plan_staging(int n, int m, int mode, Layout* L, Take& take) {
   L->stage_nsm = nsm;
   L->seg_r = take((size_t)(L->stage_jr + 1) * n * 4);
   L->seg_c = take((size_t)(L->stage_jc + 1) * m * 4);
+  L->cm_ofs_r = take((size_t)L->stage_jr * (n + 1) * 4);
+  L->cm_ofs_c = take((size_t)L->stage_jc * (m + 1) * 4);
+  L->cm_base_r = take((size_t)(L->stage_jr + 1) * 4);
+  L->cm_base_c = take((size_t)(L->stage_jc + 1) * 4);
+  // + 8 entries: the streaming pass reads whole aligned groups of 8 past the last element
+  L->cm_idx_r = take(((size_t)L->cap + 8) * 4);
+  L->cm_idx_c = take(((size_t)L->cap + 8) * 4);
+  L->cm_perm_r = take((size_t)L->cap * 4);
+  L->cm_perm_c = take((size_t)L->cap * 4);
 }
 
 bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
@@ -112,9 +122,9 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
     L->col_cur = take((size_t)m * 4);
     L->cnt2 = take((size_t)sweep_geometry(n, m).nchunk * n * 4);
     L->col_idx = take((size_t)cap * 4);
-    L->val = take((size_t)cap * vb);
+    L->val = take(((size_t)cap + 8) * vb);   // + 8: staged passes read aligned groups of 8
     L->row_idx = take((size_t)cap * 4);
-    L->valT = take((size_t)cap * vb);
+    L->valT = take(((size_t)cap + 8) * vb);
     L->csr_pos = take((size_t)cap * 4);
     L->tmp_row = take((size_t)cap * 4);
     L->tmp_src = take((size_t)cap * 4);
@@ -420,6 +430,11 @@ static sps_status spar_sink_impl(const sps_problem* P, const sps_params* Q, void
   if (res) *res = r;
   if (r.status == SPS_ERR_NUMERIC) set_error("non-finite value in the iterates");
   if (h.wait_timeout) set_error("a device-side grid barrier of the iteration kernel timed out");
+  if (h.oob_code) {
+    set_error("a device-side bounds check refused an access (place %d, index %lld)", h.oob_code, h.oob_index);
+    if (res) res->status = SPS_ERR_CUDA;
+    return SPS_ERR_CUDA;
+  }
   return (sps_status)r.status;
 }
 

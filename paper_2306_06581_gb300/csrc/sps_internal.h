@@ -41,6 +41,8 @@ struct Ctrl {
   int wait_timeout;       // a bounded device wait gave up
   int sketch_fault;       // fill disagreed with count (write skipped instead of out of range)
   int pad_overflow;       // single-pass sketch: a padded (row, chunk) slot was too small
+  int oob_code;           // a bounds check skipped an access (code of the place; 0: none)
+  long long oob_index;    //   and the index it refused
 };
 
 // Scalars of the sampling decision, computed on the device.
@@ -79,6 +81,10 @@ struct Layout {
   size_t logval, logvalT;           // log-domain: log K~ in CSR / CSC order (binary32)
   size_t bhat, erow, ecol, pot_a, pot_b;
   size_t seg_r, seg_c;              // staged gathers: chunk pointers of the CSR rows / CSC columns
+  size_t cm_ofs_r, cm_ofs_c;        // staged gathers: chunk-major offsets [J][n+1] (chunk-local) and
+  size_t cm_base_r, cm_base_c;      //   chunk bases [J+1]
+  size_t cm_idx_r, cm_idx_c;        //   indices in chunk-major order (K' values are stored in that order)
+  size_t cm_perm_r, cm_perm_c;      //   row-major position -> chunk-major position
   size_t pad_ofs, pad_col, pad_val, pad_lv, zsum, csum;   // single-pass sketch (0: two passes)
   int64_t pad_cap;
   int stage_w, stage_jr, stage_jc;  // staged gathers: chunk width, chunks over columns / rows (0: off)

@@ -58,9 +58,19 @@ struct LogArgs {
   // position of row i with column >= c W (c = 0 .. Jr), seg_c likewise for CSC.
   int stage, W, Jr, Jc, rows_pb, cols_pb;
   const int *seg_r, *seg_c;
+  // chunk-major copies for the staged passes: the elements of chunk c are
+  // cm_base[c] + [cm_ofs[c (n+1) + i], cm_ofs[c (n+1) + i + 1]) for row i; K'
+  // (val / valT) is stored in this order and perm maps row-major positions to it
+  const int *cm_ofs_r, *cm_ofs_c, *cm_base_r, *cm_base_c, *cm_idx_r, *cm_idx_c, *cm_perm_r, *cm_perm_c;
+  long long nnz_lim;   // elements the chunk-major arrays hold (bounds checks)
 };
 
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
+
+// A refused access: record where (first one wins) and skip it.
+__device__ __forceinline__ void oob(Ctrl* ctrl, int code, long long index) {
+  if (atomicCAS(&ctrl->oob_code, 0, code) == 0) ctrl->oob_index = index;
+}
 
 // log-sum-exp over one row (or column) by a whole warp: max, then sum.
 __device__ __forceinline__ float warp_lse(const int* idx, const float* logv, const float* pot, float inv_eps,
@@ -94,7 +104,9 @@ __global__ void __launch_bounds__(kT) k_lse_half(int rows, const int* ptr, const
 // scaled by 2^-e, e = floor(log2 of the largest value).
 template <typename V>
 __device__ __forceinline__ void absorb_segment(int lo, int hi, const int* idx, const float* logv, float pot_i,
-                                               const float* other, float inv_eps, V* out, float* e_out, int lane) {
+                                               const float* other, float inv_eps, V* out, float* e_out, int lane,
+                                               const int* perm = nullptr, long long limit = 0,
+                                               Ctrl* ctrl = nullptr) {
   float mx = neg_inf();
   if (pot_i != neg_inf())
     for (int k = lo + lane; k < hi; k += 32) {
@@ -107,7 +119,9 @@ __device__ __forceinline__ void absorb_segment(int lo, int hi, const int* idx, c
     const float o = other[idx[k]];
     float z = neg_inf();
     if (pot_i != neg_inf() && o != neg_inf()) z = logv[k] + (pot_i + o) * inv_eps;
-    out[k] = from_d<V>((double)exp2f(z * kLog2e - e));
+    const int dst = perm ? perm[k] : k;
+    if (perm && (dst < 0 || (long long)dst >= limit)) { oob(ctrl, 1, dst); continue; }
+    out[dst] = from_d<V>((double)exp2f(z * kLog2e - e));
   }
   if (lane == 0) *e_out = e;
 }
@@ -119,10 +133,10 @@ __global__ void __launch_bounds__(kT) k_absorb_all(LogArgs A, int t) {
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int i = gw; i < A.n; i += nw)
     absorb_segment<V>(A.row_ptr[i], A.row_ptr[i + 1], A.col_idx, A.logval, A.alpha[i], A.beta, A.inv_eps,
-                      (V*)A.val, A.erow + i, lane);
+                      (V*)A.val, A.erow + i, lane, A.cm_perm_r, A.nnz_lim, A.ctrl);
   for (int j = gw; j < A.m; j += nw)
     absorb_segment<V>(A.col_ptr[j], A.col_ptr[j + 1], A.row_idx, A.logvalT, A.beta[j], A.alpha, A.inv_eps,
-                      (V*)A.valT, A.ecol + j, lane);
+                      (V*)A.valT, A.ecol + j, lane, A.cm_perm_c, A.nnz_lim, A.ctrl);
   // scalings of the pair t: 1 where the potential is finite, 0 where the row / column is unreachable
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
   float* u = A.ubuf + (size_t)(t & 1) * A.n;
@@ -253,17 +267,46 @@ __device__ __forceinline__ void log_col_phase(const LogArgs& A, int t, float (&o
   o[0] = s1[0];
 }
 
+// Eight consecutive values from an 8-aligned position (one or two 128-bit loads).
+template <typename V> __device__ __forceinline__ void load8(const V* p, float (&o)[8]);
+template <> __device__ __forceinline__ void load8<float>(const float* p, float (&o)[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+template <> __device__ __forceinline__ void load8<__nv_bfloat16>(const __nv_bfloat16* p, float (&o)[8]) {
+  const uint4 q = *reinterpret_cast<const uint4*>(p);
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    o[2 * k] = __uint_as_float(w[k] << 16);
+    o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+  }
+}
+template <> __device__ __forceinline__ void load8<__half>(const __half* p, float (&o)[8]) {
+  const uint4 q = *reinterpret_cast<const uint4*>(p);
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
+    o[2 * k] = f.x;
+    o[2 * k + 1] = f.y;
+  }
+}
+
 // The sparse products of one block's rows [r0, r0 + nr) with x staged in
-// shared memory chunk by chunk (J chunks of W entries of x, x of length nx):
-// acc[k] += sum over the elements of row r0 + k whose column lies in the chunk.
-// seg[c * ldseg + i] is the first position of row i in chunk c.
-template <int LPR, typename V>
-__device__ __forceinline__ void staged_pass(const int* __restrict__ idx, const V* val, const float* x, int nx,
-                                            const int* __restrict__ seg, int ldseg, int r0, int nr, int W, int J,
-                                            float* xs, float* acc) {
-  constexpr int RPW = 32 / LPR;
-  const int lane = threadIdx.x & 31, sl = lane & (LPR - 1);
-  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
+// shared memory chunk by chunk (J chunks of W entries of x, x of length nx),
+// over the chunk-major copy: the block's elements of chunk c are one
+// contiguous range, streamed as aligned groups of 8 per thread with the next
+// group loaded before the current one is used.  A thread finds the row of its
+// first element by binary search over the block's segment bounds (staged in
+// shared memory) and adds each row's partial product to acc with a shared
+// atomic, so the order of the additions within a row is not fixed.
+template <typename V>
+__device__ __forceinline__ void staged_pass_cm(const int* __restrict__ idx, const V* val, const float* x, int nx,
+                                               const int* __restrict__ ofs, const int* __restrict__ base, int ld,
+                                               int r0, int nr, int W, int J, float* xs, float* acc, int* segs,
+                                               long long limit, Ctrl* ctrl) {
+  const int T = blockDim.x, t = threadIdx.x;
   for (int c = 0; c < J; ++c) {
     const int j0 = c * W;
     const int jn = min(W, nx - j0);
@@ -271,32 +314,132 @@ __device__ __forceinline__ void staged_pass(const int* __restrict__ idx, const V
     if ((((uintptr_t)(x + j0)) & 15) == 0) {
       const int n4 = jn >> 2;
       const float4* src = reinterpret_cast<const float4*>(x + j0);
-      for (int k = threadIdx.x; k < n4; k += blockDim.x) reinterpret_cast<float4*>(xs)[k] = __ldcg(src + k);
-      for (int k = 4 * n4 + threadIdx.x; k < jn; k += blockDim.x) xs[k] = __ldcg(x + j0 + k);
+      for (int k = t; k < n4; k += T) reinterpret_cast<float4*>(xs)[k] = __ldcg(src + k);
+      for (int k = 4 * n4 + t; k < jn; k += T) xs[k] = __ldcg(x + j0 + k);
     } else {
-      for (int k = threadIdx.x; k < jn; k += blockDim.x) xs[k] = __ldcg(x + j0 + k);
+      for (int k = t; k < jn; k += T) xs[k] = __ldcg(x + j0 + k);
     }
+    const int bc = base[c];
+    // a block past the last row (r0 >= rows) owns nothing and reads no bounds
+    if (nr > 0)
+      for (int k = t; k <= nr; k += T) segs[k] = bc + ofs[(size_t)c * ld + r0 + k];
+    else if (t == 0)
+      segs[0] = 0;
     __syncthreads();
-    const int* s0 = seg + (size_t)c * ldseg + r0;
-    const int* s1 = seg + (size_t)(c + 1) * ldseg + r0;
-    // each warp owns a contiguous share of the rows; the segment bounds of 32
-    // rows arrive in one coalesced load and are handed out by shuffles
-    const int q = (nr + nw - 1) / nw;
-    const int wb = warp * q, we = min(nr, wb + q);
-    for (int g = wb; g < we; g += 32) {
-      const int gl = min(32, we - g);
-      const int lo_l = lane < gl ? __ldg(s0 + g + lane) : 0;
-      const int hi_l = lane < gl ? __ldg(s1 + g + lane) : 0;
-      for (int sub = 0; sub < gl; sub += RPW) {
-        const int rl = sub + lane / LPR;
-        const int lo = __shfl_sync(0xffffffffu, lo_l, rl & 31), hi = __shfl_sync(0xffffffffu, hi_l, rl & 31);
-        const bool ok = rl < gl;
-        const float dot = seg_dot_smem<LPR, V>(idx, val, xs, j0, jn, ok ? lo : 0, ok ? hi : 0, sl);
-        if (ok && sl == 0) acc[g + rl] += dot;
+    int E0 = segs[0], E1 = segs[nr];
+    if (E0 < 0 || E1 < E0 || (long long)E1 > limit) {   // inconsistent bounds: skip the chunk
+      if (t == 0) oob(ctrl, 2, E1);
+      E1 = E0 = 0;
+    }
+    int w = (E0 & ~7) + 8 * t;
+    int id[8];
+    float vv[8];
+    if (w < E1) {
+      const int4 a = __ldg(reinterpret_cast<const int4*>(idx + w)), b = __ldg(reinterpret_cast<const int4*>(idx + w + 4));
+      id[0] = a.x; id[1] = a.y; id[2] = a.z; id[3] = a.w; id[4] = b.x; id[5] = b.y; id[6] = b.z; id[7] = b.w;
+      load8<V>(val + w, vv);
+    }
+    for (; w < E1; w += 8 * T) {
+      const int wn = w + 8 * T;
+      int idn[8];
+      float vn[8];
+      if (wn < E1) {
+        const int4 a = __ldg(reinterpret_cast<const int4*>(idx + wn));
+        const int4 b = __ldg(reinterpret_cast<const int4*>(idx + wn + 4));
+        idn[0] = a.x; idn[1] = a.y; idn[2] = a.z; idn[3] = a.w; idn[4] = b.x; idn[5] = b.y; idn[6] = b.z; idn[7] = b.w;
+        load8<V>(val + wn, vn);
       }
+      const int u0 = max(0, E0 - w), u1 = min(8, E1 - w);
+      if (u0 < u1) {
+        // row of element w + u0: the largest k with segs[k] <= w + u0 (empty rows share bounds)
+        const int g0 = w + u0;
+        int lo = 0, hi = nr - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (segs[mid] <= g0) lo = mid; else hi = mid - 1;
+        }
+        int k = lo, kend = segs[lo + 1];
+        float s = 0.0f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (u >= u0 && u < u1) {
+            while (w + u >= kend) {   // next row (at most nr - 1 steps in all)
+              atomicAdd(&acc[k], s);
+              s = 0.0f;
+              ++k;
+              kend = segs[k + 1];
+            }
+            const int q = id[u] - j0;
+            if ((unsigned)q < (unsigned)jn) s = fmaf(vv[u], xs[q], s);
+          }
+        }
+        atomicAdd(&acc[k], s);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { id[u] = idn[u]; vv[u] = vn[u]; }
     }
   }
   __syncthreads();
+}
+
+// Chunk-major copies (built once after the sketch).  ofs[c (rows+1) + i] is
+// the chunk-local start of segment i in chunk c; base[c] the chunk's start.
+__global__ void __launch_bounds__(1024) k_cm_scan(int rows, const int* seg, int J, int* ofs) {
+  __shared__ long long sh[1024];
+  const int c = blockIdx.x;
+  if (c >= J) return;
+  const int T = blockDim.x, t = threadIdx.x;
+  const int per = (rows + T - 1) / T;
+  const int lo = min(rows, t * per), hi = min(rows, lo + per);
+  const int* s0 = seg + (size_t)c * rows;
+  const int* s1 = seg + (size_t)(c + 1) * rows;
+  long long s = 0;
+  for (int i = lo; i < hi; ++i) s += s1[i] - s0[i];
+  sh[t] = s;
+  __syncthreads();
+  for (int o = 1; o < T; o <<= 1) {
+    const long long v = t >= o ? sh[t - o] : 0;
+    __syncthreads();
+    sh[t] += v;
+    __syncthreads();
+  }
+  long long run = sh[t] - s;
+  int* out = ofs + (size_t)c * (rows + 1);
+  for (int i = lo; i < hi; ++i) {
+    out[i] = (int)run;
+    run += s1[i] - s0[i];
+  }
+  if (t == T - 1) out[rows] = (int)sh[T - 1];
+}
+
+__global__ void k_cm_base(int rows, int J, const int* ofs, int* base) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int b = 0;
+  for (int c = 0; c < J; ++c) {
+    base[c] = b;
+    b += ofs[(size_t)c * (rows + 1) + rows];
+  }
+  base[J] = b;
+}
+
+__global__ void k_cm_copy(int rows, const int* seg, int J, const int* ofs, const int* base, const int* idx,
+                          int* cm_idx, int* perm, long long limit, Ctrl* ctrl) {
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += (gridDim.x * blockDim.x) >> 5) {
+    for (int c = 0; c < J; ++c) {
+      const int src = seg[(size_t)c * rows + i];
+      const int len = seg[(size_t)(c + 1) * rows + i] - src;
+      const int dst = base[c] + ofs[(size_t)c * (rows + 1) + i];
+      for (int e = lane; e < len; e += 32) {
+        if (src + e < 0 || (long long)(src + e) >= limit || dst + e < 0 || (long long)(dst + e) >= limit) {
+          oob(ctrl, 3, (long long)dst + e);
+          continue;
+        }
+        cm_idx[dst + e] = idx[src + e];
+        perm[src + e] = dst + e;
+      }
+    }
+  }
 }
 
 // Staged row pass: v passes through shared memory chunk by chunk; the partial
@@ -309,8 +452,10 @@ __device__ __forceinline__ void log_row_phase_staged(const LogArgs& A, int t, fl
   const int r0 = blockIdx.x * A.rows_pb;
   const int nr = max(0, min(A.n, r0 + A.rows_pb) - r0);
   float* acc = dsm + A.W;
+  int* segs = reinterpret_cast<int*>(acc + max(A.rows_pb, A.cols_pb));
   for (int k = threadIdx.x; k < nr; k += blockDim.x) acc[k] = 0.0f;
-  staged_pass<LPR, V>(A.col_idx, (const V*)A.val, v, A.m, A.seg_r, A.n, r0, nr, A.W, A.Jr, dsm, acc);
+  staged_pass_cm<V>(A.cm_idx_r, (const V*)A.val, v, A.m, A.cm_ofs_r, A.cm_base_r, A.n + 1, r0, nr, A.W, A.Jr, dsm, acc,
+                    segs, A.nnz_lim, A.ctrl);
   float res = 0.0f, unr = 0.0f, mlog = 0.0f;
   for (int k = threadIdx.x; k < nr; k += blockDim.x) {
     const int i = r0 + k;
@@ -328,8 +473,10 @@ __device__ __forceinline__ void log_col_phase_staged(const LogArgs& A, int t, fl
   const int c0 = blockIdx.x * A.cols_pb;
   const int nc = max(0, min(A.m, c0 + A.cols_pb) - c0);
   float* acc = dsm + A.W;
+  int* segs = reinterpret_cast<int*>(acc + max(A.rows_pb, A.cols_pb));
   for (int k = threadIdx.x; k < nc; k += blockDim.x) acc[k] = 0.0f;
-  staged_pass<LPR, V>(A.row_idx, (const V*)A.valT, u, A.n, A.seg_c, A.m, c0, nc, A.W, A.Jc, dsm, acc);
+  staged_pass_cm<V>(A.cm_idx_c, (const V*)A.valT, u, A.n, A.cm_ofs_c, A.cm_base_c, A.m + 1, c0, nc, A.W, A.Jc, dsm,
+                    acc, segs, A.nnz_lim, A.ctrl);
   float unb = 0.0f, mlog = 0.0f;
   for (int k = threadIdx.x; k < nc; k += blockDim.x) {
     const int j = c0 + k;
@@ -397,10 +544,10 @@ __device__ __forceinline__ void rewrite_block(const LogArgs& A) {
   const int tw = gridDim.x * nw;
   for (int i = gw; i < A.n; i += tw)
     absorb_segment<V>(A.row_ptr[i], A.row_ptr[i + 1], A.col_idx, A.logval, A.alpha[i], A.beta, A.inv_eps,
-                      (V*)A.val, A.erow + i, lane);
+                      (V*)A.val, A.erow + i, lane, A.cm_perm_r, A.nnz_lim, A.ctrl);
   for (int j = gw; j < A.m; j += tw)
     absorb_segment<V>(A.col_ptr[j], A.col_ptr[j + 1], A.row_idx, A.logvalT, A.beta[j], A.alpha, A.inv_eps,
-                      (V*)A.valT, A.ecol + j, lane);
+                      (V*)A.valT, A.ecol + j, lane, A.cm_perm_c, A.nnz_lim, A.ctrl);
 }
 
 // Persistent stabilised iterations.  Partial slots: 0 residual, 1 unreachable
@@ -504,7 +651,7 @@ bool coop_log(LogArgs A, int iters, int row_only, cudaStream_t st) {
   size_t smem = 0;
   if (STG) {
     // one block per SM owns a fixed row range and column range
-    smem = sizeof(float) * ((size_t)A.W + (size_t)std::max(A.rows_pb, A.cols_pb));
+    smem = sizeof(float) * ((size_t)A.W + 2 * (size_t)std::max(A.rows_pb, A.cols_pb) + 1);
     if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       cudaGetLastError();
       return false;
@@ -573,6 +720,15 @@ LogArgs make_log_args(const ProbDev& pd, const Layout& L, char* ws, const IterCf
   A.cols_pb = L.stage_nsm > 0 ? (pd.m + L.stage_nsm - 1) / L.stage_nsm : 0;
   A.seg_r = A.stage ? at<int>(ws, L.seg_r) : nullptr;
   A.seg_c = A.stage ? at<int>(ws, L.seg_c) : nullptr;
+  A.cm_ofs_r = A.stage ? at<int>(ws, L.cm_ofs_r) : nullptr;
+  A.cm_ofs_c = A.stage ? at<int>(ws, L.cm_ofs_c) : nullptr;
+  A.cm_base_r = A.stage ? at<int>(ws, L.cm_base_r) : nullptr;
+  A.cm_base_c = A.stage ? at<int>(ws, L.cm_base_c) : nullptr;
+  A.cm_idx_r = A.stage ? at<int>(ws, L.cm_idx_r) : nullptr;
+  A.cm_idx_c = A.stage ? at<int>(ws, L.cm_idx_c) : nullptr;
+  A.cm_perm_r = A.stage ? at<int>(ws, L.cm_perm_r) : nullptr;
+  A.cm_perm_c = A.stage ? at<int>(ws, L.cm_perm_c) : nullptr;
+  A.nnz_lim = L.cap;
   return A;
 }
 
@@ -698,11 +854,20 @@ void first_iteration_v(const LogArgs& A, const IterCfg& ic, const void* al0, con
                                                          A.alpha, A.eps, A.phi);
   k_lse_half<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.col_ptr, A.row_idx, A.logvalT, A.alpha, A.b,
                                                          A.beta, A.eps, A.phi);
-  k_absorb_all<V><<<grid1((int64_t)std::max(A.n, A.m) * 32, kT), kT, 0, st>>>(A, 1);
   if (A.stage) {
+    // segment pointers and chunk-major copies (the absorption below writes K' through perm)
     k_chunk_ptrs<<<grid1((int64_t)A.n * 32, kT), kT, 0, st>>>(A.n, A.row_ptr, A.col_idx, A.W, A.Jr, (int*)A.seg_r);
     k_chunk_ptrs<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.col_ptr, A.row_idx, A.W, A.Jc, (int*)A.seg_c);
+    k_cm_scan<<<A.Jr, 1024, 0, st>>>(A.n, A.seg_r, A.Jr, (int*)A.cm_ofs_r);
+    k_cm_scan<<<A.Jc, 1024, 0, st>>>(A.m, A.seg_c, A.Jc, (int*)A.cm_ofs_c);
+    k_cm_base<<<1, 32, 0, st>>>(A.n, A.Jr, A.cm_ofs_r, (int*)A.cm_base_r);
+    k_cm_base<<<1, 32, 0, st>>>(A.m, A.Jc, A.cm_ofs_c, (int*)A.cm_base_c);
+    k_cm_copy<<<grid1((int64_t)A.n * 32, kT), kT, 0, st>>>(A.n, A.seg_r, A.Jr, A.cm_ofs_r, A.cm_base_r, A.col_idx,
+                                                          (int*)A.cm_idx_r, (int*)A.cm_perm_r, A.nnz_lim, A.ctrl);
+    k_cm_copy<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.seg_c, A.Jc, A.cm_ofs_c, A.cm_base_c, A.row_idx,
+                                                          (int*)A.cm_idx_c, (int*)A.cm_perm_c, A.nnz_lim, A.ctrl);
   }
+  k_absorb_all<V><<<grid1((int64_t)std::max(A.n, A.m) * 32, kT), kT, 0, st>>>(A, 1);
   (void)ic;
 }
 
@@ -716,7 +881,7 @@ sps_status launch_log_first_iteration(const ProbDev& pd, const Layout& L, char* 
     case SPS_F16: first_iteration_v<__half>(A, ic, init_alpha, init_beta, st); break;
     default: first_iteration_v<float>(A, ic, init_alpha, init_beta, st); break;
   }
-  add_launches(A.stage ? 6 : 4);
+  add_launches(A.stage ? 12 : 4);
   return cuda_fail(cudaGetLastError(), "log-domain first iteration");
 }
 
