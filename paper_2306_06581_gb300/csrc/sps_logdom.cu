@@ -301,6 +301,61 @@ template <> __device__ __forceinline__ void load8<__half>(const __half* p, float
 // first element by binary search over the block's segment bounds (staged in
 // shared memory) and adds each row's partial product to acc with a shared
 // atomic, so the order of the additions within a row is not fixed.
+// 16-byte asynchronous copy global -> shared through L2 (cp.async.cg), and the
+// wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void load8i(const int* p, int (&o)[8]) {
+  const int4 a = __ldg(reinterpret_cast<const int4*>(p)), b = __ldg(reinterpret_cast<const int4*>(p + 4));
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+
+// One aligned group of 8 elements starting at w: the products of those inside
+// [E0, E1) added to their rows' sums.
+__device__ __forceinline__ void group8(int w, int E0, int E1, const int (&id)[8], const float (&vv)[8], int j0, int jn,
+                                       const float* xs, const int* segs, int nr, float* acc) {
+  const int u0 = max(0, E0 - w), u1 = min(8, E1 - w);
+  if (u0 >= u1) return;
+  // row of element w + u0: the largest k with segs[k] <= w + u0 (empty rows share bounds)
+  const int g0 = w + u0;
+  int lo = 0, hi = nr - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid] <= g0) lo = mid; else hi = mid - 1;
+  }
+  int k = lo, kend = segs[lo + 1];
+  float s = 0.0f;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    if (u >= u0 && u < u1) {
+      while (w + u >= kend) {   // next row (at most nr - 1 steps in all)
+        atomicAdd(&acc[k], s);
+        s = 0.0f;
+        ++k;
+        kend = segs[k + 1];
+      }
+      const int q = id[u] - j0;
+      if ((unsigned)q < (unsigned)jn) s = fmaf(vv[u], xs[q], s);
+    }
+  }
+  atomicAdd(&acc[k], s);
+}
+
+// The sparse products of one block's rows [r0, r0 + nr) with x staged in
+// shared memory chunk by chunk (J chunks of W entries of x, x of length nx),
+// over the chunk-major copy: the block's elements of chunk c are one
+// contiguous range, streamed as aligned groups of 8 per thread, two groups in
+// registers that take turns (one is used while the other loads, with no copy
+// between them).  A thread finds the row of a group's first element by binary
+// search over the block's segment bounds (staged in shared memory) and adds
+// each row's partial product to acc with a shared atomic, so the order of the
+// additions within a row is not fixed.  The chunk of x arrives by cp.async.
 template <typename V>
 __device__ __forceinline__ void staged_pass_cm(const int* __restrict__ idx, const V* val, const float* x, int nx,
                                                const int* __restrict__ ofs, const int* __restrict__ base, int ld,
@@ -313,8 +368,7 @@ __device__ __forceinline__ void staged_pass_cm(const int* __restrict__ idx, cons
     __syncthreads();   // the previous chunk is no longer read (and acc is initialised)
     if ((((uintptr_t)(x + j0)) & 15) == 0) {
       const int n4 = jn >> 2;
-      const float4* src = reinterpret_cast<const float4*>(x + j0);
-      for (int k = t; k < n4; k += T) reinterpret_cast<float4*>(xs)[k] = __ldcg(src + k);
+      for (int k = t; k < n4; k += T) cp_async16(xs + 4 * k, x + j0 + 4 * k);
       for (int k = 4 * n4 + t; k < jn; k += T) xs[k] = __ldcg(x + j0 + k);
     } else {
       for (int k = t; k < jn; k += T) xs[k] = __ldcg(x + j0 + k);
@@ -325,58 +379,26 @@ __device__ __forceinline__ void staged_pass_cm(const int* __restrict__ idx, cons
       for (int k = t; k <= nr; k += T) segs[k] = bc + ofs[(size_t)c * ld + r0 + k];
     else if (t == 0)
       segs[0] = 0;
+    cp_async_wait_all();
     __syncthreads();
     int E0 = segs[0], E1 = segs[nr];
     if (E0 < 0 || E1 < E0 || (long long)E1 > limit) {   // inconsistent bounds: skip the chunk
       if (t == 0) oob(ctrl, 2, E1);
       E1 = E0 = 0;
     }
+    const int S = 8 * T;
     int w = (E0 & ~7) + 8 * t;
-    int id[8];
-    float vv[8];
-    if (w < E1) {
-      const int4 a = __ldg(reinterpret_cast<const int4*>(idx + w)), b = __ldg(reinterpret_cast<const int4*>(idx + w + 4));
-      id[0] = a.x; id[1] = a.y; id[2] = a.z; id[3] = a.w; id[4] = b.x; id[5] = b.y; id[6] = b.z; id[7] = b.w;
-      load8<V>(val + w, vv);
-    }
-    for (; w < E1; w += 8 * T) {
-      const int wn = w + 8 * T;
-      int idn[8];
-      float vn[8];
-      if (wn < E1) {
-        const int4 a = __ldg(reinterpret_cast<const int4*>(idx + wn));
-        const int4 b = __ldg(reinterpret_cast<const int4*>(idx + wn + 4));
-        idn[0] = a.x; idn[1] = a.y; idn[2] = a.z; idn[3] = a.w; idn[4] = b.x; idn[5] = b.y; idn[6] = b.z; idn[7] = b.w;
-        load8<V>(val + wn, vn);
-      }
-      const int u0 = max(0, E0 - w), u1 = min(8, E1 - w);
-      if (u0 < u1) {
-        // row of element w + u0: the largest k with segs[k] <= w + u0 (empty rows share bounds)
-        const int g0 = w + u0;
-        int lo = 0, hi = nr - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (segs[mid] <= g0) lo = mid; else hi = mid - 1;
-        }
-        int k = lo, kend = segs[lo + 1];
-        float s = 0.0f;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (u >= u0 && u < u1) {
-            while (w + u >= kend) {   // next row (at most nr - 1 steps in all)
-              atomicAdd(&acc[k], s);
-              s = 0.0f;
-              ++k;
-              kend = segs[k + 1];
-            }
-            const int q = id[u] - j0;
-            if ((unsigned)q < (unsigned)jn) s = fmaf(vv[u], xs[q], s);
-          }
-        }
-        atomicAdd(&acc[k], s);
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) { id[u] = idn[u]; vv[u] = vn[u]; }
+    int ia[8], ib[8];
+    float va[8], vb[8];
+    if (w < E1) { load8i(idx + w, ia); load8<V>(val + w, va); }
+    while (w < E1) {
+      if (w + S < E1) { load8i(idx + w + S, ib); load8<V>(val + w + S, vb); }
+      group8(w, E0, E1, ia, va, j0, jn, xs, segs, nr, acc);
+      w += S;
+      if (w >= E1) break;
+      if (w + S < E1) { load8i(idx + w + S, ia); load8<V>(val + w + S, va); }
+      group8(w, E0, E1, ib, vb, j0, jn, xs, segs, nr, acc);
+      w += S;
     }
   }
   __syncthreads();
