@@ -309,6 +309,19 @@ def _spmv_bytes(res, n, m, kdtype="f32", log_domain=0):
     return row, col
 
 
+def _traffic(name):
+    """DRAM bytes per iteration of the iteration kernel from the committed ncu
+    summary of this workload (profiles/spmv_traffic_<name>.txt), or None."""
+    p = os.path.join(ROOT, "profiles", f"spmv_traffic_{name}.txt")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        for line in f:
+            if line.startswith("bytes_per_iteration:"):
+                return float(line.split(":", 1)[1])
+    return None
+
+
 def _golden(w):
     """FP64 oracle result of the workload stored by tests/golden (None if absent)."""
     p = os.path.join(ROOT, "tests", "golden", f"{w.name.split('_d')[0]}_oracle.json")
@@ -399,11 +412,7 @@ def run_ours(args):
     per_iter_ms = rf["ms_iter"] / max(rf["iters_enqueued"], 1)
     peak, peak_kind = _peaks()
     achieved = (row_b + col_b) / (per_iter_ms * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", f"spmv_traffic_{w.name}.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            traffic = json.load(f).get("bytes_per_iteration")
+    traffic = _traffic(w.name)
 
     # dense Sinkhorn on the same GPU, same tolerance (log-sum-exp form for small
     # eps); with --dense-cap the run stops after that many iterations and the
