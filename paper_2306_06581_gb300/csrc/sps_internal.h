@@ -206,6 +206,8 @@ sps_status launch_dense_lse_row_only(const ProbDev& pd, const Layout& L, char* w
 sps_status launch_dense_lse_objective(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                                       void* alpha_out, void* beta_out, cudaStream_t st);
 
+sps_status launch_cost_max_points(const float* x, int n, const float* y, int m, int d, void* scratch,
+                                  cudaStream_t st);
 // Shared with the batched path (sps_sketch.cu)
 void launch_scan_counts(const int* row_cnt, int* row_ptr, int n, const int* col_cnt, int* col_ptr, int* col_cur,
                         int m, long long cap, Ctrl* ctrl, cudaStream_t st);

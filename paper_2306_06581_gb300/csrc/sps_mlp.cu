@@ -435,36 +435,6 @@ __global__ void k_init(float* w, int d, uint64_t seed) {
   }
 }
 
-// Exact binary32 maximum of the squared distances (the solver's cost divisor).
-template <int DM>
-__global__ void k_max_dist(const float* x, int n, const float* y, int m, int d, unsigned* out) {
-  __shared__ float ys[256 * 16];
-  float best = 0.0f;
-  float xi[DM];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int c = 0; c < DM; ++c) xi[c] = (i < n && c < d) ? x[(size_t)i * d + c] : 0.0f;
-  for (int j0 = 0; j0 < m; j0 += 256) {
-    const int jn = min(256, m - j0);
-    __syncthreads();
-    for (int k = threadIdx.x; k < jn * d; k += blockDim.x) ys[k] = y[(size_t)j0 * d + k];
-    __syncthreads();
-    if (i < n)
-      for (int jj = 0; jj < jn; ++jj) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int c = 0; c < DM; ++c) {
-          if (c < d) {
-            const float t = __fsub_rn(xi[c], ys[jj * d + c]);
-            acc = __fmaf_rn(t, t, acc);
-          }
-        }
-        best = fmaxf(best, acc);
-      }
-  }
-  best = warp_max(best);
-  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(best));
-}
-
 Side make_side(const float* sp, const float* sw, int sn, const float* op, const float* ow, int on, int d,
                float inv_s, float eps, const float* target, float* out, const __nv_bfloat16* wb, const float* wf,
                float* grad, float* pool, float* dpool, float* loss) {
@@ -561,18 +531,12 @@ sps_status sps_cost_max(const float* x, int32_t n, const float* y, int32_t m, in
                         void* ws, sps_stream stream) {
   if (!x || !y || !cost_max || !ws || n < 1 || m < 1 || d < 1 || d > 16) { set_error("bad cost_max arguments"); return SPS_ERR_INVALID_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned* out = (unsigned*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-  SPS_TRY(cuda_fail(cudaMemsetAsync(out, 0, sizeof(unsigned), st), "memset"));
-  const int g = (n + 255) / 256;
-  if (d <= 2) k_max_dist<2><<<g, 256, 0, st>>>(x, n, y, m, d, out);
-  else if (d == 3) k_max_dist<3><<<g, 256, 0, st>>>(x, n, y, m, d, out);
-  else if (d <= 8) k_max_dist<8><<<g, 256, 0, st>>>(x, n, y, m, d, out);
-  else k_max_dist<16><<<g, 256, 0, st>>>(x, n, y, m, d, out);
-  unsigned bits = 0;
-  SPS_TRY(cuda_fail(cudaMemcpyAsync(&bits, out, sizeof(bits), cudaMemcpyDeviceToHost, st), "read back"));
+  SketchScalars* sc = (SketchScalars*)(((uintptr_t)ws + 2048 + 255) & ~(uintptr_t)255);
+  SPS_TRY(cuda_fail(cudaMemsetAsync(sc, 0, sizeof(SketchScalars), st), "memset"));
+  SPS_TRY(launch_cost_max_points(x, n, y, m, d, sc, st));   // the sketch's own tiled kernel
+  float f = 0.0f;
+  SPS_TRY(cuda_fail(cudaMemcpyAsync(&f, &sc->dmax32, sizeof(f), cudaMemcpyDeviceToHost, st), "read back"));
   SPS_TRY(cuda_fail(cudaStreamSynchronize(st), "synchronize"));
-  float f;
-  memcpy(&f, &bits, sizeof(f));
   *cost_max = (double)f;
   return SPS_OK;
 }

@@ -417,6 +417,20 @@ sps_status launch_cost_max(const ProbDev& pd, const Layout& L, char* ws, int nee
   return cuda_fail(cudaGetLastError(), "cost_max");
 }
 
+// The same maximum for bare binary32 point arrays (the warm start's cost
+// divisor); scratch holds one SketchScalars and must start at zero.
+sps_status launch_cost_max_points(const float* x, int n, const float* y, int m, int d, void* scratch,
+                                  cudaStream_t st) {
+  ProbDev pd;
+  memset(&pd, 0, sizeof(pd));
+  pd.n = n; pd.m = m; pd.d = d;
+  pd.cv.x32 = x; pd.cv.y32 = y; pd.cv.n = n; pd.cv.m = m; pd.cv.d = d;
+  Layout L;
+  memset(&L, 0, sizeof(L));
+  L.scal = 0;
+  return launch_cost_max(pd, L, (char*)scratch, 0, st);
+}
+
 sps_status launch_scalars0(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st) {
   k_scalars<<<1, 32, 0, st>>>(pd, at<SketchScalars>(ws, L.scal), at<Ctrl>(ws, L.ctrl), 0);
   add_launches(1);
