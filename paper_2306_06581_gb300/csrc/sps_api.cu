@@ -121,10 +121,11 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
     L->col_ptr = take((size_t)(m + 1) * 4);
     L->col_cur = take((size_t)m * 4);
     L->cnt2 = take((size_t)sweep_geometry(n, m).nchunk * n * 4);
-    L->col_idx = take((size_t)cap * 4);
-    L->val = take(((size_t)cap + 8) * vb);   // + 8: staged passes read aligned groups of 8
-    L->row_idx = take((size_t)cap * 4);
-    L->valT = take(((size_t)cap + 8) * vb);
+    // + 16: staged passes read aligned groups of 8, the ring copies aligned groups of 16
+    L->col_idx = take(((size_t)cap + 16) * 4);
+    L->val = take(((size_t)cap + 16) * vb);
+    L->row_idx = take(((size_t)cap + 16) * 4);
+    L->valT = take(((size_t)cap + 16) * vb);
     L->csr_pos = take((size_t)cap * 4);
     L->tmp_row = take((size_t)cap * 4);
     L->tmp_src = take((size_t)cap * 4);
@@ -164,6 +165,10 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
     L->alpha = take((size_t)n * 4);
     L->beta = take((size_t)m * 4);
     L->ahat = take((size_t)n * 4);
+    if (op == SPS_OP_SPAR_SINK && !Q->log_domain) {
+      L->unit_r = take((size_t)(n + 2) * 4);
+      L->unit_c = take((size_t)(m + 2) * 4);
+    }
     if (Q->log_domain) {
       L->bhat = take((size_t)m * 4);
       L->erow = take((size_t)n * 4);

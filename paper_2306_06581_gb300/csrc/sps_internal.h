@@ -38,6 +38,7 @@ struct Ctrl {
   float max_logv;
   unsigned int bar_count; // grid barrier of the persistent iteration kernel: arrivals
   unsigned int bar_gen;   //   and generation
+  unsigned long long bar_mono;  // arrivals at the counting grid barrier (a multiple of the grid between launches)
   int wait_timeout;       // a bounded device wait gave up
   int sketch_fault;       // fill disagreed with count (write skipped instead of out of range)
   int pad_overflow;       // single-pass sketch: a padded (row, chunk) slot was too small
@@ -86,6 +87,7 @@ struct Layout {
   size_t cm_idx_r, cm_idx_c;        //   indices in chunk-major order (K' values are stored in that order)
   size_t cm_perm_r, cm_perm_c;      //   row-major position -> chunk-major position
   size_t pad_ofs, pad_col, pad_val, pad_lv, zsum, csum;   // single-pass sketch (0: two passes)
+  size_t unit_r, unit_c;            // persistent iterations: unit starts over rows [n + 2] / columns [m + 2]
   int64_t pad_cap;
   int stage_w, stage_jr, stage_jc;  // staged gathers: chunk width, chunks over columns / rows (0: off)
   int stage_nsm;                    // SM count the staging was planned for

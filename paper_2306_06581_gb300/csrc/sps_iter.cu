@@ -52,6 +52,8 @@ struct IterArgs {
   Ctrl* ctrl;
   double* part;        // kPartSlots x nblk
   int nblk;
+  const int *unit_r, *unit_c;   // work units of the persistent kernel (null: none)
+  int ring;                     // ring elements per slot of the unit kernel
 };
 
 // Row phase of iteration t -> t+1 for the rows of this block; returns the
@@ -242,6 +244,379 @@ __global__ void __launch_bounds__(kIterThreads) k_iterate(IterArgs A, int iters)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent iterations over fixed work units.
+//
+// The rows (columns) are cut once per solve into contiguous units of at most
+// kUnitRows rows whose element counts are close to T = ceil(nnz / W), W the
+// number of working warps: a unit holds the rows whose first element falls
+// into one bucket [b T, (b + 1) T) of the element range, split every
+// kUnitRows rows.  Working warp w owns units w, w + W, ... for the whole
+// solve, so the bounds, the weights and the current iterate values of its
+// first unit stay in registers across iterations, and a phase reads only the
+// unit's elements and the gathered vector.  The unit's index and value
+// arrays stream through a two-slot ring of the warp in shared memory, filled
+// by bulk copies (TMA) one slot ahead of the one being read, so the copies in
+// flight hold no registers; the warp reads the elements in order with all 32
+// lanes and closes each row with a butterfly.
+// Warp 0 of block 0 takes no unit: it reduces the block partials of the
+// phase just finished while the other warps run the next phase.
+// With STAGE, every block first copies the whole gathered vector into shared
+// memory (one bulk copy): scattered reads of one vector make each warp-wide
+// gather touch up to 32 cache lines, so served from L1 they cost about one
+// cycle per element per SM, while shared memory serves them at the rate of
+// its bank conflicts.
+// ---------------------------------------------------------------------------
+constexpr int kUnitRows = 16;
+constexpr int kUnitThreads = 512;            // 16 warps per block, one block per SM: up to 128 registers a thread
+constexpr int kUnitWarps = kUnitThreads / 32;
+constexpr size_t kStageBudget = 160 * 1024;   // largest staged vector (bytes)
+
+template <typename T>
+struct UnitCache {   // one unit of one warp, in shared memory
+  int r0, nr;        // rows r0 .. r0 + nr - 1 (nr = 0: none)
+  int p[kUnitRows + 1];   // ptr[r0 .. r0 + nr]
+  T w[kUnitRows];    // weights of the rows
+  T x[kUnitRows];    // current iterate values of the rows
+};
+
+// Shared memory of the unit kernel: the vector copy's barrier, two ring
+// barriers per warp, three unit caches per warp (first row unit, first
+// column unit, scratch), the rings (ring elements per slot, a multiple of
+// 16) and the staged vector, each part 128-byte aligned.
+template <typename T>
+__host__ __device__ constexpr size_t unit_head_bytes() {
+  return (64 + kUnitWarps * 16 + 3 * kUnitWarps * sizeof(UnitCache<T>) + 127) / 128 * 128;
+}
+template <typename V>
+__host__ __device__ constexpr size_t ring_bytes(int ring) {
+  return (size_t)kUnitWarps * 2 * ring * (sizeof(int) + sizeof(V));
+}
+
+// Unit starts: ustart[0 .. U] (ustart[U] = n) and U in ustart[n + 1].  One
+// block; each thread scans a contiguous range of rows, so only the first row
+// of a range needs a binary search for the start of its bucket.
+__global__ void __launch_bounds__(1024) k_units(const int* __restrict__ ptr, int n, int W, int* __restrict__ ustart) {
+  __shared__ int wtot[32];
+  __shared__ int total;
+  const long long nnz = ptr[n];
+  const long long T = max(32LL, (nnz + W - 1) / W);
+  const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+  auto walk = [&](auto&& emit) {
+    if (lo >= hi) return;
+    long long bprev = lo > 0 ? (long long)ptr[lo - 1] / T : -1;
+    int first = lo;
+    for (int i = lo; i < hi; ++i) {
+      const long long b = (long long)ptr[i] / T;
+      if (b != bprev) {
+        first = i;
+      } else if (i == lo) {   // the bucket started before this range
+        const long long key = b * T;
+        int l = 0, h = lo;
+        while (l < h) {
+          const int mid = (l + h) >> 1;
+          if ((long long)ptr[mid] < key) l = mid + 1;
+          else h = mid;
+        }
+        first = l;
+      }
+      if (b != bprev || (i - first) % kUnitRows == 0) emit(i);
+      bprev = b;
+    }
+  };
+  int cnt = 0;
+  walk([&](int) { ++cnt; });
+  // exclusive scan of the counts over the block
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wtot[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    int x = lane < nw ? wtot[lane] : 0, xi = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += y;
+    }
+    if (lane < nw) wtot[lane] = xi - x;
+    if (lane == 31) total = xi;
+  }
+  __syncthreads();
+  int pos = wtot[w] + inc - cnt;
+  walk([&](int i) { ustart[pos++] = i; });
+  if (threadIdx.x == 0) {
+    ustart[total] = n;
+    ustart[n + 1] = total;
+  }
+}
+
+// Unit u (or none: nr = 0) into the warp's cache c.
+template <typename T>
+__device__ __forceinline__ void load_unit(UnitCache<T>* c, const int* ustart, int U, const int* ptr, const T* wgt,
+                                          const T* xcur, int u) {
+  const int lane = threadIdx.x & 31;
+  const int r0 = u < U ? ustart[u] : 0;
+  const int nr = u < U ? ustart[u + 1] - r0 : 0;
+  if (lane == 0) { c->r0 = r0; c->nr = nr; }
+  if (lane <= nr) c->p[lane] = __ldg(ptr + r0 + lane);
+  if (lane < nr) { c->w[lane] = wgt[r0 + lane]; c->x[lane] = xcur[r0 + lane]; }
+  __syncwarp();
+}
+
+// q_i = sum_k val[k] x[idx[k]] for the rows of one unit, returned on lane
+// i - r0 (lanes >= nr: 0).  Slot h of the ring holds `ring` elements of the
+// index array (ridx) and of the value array (rval); chunk c of the unit's
+// 16-element aligned range goes to slot c & 1 and the warp's barrier bars[h]
+// completes when it has landed; `par` holds the two barriers' phase bits.
+// Element k of a row goes to lane (k - start of the row's piece in the chunk)
+// mod 32; a lane's partial sum carries over chunk boundaries.
+template <typename V, typename T>
+__device__ __forceinline__ bool unit_products(const UnitCache<T>* c, int nr, const int* __restrict__ idx,
+                                              const V* val, const T* x, int* ridx, V* rval, uint64_t* bars,
+                                              unsigned& par, int ring, T* q_out) {
+  const int lane = threadIdx.x & 31;
+  const int k0 = c->p[0], k1 = c->p[nr];
+  const int kA = k0 & ~15, kE = (k1 + 15) & ~15;
+  const int nch = (kE - kA + ring - 1) / ring;
+  auto issue = [&](int ch) {   // lane 0
+    const int cs = kA + ch * ring;
+    const unsigned cnt = (unsigned)(min(cs + ring, kE) - cs);
+    const int h = ch & 1;
+    fence_proxy_async_shared();
+    mbar_arrive_expect_tx(bars + h, cnt * (unsigned)(sizeof(int) + sizeof(V)));
+    bulk_copy_g2s(ridx + h * ring, idx + cs, cnt * (unsigned)sizeof(int), bars + h);
+    bulk_copy_g2s(rval + h * ring, val + cs, cnt * (unsigned)sizeof(V), bars + h);
+  };
+  if (lane == 0) {
+    if (nch > 0) issue(0);
+    if (nch > 1) issue(1);
+  }
+  int i = 0, re = c->p[1];
+  T acc = 0, mine = 0;
+  bool ok = true;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int h = ch & 1;
+    long long polls = 0;
+    while (!mbar_try_wait(bars + h, (par >> h) & 1u)) {
+      if (++polls > kSpinLimit) { ok = false; break; }
+    }
+    par ^= 1u << h;
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    const int cs = kA + ch * ring;
+    const int* si = ridx + h * ring - cs;
+    const V* sv = rval + h * ring - cs;
+    const int kend = min(cs + ring, k1);
+    int k = max(cs, k0);
+    while (k < kend) {
+      const int pe = min(re, kend);
+      for (int kk = k + lane; kk < pe; kk += 32) acc += load_as<T>(sv + kk) * x[si[kk]];
+      k = pe;
+      if (k == re) {   // the row ends here (an empty row ends at once)
+        acc = warp_sum(acc);
+        if (lane == i) mine = acc;
+        acc = (T)0;
+        ++i;
+        re = c->p[min(i + 1, nr)];
+      }
+    }
+    __syncwarp();   // slot h is read
+    if (lane == 0 && ch + 2 < nch) issue(ch + 2);
+  }
+  *q_out = mine;   // rows left open are empty: 0
+  return true;
+}
+
+// Row phase (ROW: u^{t+1} = (a / q)^phi with the residual terms of (u^t, v^t))
+// or column phase (v^{t+1} = (b / r)^phi) over this warp's units.
+// s[] gathers: ROW residual, unreachable a-mass, |u^{t+1} - u^t|;
+//              column: unreachable b-mass, |v^{t+1} - v^t|.
+template <typename V, typename T, bool UOT, bool ROW>
+__device__ __forceinline__ bool unit_phase(const int* ustart, int U, const int* ptr, const int* idx, const V* val,
+                                           const T* x, const T* wgt, const T* xcur, T* xnew, UnitCache<T>* c0,
+                                           UnitCache<T>* scratch, int worker, int W, T phi, T inv_phi, T (&s)[3],
+                                           int* ridx, V* rval, uint64_t* bars, unsigned& par, int ring) {
+  const int lane = threadIdx.x & 31;
+  int k = 0;
+  for (int u = worker; u < U; u += W, ++k) {
+    UnitCache<T>* c = c0;
+    if (k > 0) {
+      load_unit(scratch, ustart, U, ptr, wgt, xcur, u);
+      c = scratch;
+    }
+    const int nr = c->nr;
+    T q;
+    if (!unit_products<V, T>(c, nr, idx, val, x, ridx, rval, bars, par, ring, &q)) return false;
+    if (lane < nr) {
+      const T wi = c->w[lane], xo = c->x[lane];
+      T xn;
+      if (q > (T)0) {
+        xn = UOT ? powT<T>(wi / q, phi) : wi / q;
+        if (ROW) {
+          const T lhs = (UOT ? powT<T>(xo, inv_phi) : xo) * q;
+          s[0] += fabs(lhs - wi);
+        }
+      } else {
+        xn = (T)0;
+        s[ROW ? 1 : 0] += wi;
+      }
+      s[ROW ? 2 : 1] += fabs(xn - xo);
+      xnew[c->r0 + lane] = xn;
+      c->x[lane] = xn;
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
+// The block partials reduced by one warp, in the order reduce_parts uses.
+template <int NP, typename R>
+__device__ __forceinline__ void reduce_parts_warp(const double* part, int nblk, double* out) {
+  const int lane = threadIdx.x & 31;
+  R s[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) s[p] = (R)0;
+#pragma unroll 4
+  for (int b = lane; b < nblk; b += 32) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) s[p] += (R)__ldcg(part + (size_t)p * nblk + b);
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) out[p] = (double)warp_sum(s[p]);
+}
+
+// A bounded wait gave up: the solve stops with an error.
+__device__ __forceinline__ void wait_failed(Ctrl* ctrl) {
+  ctrl->wait_timeout = 1;
+  ctrl->status = SPS_ERR_CUDA;
+  __threadfence();
+  ctrl->done = 1;
+}
+
+// The whole vector x[0 .. len) into shared memory: one bulk copy (TMA) of
+// its 16-byte aligned body when x is 16-byte aligned, plain loads otherwise
+// and for the tail.  x was written by other blocks before the last grid
+// barrier; the copy is ordered after that barrier by a proxy fence.  The
+// wait is bounded: false (and the error recorded) when it gives up.
+template <typename T>
+__device__ __forceinline__ bool stage_vector(T* xs, const T* x, int len, uint64_t* bar, unsigned& parity,
+                                             Ctrl* ctrl) {
+  const size_t bytes = (size_t)len * sizeof(T);
+  const bool bulk = ((uintptr_t)x & 15) == 0 && bytes >= 16;
+  const unsigned body = bulk ? (unsigned)(bytes & ~(size_t)15) : 0u;
+  if (bulk && threadIdx.x == 0) {
+    fence_proxy_async_global();
+    fence_proxy_async_shared();
+    mbar_arrive_expect_tx(bar, body);
+    bulk_copy_g2s(xs, x, body, bar);
+  }
+  for (int j = (int)(body / sizeof(T)) + (int)threadIdx.x; j < len; j += kUnitThreads) xs[j] = __ldcg(x + j);
+  int ok = 1;
+  if (bulk) {
+    long long polls = 0;
+    while (!mbar_try_wait(bar, parity)) {
+      if (++polls > kSpinLimit) { ok = 0; break; }
+    }
+    parity ^= 1u;
+  }
+  if (!__syncthreads_and(ok)) {
+    if (threadIdx.x == 0) wait_failed(ctrl);
+    return false;
+  }
+  return true;
+}
+
+template <typename V, typename T, bool UOT, bool STAGE>
+__global__ void __launch_bounds__(kUnitThreads, 1) k_iterate_units(IterArgs A, int iters) {
+  __shared__ T sh[3 * 32];
+  __shared__ DecState S;   // block 0's decision state
+  extern __shared__ __align__(128) char udyn[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ring = A.ring;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(udyn);               // STAGE: the vector copy's barrier
+  uint64_t* bars = reinterpret_cast<uint64_t*>(udyn + 64) + 2 * warp;
+  UnitCache<T>* ucache = reinterpret_cast<UnitCache<T>*>(udyn + 64 + kUnitWarps * 16) + 3 * warp;
+  char* rings = udyn + unit_head_bytes<T>();
+  int* ridx = reinterpret_cast<int*>(rings) + (size_t)warp * 2 * ring;
+  V* rval = reinterpret_cast<V*>(rings + (size_t)kUnitWarps * 2 * ring * sizeof(int)) + (size_t)warp * 2 * ring;
+  T* xs = reinterpret_cast<T*>(rings + ring_bytes<V>(ring));        // STAGE: the gathered vector
+  Ctrl* ctrl = A.ctrl;
+  if (ctrl->done) return;
+  int t = ctrl->t;
+  const bool reducer = blockIdx.x == 0 && warp == 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) S = load_state(ctrl);
+  unsigned parity = 0, par = 0;
+  if (threadIdx.x == 0 && STAGE) mbar_init(bar, 1);
+  if (lane == 0) {
+    mbar_init(bars + 0, 1);
+    mbar_init(bars + 1, 1);
+    fence_mbarrier_init();
+  }
+  __syncthreads();
+  const int W = (int)gridDim.x * kUnitWarps - 1;
+  const int worker = (int)blockIdx.x * kUnitWarps + warp - 1;
+  const int Ur = A.unit_r[A.n + 1], Uc = A.unit_c[A.m + 1];
+  const T* a = (const T*)A.a;
+  const T* b = (const T*)A.b;
+  const V* val = (const V*)A.val;
+  const V* valT = (const V*)A.valT;
+  const T phi = (T)A.phi, inv_phi = (T)A.inv_phi;
+  if (!reducer) {
+    load_unit(ucache + 0, A.unit_r, Ur, A.row_ptr, a, (const T*)A.ubuf + (size_t)(t & 1) * A.n, worker);
+    load_unit(ucache + 1, A.unit_c, Uc, A.col_ptr, b, (const T*)A.vbuf + (size_t)(t & 1) * A.m, worker);
+  }
+  for (int k = 0; k < iters; ++k) {
+    const T* v = (const T*)A.vbuf + (size_t)(t & 1) * A.m;
+    const T* uold = (const T*)A.ubuf + (size_t)(t & 1) * A.n;
+    T* unew = (T*)A.ubuf + (size_t)((t + 1) & 1) * A.n;
+    T* vnew = (T*)A.vbuf + (size_t)((t + 1) & 1) * A.m;
+    T s3[3] = {(T)0, (T)0, (T)0};
+    if (STAGE && !stage_vector<T>(xs, v, A.m, bar, parity, ctrl)) return;
+    if (!reducer &&
+        !unit_phase<V, T, UOT, true>(A.unit_r, Ur, A.row_ptr, A.col_idx, val, STAGE ? (const T*)xs : v, a, uold,
+                                     unew, ucache + 0, ucache + 2, worker, W, phi, inv_phi, s3, ridx, rval, bars, par,
+                                     ring))
+      wait_failed(ctrl);
+    block_sum_multi<3, T>(s3, sh);
+    if (threadIdx.x == 0) {
+      A.part[0 * (size_t)A.nblk + blockIdx.x] = (double)s3[0];
+      A.part[1 * (size_t)A.nblk + blockIdx.x] = (double)s3[1];
+      A.part[2 * (size_t)A.nblk + blockIdx.x] = (double)s3[2];
+    }
+    if (!grid_barrier_count(ctrl)) return;
+    if (reducer) {
+      double tot[3];
+      reduce_parts_warp<3, T>(A.part, A.nblk, tot);
+      if (lane == 0) decide_row(ctrl, S, A, t, tot);
+    }
+    T s2[3] = {(T)0, (T)0, (T)0};
+    if (STAGE && !stage_vector<T>(xs, unew, A.n, bar, parity, ctrl)) return;
+    if (!reducer &&
+        !unit_phase<V, T, UOT, false>(A.unit_c, Uc, A.col_ptr, A.row_idx, valT, STAGE ? (const T*)xs : unew, b,
+                                      (const T*)A.vbuf + (size_t)(t & 1) * A.m, vnew, ucache + 1, ucache + 2, worker,
+                                      W, phi, inv_phi, s2, ridx, rval, bars, par, ring))
+      wait_failed(ctrl);
+    T c2[2] = {s2[0], s2[1]};
+    block_sum_multi<2, T>(c2, sh);
+    if (threadIdx.x == 0) {
+      A.part[3 * (size_t)A.nblk + blockIdx.x] = (double)c2[0];
+      A.part[4 * (size_t)A.nblk + blockIdx.x] = (double)c2[1];
+    }
+    if (!grid_barrier_count(ctrl)) return;
+    if (*(volatile int*)&ctrl->done) return;
+    if (reducer) {
+      double tot[2];
+      reduce_parts_warp<2, T>(A.part + 3 * (size_t)A.nblk, A.nblk, tot);
+      if (lane == 0) decide_col(ctrl, S, t, tot);
+    }
+    ++t;
+  }
+}
+
 template <int LPR, typename V, typename T, bool UOT>
 __global__ void __launch_bounds__(kIterThreads) k_row_pass(IterArgs A) {
   __shared__ T sh[3 * 32];
@@ -289,6 +664,7 @@ __global__ void k_iter_init(int n, int m, T* u0, T* v0, const T* al, const T* be
     ctrl->t = 0; ctrl->done = 0; ctrl->iters = 0;
     ctrl->blocks_a = ctrl->blocks_b = ctrl->blocks_c = 0u;
     ctrl->bar_count = 0u;
+    ctrl->bar_mono = 0ull;
     if (ctrl->status != SPS_OK) { ctrl->done = 1; }
   }
 }
@@ -421,6 +797,8 @@ IterArgs make_args(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& 
   A.ubuf = ws + L.u; A.vbuf = ws + L.v; A.a = ws + L.a_it; A.b = ws + L.b_it;
   A.phi = ic.phi; A.inv_phi = 1.0 / ic.phi; A.tol = ic.tol; A.stop_rule = ic.stop_rule;
   A.ctrl = at<Ctrl>(ws, L.ctrl); A.part = at<double>(ws, L.part); A.nblk = L.nblk_rows;
+  A.unit_r = L.unit_r ? at<int>(ws, L.unit_r) : nullptr;
+  A.unit_c = L.unit_c ? at<int>(ws, L.unit_c) : nullptr;
   return A;
 }
 
@@ -480,10 +858,98 @@ bool coop(const IterArgs& A, int lr, int lc, int iters, cudaStream_t st) {
   return coop_lc<4, V, T, UOT>(A, lc, iters, st);
 }
 
+// Shared memory plan of the unit kernel: the gathered vector staged when it
+// fits beside rings of at least 128 elements a slot (rings of up to 512).
+struct UnitPlan {
+  bool stage;
+  int ring;
+  size_t smem;
+};
+
+template <typename V, typename T>
+UnitPlan unit_plan(int n, int m) {
+  const size_t limit = 227 * 1024 - 2048;   // dynamic part (the static arrays take under 1 KB)
+  const size_t head = unit_head_bytes<T>();
+  const size_t per16 = ring_bytes<V>(16);
+  auto ring_for = [&](size_t room) { return (int)std::min<size_t>(512, room / per16 * 16); };
+  const size_t sb = ((size_t)std::max(n, m) * sizeof(T) + 15) / 16 * 16;
+  if (sb <= kStageBudget && head + sb < limit) {
+    const int r = ring_for(limit - head - sb);
+    if (r >= 128) return {true, r, head + ring_bytes<V>(r) + sb};
+  }
+  const int r = ring_for(limit - head);
+  return {false, r, head + ring_bytes<V>(r)};
+}
+
+// Grid of the unit kernel (all SMs, as many blocks per SM as fit, at most
+// cap); false when the device refuses a cooperative launch of it.
+template <typename V, typename T, bool UOT, bool STAGE>
+bool units_grid(int cap, size_t smem, int* grid_out) {
+  auto fn = k_iterate_units<V, T, UOT, STAGE>;
+  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+  if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kUnitThreads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  *grid_out = std::max(1, std::min(cap, nsm * per_sm));
+  return true;
+}
+
+template <typename V, typename T, bool UOT, bool STAGE>
+bool coop_units_s(IterArgs A, const UnitPlan& pl, int iters, cudaStream_t st) {
+  int grid = 0;
+  if (!units_grid<V, T, UOT, STAGE>(A.nblk, pl.smem, &grid)) return false;
+  A.nblk = grid;
+  A.ring = pl.ring;
+  void* args[] = {(void*)&A, (void*)&iters};
+  if (cudaLaunchCooperativeKernel((const void*)k_iterate_units<V, T, UOT, STAGE>, dim3(grid), dim3(kUnitThreads),
+                                  args, pl.smem, st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+template <typename V, typename T, bool UOT>
+bool coop_units(const IterArgs& A, int iters, cudaStream_t st) {
+  const UnitPlan pl = unit_plan<V, T>(A.n, A.m);
+  return pl.stage ? coop_units_s<V, T, UOT, true>(A, pl, iters, st) : coop_units_s<V, T, UOT, false>(A, pl, iters, st);
+}
+
+template <typename V, typename T, bool UOT>
+int units_grid_u(int n, int m, int cap) {
+  int g = 0;
+  const UnitPlan pl = unit_plan<V, T>(n, m);
+  const bool ok = pl.stage ? units_grid<V, T, UOT, true>(cap, pl.smem, &g) : units_grid<V, T, UOT, false>(cap, pl.smem, &g);
+  return ok ? g : 0;
+}
+
+template <typename V, typename T>
+int units_grid_vt(const IterCfg& ic, int n, int m, int cap) {
+  return ic.uot ? units_grid_u<V, T, true>(n, m, cap) : units_grid_u<V, T, false>(n, m, cap);
+}
+
+int units_grid_dispatch(const IterCfg& ic, int n, int m, int cap) {
+  switch (ic.kd) {
+    case SPS_F64: return units_grid_vt<double, double>(ic, n, m, cap);
+    case SPS_F32: return units_grid_vt<float, float>(ic, n, m, cap);
+    case SPS_BF16: return units_grid_vt<__nv_bfloat16, float>(ic, n, m, cap);
+    default: return units_grid_vt<__half, float>(ic, n, m, cap);
+  }
+}
+
 // Enqueue `iters` iterations; returns the number of kernels launched.
 template <typename V, typename T>
 int iterate_vt(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, int iters, cudaStream_t st) {
   const IterArgs A = make_args(pd, L, ws, ic);
+  if (ic.persistent && A.unit_r && A.unit_c) {
+    const bool ok = ic.uot ? coop_units<V, T, true>(A, iters, st) : coop_units<V, T, false>(A, iters, st);
+    if (ok) return 1;
+  }
   if (ic.persistent) {
     const bool ok = ic.uot ? coop<V, T, true>(A, ic.lpr_rows, ic.lpr_cols, iters, st)
                            : coop<V, T, false>(A, ic.lpr_rows, ic.lpr_cols, iters, st);
@@ -548,6 +1014,16 @@ sps_status launch_iter_init(const ProbDev& pd, const Layout& L, char* ws, const 
     k_iter_init<float><<<std::max(g, 1), kThreads, 0, st>>>(pd.n, pd.m, at<float>(ws, L.u), at<float>(ws, L.v),
         (const float*)init_alpha, (const float*)init_beta, ic.eps, at<Ctrl>(ws, L.ctrl));
   add_launches(1);
+  if (ic.persistent && L.unit_r && L.unit_c) {
+    // work units for the grid the persistent kernel will get
+    const int grid = units_grid_dispatch(ic, pd.n, pd.m, L.nblk_rows);
+    if (grid > 0) {
+      const int W = grid * kUnitWarps - 1;
+      k_units<<<1, 1024, 0, st>>>(at<int>(ws, L.row_ptr), pd.n, W, at<int>(ws, L.unit_r));
+      k_units<<<1, 1024, 0, st>>>(at<int>(ws, L.col_ptr), pd.m, W, at<int>(ws, L.unit_c));
+      add_launches(2);
+    }
+  }
   return cuda_fail(cudaGetLastError(), "iter_init");
 }
 

@@ -122,6 +122,43 @@ __device__ void reduce_parts(const double* part, int nblk, double* out) {
   __syncthreads();
 }
 
+// Bulk copies (TMA, non-tensor) into shared memory with an mbarrier.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// dst, src 16-byte aligned; bytes a multiple of 16
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// make an initialised mbarrier visible to the bulk-copy unit
+__device__ __forceinline__ void fence_mbarrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// order this thread's earlier generic-proxy accesses before later async-proxy ones
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
 // Grid barrier of the cooperative kernel: arrival counter plus generation;
 // the waiting threads spin with a sleep and give up after kSpinLimit polls,
 // recording a failure instead of hanging.
@@ -145,6 +182,35 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl) {
       }
     }
     __threadfence();
+    if (!ok) { ctrl->wait_timeout = 1; ctrl->done = 1; ctrl->status = SPS_ERR_CUDA; }
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// Counting grid barrier: arrivals only ever add to one 64-bit counter (a
+// release add), and a block waits until the counter reaches the next multiple
+// of the grid (acquire loads).  Arrivals at barrier e + 1 start only after all
+// arrivals at barrier e, so the count returned to an arrival fixes its
+// barrier.  The counter starts at 0 for each solve and stays a multiple of
+// the grid between launches of one solve (same grid).  Bounded wait.
+__device__ __forceinline__ bool grid_barrier_count(Ctrl* ctrl) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long prev;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], 1;\n" : "=l"(prev) : "l"(&ctrl->bar_mono) : "memory");
+    const unsigned long long target = (prev / gridDim.x + 1) * gridDim.x;
+    int ok = 1;
+    long long spins = 0;
+    for (;;) {
+      unsigned long long cur;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(cur) : "l"(&ctrl->bar_mono) : "memory");
+      if (cur >= target) break;
+      if (++spins > kSpinLimit) { ok = 0; break; }
+      if (spins > 256) __nanosleep(32);
+    }
     if (!ok) { ctrl->wait_timeout = 1; ctrl->done = 1; ctrl->status = SPS_ERR_CUDA; }
     ok_sh = ok;
   }
