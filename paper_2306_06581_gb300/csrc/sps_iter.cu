@@ -375,38 +375,70 @@ __device__ __forceinline__ void load_unit(UnitCache<T>* c, const int* ustart, in
 // completes when it has landed; `par` holds the two barriers' phase bits.
 // Element k of a row goes to lane (k - start of the row's piece in the chunk)
 // mod 32; a lane's partial sum carries over chunk boundaries.
+// Chunk ch of a unit's aligned element range [kA, kE) into ring slot ch & 1 (lane 0).
+template <typename V>
+__device__ __forceinline__ void ring_issue(const int* idx, const V* val, int kA, int kE, int ch, int* ridx, V* rval,
+                                           uint64_t* bars, int ring) {
+  const int cs = kA + ch * ring;
+  const unsigned cnt = (unsigned)(min(cs + ring, kE) - cs);
+  const int h = ch & 1;
+  fence_proxy_async_shared();
+  mbar_arrive_expect_tx(bars + h, cnt * (unsigned)(sizeof(int) + sizeof(V)));
+  bulk_copy_g2s(ridx + h * ring, idx + cs, cnt * (unsigned)sizeof(int), bars + h);
+  bulk_copy_g2s(rval + h * ring, val + cs, cnt * (unsigned)sizeof(V), bars + h);
+}
+
+template <typename T>
+__device__ __forceinline__ int ring_chunks(const UnitCache<T>* c, int ring) {
+  const int kA = c->p[0] & ~15, kE = (c->p[c->nr] + 15) & ~15;
+  return (kE - kA + ring - 1) / ring;
+}
+
+// The unit's first two chunks, issued ahead (the ring must be free).
+template <typename V, typename T>
+__device__ __forceinline__ void ring_start(const UnitCache<T>* c, const int* idx, const V* val, int* ridx, V* rval,
+                                           uint64_t* bars, int ring) {
+  if ((threadIdx.x & 31) == 0) {
+    const int kA = c->p[0] & ~15, kE = (c->p[c->nr] + 15) & ~15;
+    const int nch = (kE - kA + ring - 1) / ring;
+    if (nch > 0) ring_issue<V>(idx, val, kA, kE, 0, ridx, rval, bars, ring);
+    if (nch > 1) ring_issue<V>(idx, val, kA, kE, 1, ridx, rval, bars, ring);
+  }
+}
+
+// Bounded wait for chunk ch's slot; false when it gave up.
+__device__ __forceinline__ bool ring_wait(uint64_t* bars, unsigned& par, int ch) {
+  const int h = ch & 1;
+  bool ok = true;
+  long long polls = 0;
+  while (!mbar_try_wait(bars + h, (par >> h) & 1u)) {
+    if (++polls > kSpinLimit) { ok = false; break; }
+  }
+  par ^= 1u << h;
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Wait for the chunks ring_start issued and use none of them (before an exit).
+template <typename T>
+__device__ __forceinline__ void ring_drain(const UnitCache<T>* c, uint64_t* bars, unsigned& par, int ring) {
+  const int nch = min(ring_chunks(c, ring), 2);
+  for (int ch = 0; ch < nch; ++ch) ring_wait(bars, par, ch);
+}
+
 template <typename V, typename T>
 __device__ __forceinline__ bool unit_products(const UnitCache<T>* c, int nr, const int* __restrict__ idx,
                                               const V* val, const T* x, int* ridx, V* rval, uint64_t* bars,
-                                              unsigned& par, int ring, T* q_out) {
+                                              unsigned& par, int ring, bool started, T* q_out) {
   const int lane = threadIdx.x & 31;
   const int k0 = c->p[0], k1 = c->p[nr];
   const int kA = k0 & ~15, kE = (k1 + 15) & ~15;
   const int nch = (kE - kA + ring - 1) / ring;
-  auto issue = [&](int ch) {   // lane 0
-    const int cs = kA + ch * ring;
-    const unsigned cnt = (unsigned)(min(cs + ring, kE) - cs);
-    const int h = ch & 1;
-    fence_proxy_async_shared();
-    mbar_arrive_expect_tx(bars + h, cnt * (unsigned)(sizeof(int) + sizeof(V)));
-    bulk_copy_g2s(ridx + h * ring, idx + cs, cnt * (unsigned)sizeof(int), bars + h);
-    bulk_copy_g2s(rval + h * ring, val + cs, cnt * (unsigned)sizeof(V), bars + h);
-  };
-  if (lane == 0) {
-    if (nch > 0) issue(0);
-    if (nch > 1) issue(1);
-  }
+  if (!started) ring_start<V, T>(c, idx, val, ridx, rval, bars, ring);
   int i = 0, re = c->p[1];
   T acc = 0, mine = 0;
-  bool ok = true;
   for (int ch = 0; ch < nch; ++ch) {
     const int h = ch & 1;
-    long long polls = 0;
-    while (!mbar_try_wait(bars + h, (par >> h) & 1u)) {
-      if (++polls > kSpinLimit) { ok = false; break; }
-    }
-    par ^= 1u << h;
-    if (!__all_sync(0xffffffffu, ok)) return false;
+    if (!ring_wait(bars, par, ch)) return false;
     const int cs = kA + ch * ring;
     const int* si = ridx + h * ring - cs;
     const V* sv = rval + h * ring - cs;
@@ -414,6 +446,7 @@ __device__ __forceinline__ bool unit_products(const UnitCache<T>* c, int nr, con
     int k = max(cs, k0);
     while (k < kend) {
       const int pe = min(re, kend);
+#pragma unroll 4
       for (int kk = k + lane; kk < pe; kk += 32) acc += load_as<T>(sv + kk) * x[si[kk]];
       k = pe;
       if (k == re) {   // the row ends here (an empty row ends at once)
@@ -425,7 +458,7 @@ __device__ __forceinline__ bool unit_products(const UnitCache<T>* c, int nr, con
       }
     }
     __syncwarp();   // slot h is read
-    if (lane == 0 && ch + 2 < nch) issue(ch + 2);
+    if (lane == 0 && ch + 2 < nch) ring_issue<V>(idx, val, kA, kE, ch + 2, ridx, rval, bars, ring);
   }
   *q_out = mine;   // rows left open are empty: 0
   return true;
@@ -439,7 +472,8 @@ template <typename V, typename T, bool UOT, bool ROW>
 __device__ __forceinline__ bool unit_phase(const int* ustart, int U, const int* ptr, const int* idx, const V* val,
                                            const T* x, const T* wgt, const T* xcur, T* xnew, UnitCache<T>* c0,
                                            UnitCache<T>* scratch, int worker, int W, T phi, T inv_phi, T (&s)[3],
-                                           int* ridx, V* rval, uint64_t* bars, unsigned& par, int ring) {
+                                           int* ridx, V* rval, uint64_t* bars, unsigned& par, int ring,
+                                           bool first_started) {
   const int lane = threadIdx.x & 31;
   int k = 0;
   for (int u = worker; u < U; u += W, ++k) {
@@ -450,7 +484,8 @@ __device__ __forceinline__ bool unit_phase(const int* ustart, int U, const int* 
     }
     const int nr = c->nr;
     T q;
-    if (!unit_products<V, T>(c, nr, idx, val, x, ridx, rval, bars, par, ring, &q)) return false;
+    if (!unit_products<V, T>(c, nr, idx, val, x, ridx, rval, bars, par, ring, k == 0 && first_started, &q))
+      return false;
     if (lane < nr) {
       const T wi = c->w[lane], xo = c->x[lane];
       T xn;
@@ -569,45 +604,66 @@ __global__ void __launch_bounds__(kUnitThreads, 1) k_iterate_units(IterArgs A, i
     load_unit(ucache + 0, A.unit_r, Ur, A.row_ptr, a, (const T*)A.ubuf + (size_t)(t & 1) * A.n, worker);
     load_unit(ucache + 1, A.unit_c, Uc, A.col_ptr, b, (const T*)A.vbuf + (size_t)(t & 1) * A.m, worker);
   }
+  // The index and value arrays do not change: the first chunks of a warp's
+  // next unit are issued before the grid barrier that precedes its phase.
+  const bool has_r = !reducer && worker < Ur, has_c = !reducer && worker < Uc;
+  int pre = 0;   // 1: row unit started, 2: column unit started
+  auto bail = [&]() {
+    if (pre) ring_drain(ucache + (pre - 1), bars, par, ring);
+  };
+  if (has_r) {
+    ring_start<V, T>(ucache + 0, A.col_idx, val, ridx, rval, bars, ring);
+    pre = 1;
+  }
   for (int k = 0; k < iters; ++k) {
     const T* v = (const T*)A.vbuf + (size_t)(t & 1) * A.m;
     const T* uold = (const T*)A.ubuf + (size_t)(t & 1) * A.n;
     T* unew = (T*)A.ubuf + (size_t)((t + 1) & 1) * A.n;
     T* vnew = (T*)A.vbuf + (size_t)((t + 1) & 1) * A.m;
     T s3[3] = {(T)0, (T)0, (T)0};
-    if (STAGE && !stage_vector<T>(xs, v, A.m, bar, parity, ctrl)) return;
+    if (STAGE && !stage_vector<T>(xs, v, A.m, bar, parity, ctrl)) { bail(); return; }
     if (!reducer &&
         !unit_phase<V, T, UOT, true>(A.unit_r, Ur, A.row_ptr, A.col_idx, val, STAGE ? (const T*)xs : v, a, uold,
                                      unew, ucache + 0, ucache + 2, worker, W, phi, inv_phi, s3, ridx, rval, bars, par,
-                                     ring))
+                                     ring, pre == 1))
       wait_failed(ctrl);
+    pre = 0;
+    if (has_c) {
+      ring_start<V, T>(ucache + 1, A.row_idx, valT, ridx, rval, bars, ring);
+      pre = 2;
+    }
     block_sum_multi<3, T>(s3, sh);
     if (threadIdx.x == 0) {
       A.part[0 * (size_t)A.nblk + blockIdx.x] = (double)s3[0];
       A.part[1 * (size_t)A.nblk + blockIdx.x] = (double)s3[1];
       A.part[2 * (size_t)A.nblk + blockIdx.x] = (double)s3[2];
     }
-    if (!grid_barrier_count(ctrl)) return;
+    if (!grid_barrier_count(ctrl)) { bail(); return; }
     if (reducer) {
       double tot[3];
       reduce_parts_warp<3, T>(A.part, A.nblk, tot);
       if (lane == 0) decide_row(ctrl, S, A, t, tot);
     }
     T s2[3] = {(T)0, (T)0, (T)0};
-    if (STAGE && !stage_vector<T>(xs, unew, A.n, bar, parity, ctrl)) return;
+    if (STAGE && !stage_vector<T>(xs, unew, A.n, bar, parity, ctrl)) { bail(); return; }
     if (!reducer &&
         !unit_phase<V, T, UOT, false>(A.unit_c, Uc, A.col_ptr, A.row_idx, valT, STAGE ? (const T*)xs : unew, b,
                                       (const T*)A.vbuf + (size_t)(t & 1) * A.m, vnew, ucache + 1, ucache + 2, worker,
-                                      W, phi, inv_phi, s2, ridx, rval, bars, par, ring))
+                                      W, phi, inv_phi, s2, ridx, rval, bars, par, ring, pre == 2))
       wait_failed(ctrl);
+    pre = 0;
+    if (has_r && k + 1 < iters) {
+      ring_start<V, T>(ucache + 0, A.col_idx, val, ridx, rval, bars, ring);
+      pre = 1;
+    }
     T c2[2] = {s2[0], s2[1]};
     block_sum_multi<2, T>(c2, sh);
     if (threadIdx.x == 0) {
       A.part[3 * (size_t)A.nblk + blockIdx.x] = (double)c2[0];
       A.part[4 * (size_t)A.nblk + blockIdx.x] = (double)c2[1];
     }
-    if (!grid_barrier_count(ctrl)) return;
-    if (*(volatile int*)&ctrl->done) return;
+    if (!grid_barrier_count(ctrl)) { bail(); return; }
+    if (*(volatile int*)&ctrl->done) { bail(); return; }
     if (reducer) {
       double tot[2];
       reduce_parts_warp<2, T>(A.part + 3 * (size_t)A.nblk, A.nblk, tot);
