@@ -90,6 +90,14 @@ def load():
             _lib.orc_sample_row.restype = i32
             _lib.orc_sparsify.argtypes = [P] + [P] * 10 + [P]
             _lib.orc_sparsify.restype = i64
+            _lib.orc_sparsify_skip.argtypes = [P] + [P] * 10 + [P]
+            _lib.orc_sparsify_skip.restype = i64
+            _lib.orc_log1m32_vec.argtypes = [P, P, i64]
+            _lib.orc_skip_words.argtypes = [u64, u32, u32, u32, P]
+            _lib.orc_colf_max.argtypes = [P, i32]
+            _lib.orc_colf_max.restype = C.c_float
+            _lib.orc_skip_row.argtypes = [P, P, P, P, C.c_float, i32, P, P, P, P, P]
+            _lib.orc_skip_row.restype = i32
             _lib.orc_dense_kernel.argtypes = [P, P, P]
             _lib.orc_dense_kernel.restype = C.c_int
             _lib.orc_sinkhorn_sparse.argtypes = [i32, i32, P, P, P, P, P, P, P, P, f64, f64, f64,
@@ -148,6 +156,23 @@ def log32(x):
     y = np.empty_like(x)
     lib.orc_log32_vec(_ptr(x), _ptr(y), x.size)
     return y
+
+
+def log1m32(q):
+    """Spec log(1 - q) in binary32, 0 < q < 1 (skip sampler gaps)."""
+    lib = load()
+    q = _c(np.ravel(q), np.float32)
+    y = np.empty_like(q)
+    lib.orc_log1m32_vec(_ptr(q), _ptr(y), q.size)
+    return y
+
+
+def skip_words(seed, pid, i, t):
+    """The two Philox words of candidate t of row i in the skip sampler."""
+    lib = load()
+    w = np.empty(2, np.uint32)
+    lib.orc_skip_words(int(seed), int(pid), int(i), int(t), _ptr(w))
+    return int(w[0]), int(w[1])
 
 
 def exact_sum_f32(x):
@@ -223,9 +248,39 @@ class OracleProblem:
         return {"cols": cols[:c].copy(), "val": val[:c].copy(), "logval": logv[:c].copy(),
                 "pstar": ps[:c].copy(), "cost": cost[:c].copy()}
 
-    def sparsify(self):
+    def skip_row(self, i):
+        """Row i of the skip sampler's sketch (balanced OT only)."""
         lib = load()
-        _, nnz = self.count()
+        rowf, colf, S = self.factors()
+        cmax = lib.orc_colf_max(_ptr(colf), self.m)
+        m = self.m
+        cols = np.empty(m, np.int32)
+        val = np.empty(m, np.float64)
+        logv = np.empty(m, np.float64)
+        ps = np.empty(m, np.float32)
+        cost = np.empty(m, np.float64)
+        c = lib.orc_skip_row(C.byref(self.struct), _ptr(rowf), _ptr(colf), C.byref(S), cmax, int(i),
+                             _ptr(cols), _ptr(val), _ptr(logv), _ptr(ps), _ptr(cost))
+        return {"cols": cols[:c].copy(), "val": val[:c].copy(), "logval": logv[:c].copy(),
+                "pstar": ps[:c].copy(), "cost": cost[:c].copy()}
+
+    def skip_count(self):
+        """Row counts of the skip sampler's sketch (O(sampled) work)."""
+        lib = load()
+        rowf, colf, S = self.factors()
+        cmax = lib.orc_colf_max(_ptr(colf), self.m)
+        cnt = np.array([lib.orc_skip_row(C.byref(self.struct), _ptr(rowf), _ptr(colf), C.byref(S), cmax, i,
+                                         None, None, None, None, None) for i in range(self.n)], np.int32)
+        return cnt, int(cnt.sum())
+
+    def sparsify(self, sampler="element"):
+        """Full sketch.  sampler: "element" (one decision per element) or
+        "skip" (geometric skips with thinning; balanced OT only)."""
+        lib = load()
+        if sampler == "skip":
+            _, nnz = self.skip_count()
+        else:
+            _, nnz = self.count()
         n, m = self.n, self.m
         out = {
             "row_ptr": np.empty(n + 1, np.int32), "col_idx": np.empty(nnz, np.int32),
@@ -236,7 +291,8 @@ class OracleProblem:
         }
         S = Scalars()
         k = ["row_ptr", "col_idx", "val", "logval", "pstar", "cost", "col_ptr", "row_idx", "valT", "perm"]
-        got = lib.orc_sparsify(C.byref(self.struct), *[_ptr(out[x]) for x in k], C.byref(S))
+        fn = lib.orc_sparsify_skip if sampler == "skip" else lib.orc_sparsify
+        got = fn(C.byref(self.struct), *[_ptr(out[x]) for x in k], C.byref(S))
         if got != nnz:
             raise RuntimeError("sparsify count mismatch")
         out["nnz"] = nnz
@@ -377,6 +433,7 @@ def dense_sinkhorn(prob: OracleProblem, tol=1e-6, max_iter=1000, stop_rule=STOP_
             "terms": terms, "obj": r1, "K": K, "C": Cn}
 
 
-__all__ = ["build_oracle", "load", "philox4x32_10", "draw24", "exp32", "log32", "exact_sum_f32",
+__all__ = ["build_oracle", "load", "philox4x32_10", "draw24", "exp32", "log32", "log1m32", "skip_words",
+           "exact_sum_f32",
            "OracleProblem", "sinkhorn_sparse", "sinkhorn_dense", "sinkhorn_log_sparse",
            "objective_terms", "spar_sink", "dense_sinkhorn", "STOP_RESIDUAL", "STOP_DELTA_UV"]

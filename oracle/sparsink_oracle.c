@@ -393,6 +393,19 @@ int64_t orc_count(const orc_problem* P, const float* rowf, const float* colf,
   return total;
 }
 
+/* Value of a sampled element (i, j) with p* = ps, written at position c. */
+static void emit_elem(const orc_problem* P, const orc_scalars* S, int32_t i, int32_t j, float ps, int32_t c,
+                      int32_t* cols, double* val, double* logval, float* pstar, double* cost) {
+  double d64 = raw_cost64(P, i, j);
+  double Cn = d64 / cost_divisor(P, S);
+  double Kij = exp(-Cn / P->eps);
+  if (cols) cols[c] = j;
+  if (val) val[c] = Kij / (double)ps;
+  if (logval) logval[c] = -Cn / P->eps - log((double)ps);
+  if (pstar) pstar[c] = ps;
+  if (cost) cost[c] = Cn;
+}
+
 int32_t orc_sample_row(const orc_problem* P, const float* rowf, const float* colf,
                        const orc_scalars* S, int32_t i, int32_t* cols, double* val,
                        double* logval, float* pstar, double* cost) {
@@ -400,35 +413,131 @@ int32_t orc_sample_row(const orc_problem* P, const float* rowf, const float* col
   for (int32_t j = 0; j < P->m; ++j) {
     float ps;
     if (!sample_elem(P, rowf, colf, S, i, j, &ps)) continue;
-    double d64 = raw_cost64(P, i, j);
-    double Cn = d64 / cost_divisor(P, S);
-    double Kij = exp(-Cn / P->eps);
-    if (cols) cols[c] = j;
-    if (val) val[c] = Kij / (double)ps;
-    if (logval) logval[c] = -Cn / P->eps - log((double)ps);
-    if (pstar) pstar[c] = ps;
-    if (cost) cost[c] = Cn;
+    emit_elem(P, S, i, j, ps, c, cols, val, logval, pstar, cost);
     ++c;
   }
   return c;
 }
 
-int64_t orc_sparsify(const orc_problem* P, int32_t* row_ptr, int32_t* col_idx, double* val,
-                     double* logval, float* pstar, double* cost, int32_t* col_ptr,
-                     int32_t* row_idx, double* valT, int32_t* perm, orc_scalars* S) {
+/* ======================================================================
+ * Skip sampler for the separable OT probabilities p_ij = r_i c_j: the same
+ * law as one Bernoulli(p*_ij) decision per element, with work proportional
+ * to the sampled count instead of n m.  Thinning construction: q_i =
+ * min(1, fl(r_i cmax)) bounds every p_ij = fl(r_i c_j) of row i (rounding is
+ * monotone), cmax = max_j c_j.  Candidates form a Bernoulli(q_i) process
+ * over j = 0 .. m-1, generated by geometric gaps: with U uniform on (0, 1],
+ * G = floor(log U / log(1 - q_i)) has P(G >= k) = P(U <= (1 - q_i)^k) =
+ * (1 - q_i)^k.  A candidate j is kept when V < fl(p_ij / q_i), V uniform on
+ * [0, 1), so j is kept with probability q_i (p_ij / q_i) = p_ij,
+ * independently of every other element (to the 2^-24 resolution of U, V).
+ * Draws: candidate t of row i reads Philox4x32-10 at counter (t >> 1, i,
+ * pid, 0x5B1E) under key (seed), words 2(t & 1) (gap) and 2(t & 1) + 1
+ * (acceptance); U = ((w >> 8) + 1) 2^-24, V = (w >> 8) 2^-24.  Every step is
+ * the binary32 operation written here (log1m and log are the spec's).
+ * Pinned by tests/test_oracle_skip.py (inclusion frequencies, pairwise
+ * independence, expected count, degenerate rows).
+ * ====================================================================== */
+
+/* log(1 - q) for 0 < q < 1: the spec log of 1 - q for q >= 1/4; below, 2
+ * atanh(z) with z = -q / (2 - q) (|z| <= 1/7) by its series to z^13. */
+float orc_log1m32(float q) {
+  if (q >= 0.25f) return orc_log32(1.0f - q);
+  float z = -q / (2.0f - q);
+  float w = z * z;
+  float P = (float)(1.0 / 13.0);
+  P = fmaf(P, w, (float)(1.0 / 11.0));
+  P = fmaf(P, w, (float)(1.0 / 9.0));
+  P = fmaf(P, w, (float)(1.0 / 7.0));
+  P = fmaf(P, w, 0.2f);
+  P = fmaf(P, w, (float)(1.0 / 3.0));
+  float z2 = z + z;
+  return fmaf(z2, w * P, z2);
+}
+
+void orc_log1m32_vec(const float* q, float* y, int64_t n) {
+  for (int64_t k = 0; k < n; ++k) y[k] = orc_log1m32(q[k]);
+}
+
+void orc_skip_words(uint64_t seed, uint32_t pid, uint32_t i, uint32_t t, uint32_t w[2]) {
+  uint32_t ctr[4] = {t >> 1, i, pid, 0x5B1Eu};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
+  w[0] = out[2u * (t & 1u)];
+  w[1] = out[2u * (t & 1u) + 1u];
+}
+
+/* The largest column factor (a maximum is exact). */
+float orc_colf_max(const float* colf, int32_t m) {
+  float c = 0.0f;
+  for (int32_t j = 0; j < m; ++j) if (colf[j] > c) c = colf[j];
+  return c;
+}
+
+int32_t orc_skip_row(const orc_problem* P, const float* rowf, const float* colf, const orc_scalars* S,
+                     float cmax, int32_t i, int32_t* cols, double* val, double* logval, float* pstar,
+                     double* cost) {
+  const float r = rowf[i];
+  const float q = r * cmax;
+  if (!(q > 0.0f)) return 0;
+  const int full = q >= 1.0f;
+  const float L = full ? 0.0f : orc_log1m32(q);
+  int64_t j = -1;
+  int32_t c = 0;
+  for (uint32_t t = 0;; ++t) {
+    uint32_t w[2];
+    orc_skip_words(P->seed, P->pid, (uint32_t)i, t, w);
+    if (full) {
+      j += 1;
+    } else {
+      const float U = (float)((w[0] >> 8) + 1u) * 0x1p-24f;
+      const float ratio = orc_log32(U) / L;
+      if (!(ratio < (float)P->m)) break;
+      j += 1 + (int64_t)floorf(ratio);
+    }
+    if (j >= P->m) break;
+    const float p = r * colf[j];
+    const float acc = full ? p : p / q;
+    const float V = (float)(w[1] >> 8) * 0x1p-24f;
+    if (V < acc) {
+      emit_elem(P, S, i, (int32_t)j, p < 1.0f ? p : 1.0f, c, cols, val, logval, pstar, cost);
+      ++c;
+    }
+  }
+  return c;
+}
+
+static int64_t sparsify_impl(const orc_problem* P, int skip, int32_t* row_ptr, int32_t* col_idx, double* val,
+                             double* logval, float* pstar, double* cost, int32_t* col_ptr,
+                             int32_t* row_idx, double* valT, int32_t* perm, orc_scalars* S) {
   const int32_t n = P->n, m = P->m;
+  if (skip && !is_ot(P)) return -1;
   float* rowf = (float*)malloc(sizeof(float) * (size_t)n);
   float* colf = (float*)malloc(sizeof(float) * (size_t)m);
   if (orc_factors(P, rowf, colf, S)) { free(rowf); free(colf); return -1; }
+  const float cmax = skip ? orc_colf_max(colf, m) : 0.0f;
   int32_t* cnt = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-  int64_t nnz = orc_count(P, rowf, colf, S, cnt);
+  int64_t nnz = 0;
+  if (skip) {
+#pragma omp parallel for reduction(+ : nnz) schedule(dynamic, 64)
+    for (int32_t i = 0; i < n; ++i) {
+      cnt[i] = orc_skip_row(P, rowf, colf, S, cmax, i, NULL, NULL, NULL, NULL, NULL);
+      nnz += cnt[i];
+    }
+  } else {
+    nnz = orc_count(P, rowf, colf, S, cnt);
+  }
   row_ptr[0] = 0;
   for (int32_t i = 0; i < n; ++i) row_ptr[i + 1] = row_ptr[i] + cnt[i];
 #pragma omp parallel for schedule(dynamic, 8)
   for (int32_t i = 0; i < n; ++i) {
     int64_t o = row_ptr[i];
-    orc_sample_row(P, rowf, colf, S, i, col_idx + o, val ? val + o : NULL,
-                   logval ? logval + o : NULL, pstar ? pstar + o : NULL, cost ? cost + o : NULL);
+    if (skip)
+      orc_skip_row(P, rowf, colf, S, cmax, i, col_idx + o, val ? val + o : NULL, logval ? logval + o : NULL,
+                   pstar ? pstar + o : NULL, cost ? cost + o : NULL);
+    else
+      orc_sample_row(P, rowf, colf, S, i, col_idx + o, val ? val + o : NULL,
+                     logval ? logval + o : NULL, pstar ? pstar + o : NULL, cost ? cost + o : NULL);
   }
   /* stable transpose: rows ascending inside every column */
   if (col_ptr) {
@@ -451,6 +560,18 @@ int64_t orc_sparsify(const orc_problem* P, int32_t* row_ptr, int32_t* col_idx, d
   free(rowf);
   free(colf);
   return nnz;
+}
+
+int64_t orc_sparsify(const orc_problem* P, int32_t* row_ptr, int32_t* col_idx, double* val,
+                     double* logval, float* pstar, double* cost, int32_t* col_ptr,
+                     int32_t* row_idx, double* valT, int32_t* perm, orc_scalars* S) {
+  return sparsify_impl(P, 0, row_ptr, col_idx, val, logval, pstar, cost, col_ptr, row_idx, valT, perm, S);
+}
+
+int64_t orc_sparsify_skip(const orc_problem* P, int32_t* row_ptr, int32_t* col_idx, double* val,
+                          double* logval, float* pstar, double* cost, int32_t* col_ptr,
+                          int32_t* row_idx, double* valT, int32_t* perm, orc_scalars* S) {
+  return sparsify_impl(P, 1, row_ptr, col_idx, val, logval, pstar, cost, col_ptr, row_idx, valT, perm, S);
 }
 
 int orc_dense_kernel(const orc_problem* P, double* K, double* Cn) {
