@@ -362,6 +362,8 @@ def run_ours(args):
 
     def solve(**extra):
         k = dict(kw, kdtype=kd, log_domain=logd)
+        if not uot:
+            k["sampler"] = args.sampler
         k.update(extra)
         if uot:
             return S.spar_sink_uot(k.pop("a", a), k.pop("b", b), k.pop("x", x), k.pop("y", y), lam=w.lam, **k)
@@ -434,10 +436,30 @@ def run_ours(args):
                            "extrapolated_ms_at_spar_sink_iters": round(est, 1),
                            "speedup_of_spar_sink_extrapolated": round(est / ms, 2)})
 
+    # balanced OT: the same solve with the other sampler (same law, another random stream)
+    other = None
+    if not uot and rank == 0:
+        alt = "skip" if args.sampler == "element" else "element"
+        ro = solve(sampler=alt)
+        tms = []
+        for _ in range(3):
+            flush_buf.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ro = solve(sampler=alt, workspace=ro["workspace"])
+            e1.record(st)
+            e1.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        other = {"sampler": alt, "ms": round(sum(tms) / len(tms), 4),
+                 "phases_ms": {"sketch": round(ro["ms_sketch"], 4), "iterations": round(ro["ms_iter"], 4),
+                               "objective": round(ro["ms_obj"], 4)},
+                 "iters": ro["iters"], "nnz": ro["nnz"], "obj": ro["obj"],
+                 "rel_obj_diff": abs(ro["obj"] - last["obj"]) / abs(last["obj"])}
+
     # storage precision forms of the stabilised path against the stored FP64 oracle value
     precision = None
     gold = _golden(w)
-    if logd and rank == 0 and gold is not None:
+    if logd and rank == 0 and gold is not None and (uot or args.sampler == "element"):
         precision = {}
         for k2 in ("f32", "bf16", "f16"):
             rr = solve(kdtype=k2)
@@ -485,6 +507,9 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    line["config"]["sampler"] = "element" if uot else args.sampler
+    if other is not None:
+        line["other_sampler"] = other
     if precision is not None:
         line["precision_forms"] = precision
     if args.warm_start:
@@ -680,6 +705,8 @@ def main():
     ap.add_argument("--dense-cap", type=int, default=0,
                     help="stop dense Sinkhorn after this many iterations and extrapolate (0: run to tolerance)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sampler", default="element", choices=["element", "skip"],
+                    help="sketch draws: one decision per element, or geometric skips (balanced OT only)")
     ap.add_argument("--n", type=int, default=None, help="profiling: the workload's family at another size")
     ap.add_argument("--solve-only", action="store_true", help="profiling: two solves, no timing loop")
     ap.add_argument("--warm-start", action="store_true", help="also train and time the learned warm start")

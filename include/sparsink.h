@@ -104,10 +104,23 @@ typedef struct {
                           about 8 standard deviations above its mean) the two passes run
                           instead.  SPS_SKETCH_TWO_PASS (1): count, then fill.  Both give the
                           same sketch bit for bit. */
+  int32_t sampler;     /* How the sketch draws Eq. (pois).  SPS_SAMPLER_ELEMENT (0): one
+                          Philox decision per element (n m work; every (i, j) tested).
+                          SPS_SAMPLER_SKIP (1), balanced OT only (lambda = +inf; else
+                          SPS_ERR_INVALID_ARG): the separable probabilities of Eq. (pij-ot)
+                          let every row draw its kept columns by geometric gaps over a bound
+                          q_i = min(1, r_i max_j c_j) followed by thinning with p_ij / q_i --
+                          the same law (each element kept independently with probability
+                          p*_ij) from a different random stream, with work proportional to the
+                          sampled count.  sketch_mode does not apply to it; spar_sink_batched
+                          accepts SPS_SAMPLER_ELEMENT only. */
 } sps_params;
 
 #define SPS_SKETCH_SINGLE 0
 #define SPS_SKETCH_TWO_PASS 1
+
+#define SPS_SAMPLER_ELEMENT 0
+#define SPS_SAMPLER_SKIP 1
 
 #define SPS_GATHER_AUTO 0
 #define SPS_GATHER_DIRECT 1

@@ -98,6 +98,8 @@ def load():
             _lib.orc_colf_max.restype = C.c_float
             _lib.orc_skip_row.argtypes = [P, P, P, P, C.c_float, i32, P, P, P, P, P]
             _lib.orc_skip_row.restype = i32
+            _lib.orc_skip_count.argtypes = [P, P, P, P, P]
+            _lib.orc_skip_count.restype = i64
             _lib.orc_dense_kernel.argtypes = [P, P, P]
             _lib.orc_dense_kernel.restype = C.c_int
             _lib.orc_sinkhorn_sparse.argtypes = [i32, i32, P, P, P, P, P, P, P, P, f64, f64, f64,
@@ -268,10 +270,9 @@ class OracleProblem:
         """Row counts of the skip sampler's sketch (O(sampled) work)."""
         lib = load()
         rowf, colf, S = self.factors()
-        cmax = lib.orc_colf_max(_ptr(colf), self.m)
-        cnt = np.array([lib.orc_skip_row(C.byref(self.struct), _ptr(rowf), _ptr(colf), C.byref(S), cmax, i,
-                                         None, None, None, None, None) for i in range(self.n)], np.int32)
-        return cnt, int(cnt.sum())
+        cnt = np.empty(self.n, np.int32)
+        nnz = lib.orc_skip_count(C.byref(self.struct), _ptr(rowf), _ptr(colf), C.byref(S), _ptr(cnt))
+        return cnt, int(nnz)
 
     def sparsify(self, sampler="element"):
         """Full sketch.  sampler: "element" (one decision per element) or

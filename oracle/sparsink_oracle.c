@@ -507,6 +507,19 @@ int32_t orc_skip_row(const orc_problem* P, const float* rowf, const float* colf,
   return c;
 }
 
+/* Row counts of the skip sampler's sketch (row_cnt[n]); returns the total. */
+int64_t orc_skip_count(const orc_problem* P, const float* rowf, const float* colf, const orc_scalars* S,
+                       int32_t* row_cnt) {
+  const float cmax = orc_colf_max(colf, P->m);
+  int64_t nnz = 0;
+#pragma omp parallel for reduction(+ : nnz) schedule(dynamic, 64)
+  for (int32_t i = 0; i < P->n; ++i) {
+    row_cnt[i] = orc_skip_row(P, rowf, colf, S, cmax, i, NULL, NULL, NULL, NULL, NULL);
+    nnz += row_cnt[i];
+  }
+  return nnz;
+}
+
 static int64_t sparsify_impl(const orc_problem* P, int skip, int32_t* row_ptr, int32_t* col_idx, double* val,
                              double* logval, float* pstar, double* cost, int32_t* col_ptr,
                              int32_t* row_idx, double* valT, int32_t* perm, orc_scalars* S) {
@@ -519,11 +532,7 @@ static int64_t sparsify_impl(const orc_problem* P, int skip, int32_t* row_ptr, i
   int32_t* cnt = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
   int64_t nnz = 0;
   if (skip) {
-#pragma omp parallel for reduction(+ : nnz) schedule(dynamic, 64)
-    for (int32_t i = 0; i < n; ++i) {
-      cnt[i] = orc_skip_row(P, rowf, colf, S, cmax, i, NULL, NULL, NULL, NULL, NULL);
-      nnz += cnt[i];
-    }
+    nnz = orc_skip_count(P, rowf, colf, S, cnt);
   } else {
     nnz = orc_count(P, rowf, colf, S, cnt);
   }

@@ -134,6 +134,8 @@ float orc_colf_max(const float* colf, int32_t m);
 int32_t orc_skip_row(const orc_problem* P, const float* rowf, const float* colf, const orc_scalars* S,
                      float cmax, int32_t i, int32_t* cols, double* val, double* logval, float* pstar,
                      double* cost);
+int64_t orc_skip_count(const orc_problem* P, const float* rowf, const float* colf, const orc_scalars* S,
+                       int32_t* row_cnt);
 int64_t orc_sparsify_skip(const orc_problem* P, int32_t* row_ptr, int32_t* col_idx, double* val,
                           double* logval, float* pstar, double* cost, int32_t* col_ptr,
                           int32_t* row_idx, double* valT, int32_t* perm, orc_scalars* S);

@@ -140,7 +140,8 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
     const double cells = (double)n * g.nchunk;
     double pcap = ceil(1.001 * Q->s + 8.0 * sqrt(cells * Q->s) + 17.0 * cells + 1024.0);
     pcap = std::min(pcap, (double)n * (double)m);
-    if (Q->sketch_mode == SPS_SKETCH_SINGLE && pcap < 2147483000.0 && cells * 2.0 + 1.0 < 2147483000.0) {
+    if (Q->sketch_mode == SPS_SKETCH_SINGLE && Q->sampler == SPS_SAMPLER_ELEMENT && pcap < 2147483000.0 &&
+        cells * 2.0 + 1.0 < 2147483000.0) {
       L->pad_cap = (int64_t)pcap;
       L->pad_ofs = take((size_t)(2 * cells + 1) * 4);
       L->pad_col = take((size_t)pcap * 4);
@@ -213,6 +214,11 @@ static sps_status validate(const sps_problem* P, const sps_params* Q, int op) {
   if (Q->log_domain && Q->absorb_tau < 0.0) { set_error("absorb_tau must be >= 0"); return SPS_ERR_INVALID_ARG; }
   if (Q->gather_mode < SPS_GATHER_AUTO || Q->gather_mode > SPS_GATHER_STAGED) { set_error("unknown gather_mode %d", Q->gather_mode); return SPS_ERR_INVALID_ARG; }
   if (Q->sketch_mode != SPS_SKETCH_SINGLE && Q->sketch_mode != SPS_SKETCH_TWO_PASS) { set_error("unknown sketch_mode %d", Q->sketch_mode); return SPS_ERR_INVALID_ARG; }
+  if (Q->sampler != SPS_SAMPLER_ELEMENT && Q->sampler != SPS_SAMPLER_SKIP) { set_error("unknown sampler %d", Q->sampler); return SPS_ERR_INVALID_ARG; }
+  if (op != SPS_OP_DENSE && Q->sampler == SPS_SAMPLER_SKIP && !isinf(Q->lambda)) {
+    set_error("the skip sampler needs the separable probabilities of balanced OT (lambda = +inf)");
+    return SPS_ERR_INVALID_ARG;
+  }
   if (op != SPS_OP_DENSE && (double)Q->s + 8.0 * sqrt(Q->s) + 1024.0 > 2147483647.0 &&
       (double)P->n * (double)P->m > 2147483647.0) {
     set_error("sample budget too large for int32 indices"); return SPS_ERR_CAPACITY;
@@ -273,7 +279,8 @@ static sps_status run_sketch(const sps_problem* P, const sps_params* Q, const La
   SPS_TRY(launch_prepare(pd, L, ws, it64, st));
   if (P->cost_norm == SPS_COST_MAXNORM) SPS_TRY(launch_cost_max(pd, L, ws, 0, st));
   SPS_TRY(launch_factors(pd, L, ws, st));
-  SPS_TRY(launch_sample(pd, L, ws, Q->kdtype, st));
+  if (Q->sampler == SPS_SAMPLER_SKIP) SPS_TRY(launch_skip_sample(pd, L, ws, Q->kdtype, st));
+  else SPS_TRY(launch_sample(pd, L, ws, Q->kdtype, st));
   SPS_TRY(read_ctrl(L, ws, hctrl, st));
   if (hctrl->status == SPS_OK && hctrl->nnz != hctrl->nnz_cols) {
     set_error("internal error: row and column counts of the sketch disagree (%lld vs %lld)",

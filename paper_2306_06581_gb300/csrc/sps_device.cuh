@@ -109,6 +109,30 @@ __device__ __forceinline__ float spec_log(float x) {
   return __fmaf_rn(fe, 0.693145751953125f, r);
 }
 
+// log(1 - q) for 0 < q < 1 (the skip sampler's gap rate): spec_log(1 - q)
+// for q >= 1/4; below, 2 atanh(z) with z = -q / (2 - q), |z| <= 1/7, by its
+// odd series to z^13.
+__device__ __forceinline__ float spec_log1m(float q) {
+  if (q >= 0.25f) return spec_log(__fsub_rn(1.0f, q));
+  const float z = __fdiv_rn(-q, __fsub_rn(2.0f, q));
+  const float w = __fmul_rn(z, z);
+  float P = (float)(1.0 / 13.0);
+  P = __fmaf_rn(P, w, (float)(1.0 / 11.0));
+  P = __fmaf_rn(P, w, (float)(1.0 / 9.0));
+  P = __fmaf_rn(P, w, (float)(1.0 / 7.0));
+  P = __fmaf_rn(P, w, 0.2f);
+  P = __fmaf_rn(P, w, (float)(1.0 / 3.0));
+  const float z2 = __fadd_rn(z, z);
+  return __fmaf_rn(z2, __fmul_rn(w, P), z2);
+}
+
+// The words of skip-sampler candidates 2c and 2c + 1 of row i: counter
+// (c, i, pid, 0x5B1E); candidate 2c uses (x, y), 2c + 1 uses (z, w), the
+// first word of a pair for the gap and the second for the acceptance.
+__device__ __forceinline__ uint4 skip_words4(uint64_t seed, uint32_t pid, uint32_t i, uint32_t c) {
+  return philox4x32_10(make_uint4(c, i, pid, 0x5B1Eu), (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
 // ---------------------------------------------------------------------------
 // Cost access.  Decision path: binary32 squared distance accumulated in
 // ascending coordinate order, one fused multiply-add per coordinate; or the

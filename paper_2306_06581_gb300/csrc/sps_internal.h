@@ -58,6 +58,7 @@ struct SketchScalars {
   float kappa32;      // UOT: fl32(1/(Dnorm (2 lam + eps)))
   float dn32;         // value path: cost normaliser (binary32)
   double dn64;        // value path: cost normaliser (FP64)
+  float cmax32;       // skip sampler: max_j of the column factors (exact)
   ExactAcc acc1, acc2;
 };
 
@@ -208,6 +209,9 @@ sps_status launch_dense_lse_row_only(const ProbDev& pd, const Layout& L, char* w
 sps_status launch_dense_lse_objective(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic,
                                       void* alpha_out, void* beta_out, cudaStream_t st);
 
+// Skip sampler (balanced OT): count, scan, fill and CSC of the sketch (sps_sweep.cu).
+sps_status launch_skip_sample(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st);
+void launch_csc_sort(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st);
 sps_status launch_cost_max_points(const float* x, int n, const float* y, int m, int d, void* scratch,
                                   cudaStream_t st);
 // Shared with the batched path (sps_sketch.cu)

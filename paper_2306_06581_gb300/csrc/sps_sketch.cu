@@ -478,6 +478,15 @@ void launch_scan_counts(const int* row_cnt, int* row_ptr, int n, const int* col_
   k_scan2<<<2, 1024, 0, st>>>(row_cnt, row_ptr, n, col_cnt, col_ptr, col_cur, m, cap, ctrl);
 }
 
+void launch_csc_sort(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st) {
+  switch (kd) {
+    case SPS_F64: csc_sort<double>(pd, L, ws, st); break;
+    case SPS_F32: csc_sort<float>(pd, L, ws, st); break;
+    case SPS_BF16: csc_sort<__nv_bfloat16>(pd, L, ws, st); break;
+    case SPS_F16: csc_sort<__half>(pd, L, ws, st); break;
+  }
+}
+
 void launch_csc_sort_f32(int m, const int* col_ptr, const int* tmp_row, const int* tmp_src, const float* val,
                          int* row_idx, int* csr_pos, float* valT, Ctrl* ctrl, cudaStream_t st) {
   const int gs = grid_for((int64_t)m * 32, 32 * kSortWarps);

@@ -54,6 +54,7 @@ struct SweepArgs {
   void* pad_val;
   float* pad_lv;
   float* zsum;          // UOT Z sweep: [nchunk][n] sums of w per (row, chunk) (or null)
+  int* cnt_row;         // skip sampler: kept elements per row
 };
 
 template <typename V> struct ValMath;
@@ -437,6 +438,106 @@ SweepGeo sweep_geometry(int n, int m) {
   return g;
 }
 
+// ---------------------------------------------------------------------------
+// Skip sampler for the separable OT probabilities p_ij = r_i c_j (Eq. pij-ot):
+// the law of one Bernoulli(p*_ij) decision per element (Eq. pois) with work
+// proportional to the sampled count.  Row i bounds every p_ij by q_i =
+// min(1, fl(r_i cmax)); candidates form a Bernoulli(q_i) process generated by
+// geometric gaps G = floor(log U / log(1 - q_i)), U = ((w >> 8) + 1) 2^-24
+// on (0, 1]; a candidate j is kept when V < fl(p_ij / q_i), V = (w' >> 8)
+// 2^-24.  Candidate t of row i reads Philox at counter (t >> 1, i, pid,
+// 0x5B1E), words 2 (t & 1) and 2 (t & 1) + 1.  One thread per row (rows are
+// independent; the gaps of a row form a chain); COUNT writes the row counts
+// and the column counts, FILL the CSR entries and the CSC scatter.
+// ---------------------------------------------------------------------------
+enum { SK_COUNT = 0, SK_FILL = 1 };
+
+__global__ void k_colf_max(const float* __restrict__ colf, int m, SketchScalars* sc) {
+  float c = 0.0f;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) c = fmaxf(c, colf[j]);
+  c = warp_max(c);
+  if ((threadIdx.x & 31) == 0 && c > 0.0f) atomicMax(reinterpret_cast<int*>(&sc->cmax32), __float_as_int(c));
+}
+
+template <int MODE, typename V>
+__global__ void __launch_bounds__(256) k_skip(SweepArgs A) {
+  if (A.ctrl->status != SPS_OK) return;
+  const ProbDev& pd = A.pd;
+  const int n = pd.n, m = pd.m, d = pd.d;
+  const float cmax = A.sc->cmax32;
+  const bool lv32 = MODE == SK_FILL && A.logval != nullptr && !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64;
+  float k_hi = 0.0f, k_lo = 0.0f;
+  if (lv32) {
+    const double k64 = 1.0 / (A.sc->dn64 * pd.eps);
+    k_hi = __double2float_rn(k64);
+    k_lo = __double2float_rn(k64 - (double)k_hi);
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float r = A.rowf[i];
+    const float q = __fmul_rn(r, cmax);
+    int cnt = 0;
+    int pos = 0, pend = 0;
+    if (MODE == SK_FILL) { pos = A.row_ptr[i]; pend = A.row_ptr[i + 1]; }
+    if (q > 0.0f) {
+      const bool full = q >= 1.0f;
+      const float L = full ? 0.0f : spec_log1m(q);
+      long long j = -1;
+      uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+      for (uint32_t t = 0;; ++t) {
+        if ((t & 1u) == 0u) w4 = skip_words4(pd.seed, pd.pid, (uint32_t)i, t >> 1);
+        const uint32_t g = (t & 1u) ? w4.z : w4.x;
+        const uint32_t h = (t & 1u) ? w4.w : w4.y;
+        if (full) {
+          j += 1;
+        } else {
+          const float U = __fmul_rn(__uint2float_rn((g >> 8) + 1u), 5.9604644775390625e-08f);
+          const float ratio = __fdiv_rn(spec_log(U), L);
+          if (!(ratio < (float)m)) break;
+          j += 1 + (long long)floorf(ratio);
+        }
+        if (j >= m) break;
+        const int jj = (int)j;
+        const float p = __fmul_rn(r, A.colf[jj]);
+        const float acc = full ? p : __fdiv_rn(p, q);
+        const float Vu = __fmul_rn(__uint2float_rn(h >> 8), 5.9604644775390625e-08f);
+        if (!(Vu < acc)) continue;
+        if (MODE == SK_COUNT) {
+          ++cnt;
+          atomicAdd(&A.col_cnt[jj], 1);
+        } else {
+          if (pos >= pend) {   // count and fill disagree: never write out of range
+            A.ctrl->sketch_fault = 1;
+            break;
+          }
+          const float ps = p < 1.0f ? p : 1.0f;
+          A.col_idx[pos] = jj;
+          if (lv32) {
+            const float ce = cost_over_eps_df(pd.cv.x32 + (int64_t)i * d, pd.cv.y32 + (int64_t)jj * d, d, k_hi, k_lo);
+            A.logval[pos] = __fsub_rn(-ce, logf(ps));
+          } else {
+            reinterpret_cast<V*>(A.val)[pos] =
+                from_d<V>(ValMath<V>::value(pd, *A.sc, i, jj, raw32(pd.cv, i, jj), ps));
+            if (A.logval) {
+              const double C64 = raw64(pd.cv, i, jj) / A.sc->dn64;
+              A.logval[pos] = (float)(-C64 / pd.eps - (double)logf(ps));
+            }
+          }
+          const int slot = atomicAdd(&A.col_cur[jj], 1);
+          if (slot < A.col_end[jj]) {
+            A.tmp_row[slot] = i;
+            A.tmp_src[slot] = pos;
+          } else {
+            A.ctrl->sketch_fault = 1;
+          }
+          ++pos;
+        }
+      }
+    }
+    if (MODE == SK_COUNT) A.cnt_row[i] = cnt;
+    else if (pos != pend) A.ctrl->sketch_fault = 1;
+  }
+}
+
 static SweepArgs base_args(const ProbDev& pd, const Layout& L, char* ws) {
   SweepArgs A;
   memset(&A, 0, sizeof(A));
@@ -553,6 +654,41 @@ void launch_compact(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, 
     case SPS_BF16: compact_v<__nv_bfloat16>(pd, L, ws, st); break;
     case SPS_F16: compact_v<__half>(pd, L, ws, st); break;
   }
+}
+
+template <typename V>
+static void skip_fill_v(const ProbDev& pd, const Layout& L, char* ws, int grid, cudaStream_t st) {
+  SweepArgs A = base_args(pd, L, ws);
+  A.row_ptr = at<int>(ws, L.row_ptr);
+  A.col_idx = at<int>(ws, L.col_idx);
+  A.val = ws + L.val;
+  A.col_cur = at<int>(ws, L.col_cur);
+  A.col_end = at<int>(ws, L.col_ptr) + 1;
+  A.logval = L.logval ? at<float>(ws, L.logval) : nullptr;
+  A.tmp_row = at<int>(ws, L.tmp_row);
+  A.tmp_src = at<int>(ws, L.tmp_src);
+  k_skip<SK_FILL, V><<<grid, 256, 0, st>>>(A);
+}
+
+sps_status launch_skip_sample(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st) {
+  SweepArgs A = base_args(pd, L, ws);
+  A.col_cnt = at<int>(ws, L.col_cnt);
+  A.cnt_row = at<int>(ws, L.row_cnt);
+  const int grid = std::max(1, std::min(152 * 8, (pd.n + 255) / 256));
+  cudaMemsetAsync(A.col_cnt, 0, sizeof(int) * (size_t)pd.m, st);
+  k_colf_max<<<std::max(1, std::min(1024, (pd.m + 255) / 256)), 256, 0, st>>>(A.colf, pd.m, A.sc);
+  k_skip<SK_COUNT, float><<<grid, 256, 0, st>>>(A);
+  launch_scan_counts(A.cnt_row, at<int>(ws, L.row_ptr), pd.n, A.col_cnt, at<int>(ws, L.col_ptr),
+                     at<int>(ws, L.col_cur), pd.m, (long long)L.cap, A.ctrl, st);
+  switch (kd) {
+    case SPS_F64: skip_fill_v<double>(pd, L, ws, grid, st); break;
+    case SPS_F32: skip_fill_v<float>(pd, L, ws, grid, st); break;
+    case SPS_BF16: skip_fill_v<__nv_bfloat16>(pd, L, ws, grid, st); break;
+    case SPS_F16: skip_fill_v<__half>(pd, L, ws, grid, st); break;
+  }
+  launch_csc_sort(pd, L, ws, kd, st);
+  add_launches(5);
+  return cuda_fail(cudaGetLastError(), "skip sample");
 }
 
 }  // namespace sps

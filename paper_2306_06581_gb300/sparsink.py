@@ -51,7 +51,8 @@ class Params(C.Structure):
                 ("max_iter", C.c_int32), ("check_every", C.c_int32), ("stop_rule", C.c_int32),
                 ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("kdtype", C.c_int32),
                 ("log_domain", C.c_int32), ("absorb_tau", C.c_double), ("init_alpha", C.c_void_p),
-                ("init_beta", C.c_void_p), ("gather_mode", C.c_int32), ("sketch_mode", C.c_int32)]
+                ("init_beta", C.c_void_p), ("gather_mode", C.c_int32), ("sketch_mode", C.c_int32),
+                ("sampler", C.c_int32)]
 
 GATHER_AUTO, GATHER_DIRECT, GATHER_STAGED = 0, 1, 2
 
@@ -145,13 +146,16 @@ def make_problem(a, b, x=None, y=None, C_=None, dtype="f32", cost_norm=COST_MAXN
     return Marshalled(p, (a, b, x, y, C_))
 
 
+SAMPLERS = {"element": 0, "skip": 1}
+
+
 def make_params(eps, lam=math.inf, s=1.0, tol=1e-6, max_iter=1000, check_every=0, stop_rule=STOP_RESIDUAL,
                 seed=0x5EED, problem_id=0, kdtype="f32", log_domain=0, absorb_tau=0.0, init_alpha=None,
-                init_beta=None, gather_mode=GATHER_AUTO, sketch_mode=0):
+                init_beta=None, gather_mode=GATHER_AUTO, sketch_mode=0, sampler="element"):
     return Params(float(eps), float(lam), float(s), float(tol), int(max_iter), int(check_every), int(stop_rule),
                   int(seed) & ((1 << 64) - 1), int(problem_id), DTYPE_CODES[kdtype] if isinstance(kdtype, str) else kdtype,
                   int(log_domain), float(absorb_tau), _ptr(init_alpha), _ptr(init_beta), int(gather_mode),
-                  int(sketch_mode))
+                  int(sketch_mode), SAMPLERS[sampler] if isinstance(sampler, str) else int(sampler))
 
 
 def sps_workspace_bytes(prob: Problem, prm: Params, op: int) -> int:
@@ -201,30 +205,33 @@ def _solve(fn_name, prob: Problem, prm: Params, device, op, workspace=None, rais
 def spar_sink_ot(a, b, x=None, y=None, C_=None, *, eps, s, tol=1e-6, max_iter=1000, dtype="f32", kdtype=None,
                  seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL,
                  check_every=0, init_alpha=None, init_beta=None, log_domain=0, absorb_tau=0.0, gather_mode=0, sketch_mode=0, workspace=None,
-                 device=None, raise_on_error=True):
-    """Alg. 3: importance-sparsified Sinkhorn for balanced OT."""
+                 device=None, raise_on_error=True, sampler="element"):
+    """Alg. 3: importance-sparsified Sinkhorn for balanced OT.  sampler="skip"
+    draws the sketch by geometric gaps with thinning (work proportional to the
+    sampled count; the same law as the per-element decisions)."""
     M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
     dev = M.keep[0].device
     kd = kdtype or dtype
     it = torch.float64 if kd == "f64" else torch.float32
     ia, ib = _dev(init_alpha, it, dev), _dev(init_beta, it, dev)
     prm = make_params(eps, math.inf, s, tol, max_iter, check_every, stop_rule, seed, problem_id, kd, log_domain,
-                      absorb_tau, ia, ib, gather_mode, sketch_mode)
+                      absorb_tau, ia, ib, gather_mode, sketch_mode, sampler)
     return _solve("spar_sink_ot", M.prob, prm, dev, OP_SPAR_SINK, workspace, raise_on_error)
 
 
 def spar_sink_uot(a, b, x=None, y=None, C_=None, *, eps, lam, s, tol=1e-6, max_iter=1000, dtype="f32", kdtype=None,
                   seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL,
                   check_every=0, init_alpha=None, init_beta=None, log_domain=0, absorb_tau=0.0, gather_mode=0, sketch_mode=0, workspace=None,
-                  device=None, raise_on_error=True):
-    """Alg. 4: importance-sparsified Sinkhorn for UOT with KL penalty lam."""
+                  device=None, raise_on_error=True, sampler="element"):
+    """Alg. 4: importance-sparsified Sinkhorn for UOT with KL penalty lam
+    (the skip sampler is refused: the UOT probabilities are not separable)."""
     M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
     dev = M.keep[0].device
     kd = kdtype or dtype
     it = torch.float64 if kd == "f64" else torch.float32
     ia, ib = _dev(init_alpha, it, dev), _dev(init_beta, it, dev)
     prm = make_params(eps, lam, s, tol, max_iter, check_every, stop_rule, seed, problem_id, kd, log_domain,
-                      absorb_tau, ia, ib, gather_mode, sketch_mode)
+                      absorb_tau, ia, ib, gather_mode, sketch_mode, sampler)
     return _solve("spar_sink_uot", M.prob, prm, dev, OP_SPAR_SINK, workspace, raise_on_error)
 
 
@@ -246,12 +253,12 @@ _NP_DT = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: tor
 
 def sparsify_kernel(a, b, x=None, y=None, C_=None, *, eps, s, lam=math.inf, dtype="f32", kdtype=None, seed=0x5EED,
                     problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, sketch_mode=0, workspace=None,
-                    device=None):
+                    device=None, sampler="element"):
     """Eq. (pois) sketch K~ as CSR + CSC tensor views (copied out of the workspace)."""
     M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
     dev = M.keep[0].device
     kd = kdtype or dtype
-    prm = make_params(eps, lam, s, 0.0, 1, 0, 0, seed, problem_id, kd, sketch_mode=sketch_mode)
+    prm = make_params(eps, lam, s, 0.0, 1, 0, 0, seed, problem_id, kd, sketch_mode=sketch_mode, sampler=sampler)
     nbytes = sps_workspace_bytes(M.prob, prm, OP_SPARSIFY)
     if nbytes == 0:
         raise SpsError(SPS_ERR_INVALID_ARG, last_error())
