@@ -89,6 +89,7 @@ struct Layout {
   size_t cm_perm_r, cm_perm_c;      //   row-major position -> chunk-major position
   size_t pad_ofs, pad_col, pad_val, pad_lv, zsum, csum;   // single-pass sketch (0: two passes)
   size_t unit_r, unit_c;            // persistent iterations: unit starts over rows [n + 2] / columns [m + 2]
+  size_t cmx;                       // pruned cost maximum: scratch (0: the full sweep only)
   int64_t pad_cap;
   int stage_w, stage_jr, stage_jc;  // staged gathers: chunk width, chunks over columns / rows (0: off)
   int stage_nsm;                    // SM count the staging was planned for
@@ -212,6 +213,10 @@ sps_status launch_dense_lse_objective(const ProbDev& pd, const Layout& L, char* 
 // Skip sampler (balanced OT): count, scan, fill and CSC of the sketch (sps_sweep.cu).
 sps_status launch_skip_sample(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st);
 void launch_csc_sort(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st);
+// Cost divisor by bucketed bounds (sps_costmax.cu); *overflow_flag gates the full sweep.
+size_t cost_max_scratch_bytes(int n, int m, int d);
+sps_status launch_cost_max_pruned(const float* x, const float* y, int n, int m, int d, SketchScalars* sc,
+                                  char* scratch, const int** overflow_flag, cudaStream_t st);
 sps_status launch_cost_max_points(const float* x, int n, const float* y, int m, int d, void* scratch,
                                   cudaStream_t st);
 // Shared with the batched path (sps_sketch.cu)

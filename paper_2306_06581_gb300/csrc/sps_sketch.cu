@@ -96,7 +96,9 @@ constexpr int kTileJ = 256;
 constexpr int kMaxDReg = 16;
 
 template <int D>
-__global__ void __launch_bounds__(kTileI) k_cost_max(ProbDev pd, SketchScalars* sc, int need64, int jchunk) {
+__global__ void __launch_bounds__(kTileI) k_cost_max(ProbDev pd, SketchScalars* sc, int need64, int jchunk,
+                                                     const int* gate) {
+  if (gate && *gate == 0) return;   // the pruned maximum already holds the result
   const int n = pd.n, m = pd.m;
   const int d = D > 0 ? D : pd.d;
   extern __shared__ float ys[];  // kTileJ * d
@@ -406,12 +408,17 @@ sps_status launch_cost_max(const ProbDev& pd, const Layout& L, char* ws, int nee
   dim3 grid(gi, gj);
   const size_t shm = (pd.cv.C32 || pd.d > kMaxDReg) ? 0 : (size_t)kTileJ * pd.d * sizeof(float);
   SketchScalars* sc = at<SketchScalars>(ws, L.scal);
+  const int* gate = nullptr;
+  if (L.cmx && !need64 && !pd.cv.C32 && pd.cv.x32 && pd.d >= 1 && pd.d <= 16) {
+    // bucketed bounds first; the full sweep below then runs only if its pair list overflowed
+    SPS_TRY(launch_cost_max_pruned(pd.cv.x32, pd.cv.y32, pd.n, pd.m, pd.d, sc, ws + L.cmx, &gate, st));
+  }
   switch (pd.cv.C32 ? 0 : pd.d) {
-    case 2: k_cost_max<2><<<grid, kTileI, shm, st>>>(pd, sc, need64, jchunk); break;
-    case 3: k_cost_max<3><<<grid, kTileI, shm, st>>>(pd, sc, need64, jchunk); break;
-    case 5: k_cost_max<5><<<grid, kTileI, shm, st>>>(pd, sc, need64, jchunk); break;
-    case 10: k_cost_max<10><<<grid, kTileI, shm, st>>>(pd, sc, need64, jchunk); break;
-    default: k_cost_max<0><<<grid, kTileI, shm, st>>>(pd, sc, need64, jchunk); break;
+    case 2: k_cost_max<2><<<grid, kTileI, shm, st>>>(pd, sc, need64, jchunk, gate); break;
+    case 3: k_cost_max<3><<<grid, kTileI, shm, st>>>(pd, sc, need64, jchunk, gate); break;
+    case 5: k_cost_max<5><<<grid, kTileI, shm, st>>>(pd, sc, need64, jchunk, gate); break;
+    case 10: k_cost_max<10><<<grid, kTileI, shm, st>>>(pd, sc, need64, jchunk, gate); break;
+    default: k_cost_max<0><<<grid, kTileI, shm, st>>>(pd, sc, need64, jchunk, gate); break;
   }
   add_launches(1);
   return cuda_fail(cudaGetLastError(), "cost_max");
