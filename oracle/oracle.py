@@ -251,7 +251,7 @@ class OracleProblem:
                 "pstar": ps[:c].copy(), "cost": cost[:c].copy()}
 
     def skip_row(self, i):
-        """Row i of the skip sampler's sketch (balanced OT only)."""
+        """Row i of the skip sampler's sketch."""
         lib = load()
         rowf, colf, S = self.factors()
         cmax = lib.orc_colf_max(_ptr(colf), self.m)
@@ -276,7 +276,7 @@ class OracleProblem:
 
     def sparsify(self, sampler="element"):
         """Full sketch.  sampler: "element" (one decision per element) or
-        "skip" (geometric skips with thinning; balanced OT only)."""
+        "skip" (geometric skips with thinning)."""
         lib = load()
         if sampler == "skip":
             _, nnz = self.skip_count()

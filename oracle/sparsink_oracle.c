@@ -420,11 +420,12 @@ int32_t orc_sample_row(const orc_problem* P, const float* rowf, const float* col
 }
 
 /* ======================================================================
- * Skip sampler for the separable OT probabilities p_ij = r_i c_j: the same
- * law as one Bernoulli(p*_ij) decision per element, with work proportional
- * to the sampled count instead of n m.  Thinning construction: q_i =
- * min(1, fl(r_i cmax)) bounds every p_ij = fl(r_i c_j) of row i (rounding is
- * monotone), cmax = max_j c_j.  Candidates form a Bernoulli(q_i) process
+ * Skip sampler: the same law as one Bernoulli(p*_ij) decision per element,
+ * with work proportional to the sampled count instead of n m.  Thinning
+ * construction with a row bound q_i >= p_ij for every j: OT p_ij =
+ * fl(r_i c_j), q_i = min(1, fl(r_i cmax)); UOT p_ij = fl(scale fl(fl(A_i B_j)
+ * E(-D_ij kappa))), q_i = min(1, fl(scale fl(A_i cmax))) (E <= 1 and
+ * rounding is monotone), cmax = max_j of the column factors.  Candidates form a Bernoulli(q_i) process
  * over j = 0 .. m-1, generated by geometric gaps: with U uniform on (0, 1],
  * G = floor(log U / log(1 - q_i)) has P(G >= k) = P(U <= (1 - q_i)^k) =
  * (1 - q_i)^k.  A candidate j is kept when V < fl(p_ij / q_i), V uniform on
@@ -478,7 +479,7 @@ int32_t orc_skip_row(const orc_problem* P, const float* rowf, const float* colf,
                      float cmax, int32_t i, int32_t* cols, double* val, double* logval, float* pstar,
                      double* cost) {
   const float r = rowf[i];
-  const float q = r * cmax;
+  const float q = is_ot(P) ? r * cmax : S->scale32 * (r * cmax);
   if (!(q > 0.0f)) return 0;
   const int full = q >= 1.0f;
   const float L = full ? 0.0f : orc_log1m32(q);
@@ -496,7 +497,7 @@ int32_t orc_skip_row(const orc_problem* P, const float* rowf, const float* colf,
       j += 1 + (int64_t)floorf(ratio);
     }
     if (j >= P->m) break;
-    const float p = r * colf[j];
+    const float p = orc_pstar_raw(P, rowf, colf, S, i, (int32_t)j);
     const float acc = full ? p : p / q;
     const float V = (float)(w[1] >> 8) * 0x1p-24f;
     if (V < acc) {
@@ -524,7 +525,6 @@ static int64_t sparsify_impl(const orc_problem* P, int skip, int32_t* row_ptr, i
                              double* logval, float* pstar, double* cost, int32_t* col_ptr,
                              int32_t* row_idx, double* valT, int32_t* perm, orc_scalars* S) {
   const int32_t n = P->n, m = P->m;
-  if (skip && !is_ot(P)) return -1;
   float* rowf = (float*)malloc(sizeof(float) * (size_t)n);
   float* colf = (float*)malloc(sizeof(float) * (size_t)m);
   if (orc_factors(P, rowf, colf, S)) { free(rowf); free(colf); return -1; }

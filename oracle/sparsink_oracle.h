@@ -124,9 +124,9 @@ int64_t orc_sparsify(const orc_problem* P, int32_t* row_ptr, int32_t* col_idx, d
                      double* logval, float* pstar, double* cost, int32_t* col_ptr,
                      int32_t* row_idx, double* valT, int32_t* perm, orc_scalars* S);
 
-/* Skip sampler (balanced OT only): the same law as orc_sample_row's
- * per-element decisions through a different random stream, with work
- * proportional to the sampled count (see the comment in the source). */
+/* Skip sampler (OT and UOT): the same law as orc_sample_row's per-element
+ * decisions through a different random stream, with work proportional to
+ * the sampled count (see the comment in the source). */
 float orc_log1m32(float q);                      /* log(1 - q), 0 < q < 1, binary32 spec */
 void orc_log1m32_vec(const float* q, float* y, int64_t n);
 void orc_skip_words(uint64_t seed, uint32_t pid, uint32_t i, uint32_t t, uint32_t w[2]);

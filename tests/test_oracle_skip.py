@@ -1,6 +1,6 @@
-"""Pins for the oracle's skip sampler (separable OT probabilities, thinning
-by geometric skips): it must draw the law of Eq. (pois) with Eq. (pij-ot) --
-every element kept independently with probability p*_ij = min(1, s p_ij).
+"""Pins for the oracle's skip sampler (thinning by geometric skips over a row
+bound): it must draw the law of Eq. (pois) with Eq. (pij-ot) or Eq. (pij-uot)
+-- every element kept independently with probability p*_ij = min(1, s p_ij).
 
 - the spec log(1 - q) against FP64 log1p;
 - per-element inclusion frequencies over many Philox problem ids against
@@ -128,3 +128,31 @@ def test_values_follow_definition(orc):
     # the skip stream is not the element stream (a different random source)
     el = P.sparsify()
     assert not (el["nnz"] == sk["nnz"] and np.array_equal(el["col_idx"], sk["col_idx"]))
+
+
+def test_uot_inclusion_frequencies(orc):
+    # Eq. (pij-uot): p_ij proportional to (a_i b_j)^gamma exp(-C_ij / (2 lam + eps))
+    rng = np.random.default_rng(21)
+    n, m, lam, eps = 3, 40, 1.0, 0.1
+    a = rng.uniform(0.05, 1.0, n)
+    b = rng.uniform(0.05, 1.5, m)
+    x = rng.standard_normal((n, 2))
+    y = rng.standard_normal((m, 2)) + 0.5
+    s, K = 30.0, 2500
+    D = ((x[:, None, :] - y[None, :, :]) ** 2).sum(-1)
+    C = D / D.astype(np.float32).max()
+    g = lam / (2 * lam + eps)
+    w = np.outer(a, b) ** g * np.exp(-C / (2 * lam + eps))
+    p = np.minimum(1.0, s * w / w.sum())
+    hits = np.zeros((n, m))
+    for pid in range(K):
+        P = orc.OracleProblem(a, b, eps, s, lam, x=x, y=y, pid=pid)
+        for i in range(n):
+            hits[i, P.skip_row(i)["cols"]] += 1.0
+    f = hits / K
+    z = (f - p) / np.sqrt(np.maximum(p * (1 - p), 1e-12) / K)
+    inner = (p < 1) & (p * K >= 25)
+    assert inner.sum() > 60
+    assert np.abs(z[inner]).max() < 5.0, np.abs(z[inner]).max()
+    # the per-element and skip streams agree in expectation
+    assert abs(f.sum() - p.sum()) < 5 * math.sqrt((p * (1 - p)).sum() / K)
