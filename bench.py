@@ -361,9 +361,7 @@ def run_ours(args):
     kw = dict(eps=w.eps, s=w.s, tol=TOL, max_iter=20000, dtype=pdt, seed=w.seed, problem_id=rank)
 
     def solve(**extra):
-        k = dict(kw, kdtype=kd, log_domain=logd)
-        if not uot:
-            k["sampler"] = args.sampler
+        k = dict(kw, kdtype=kd, log_domain=logd, sampler=args.sampler)
         k.update(extra)
         if uot:
             return S.spar_sink_uot(k.pop("a", a), k.pop("b", b), k.pop("x", x), k.pop("y", y), lam=w.lam, **k)
@@ -436,9 +434,9 @@ def run_ours(args):
                            "extrapolated_ms_at_spar_sink_iters": round(est, 1),
                            "speedup_of_spar_sink_extrapolated": round(est / ms, 2)})
 
-    # balanced OT: the same solve with the other sampler (same law, another random stream)
+    # the same solve with the other sampler (same law, another random stream)
     other = None
-    if not uot and rank == 0:
+    if rank == 0:
         alt = "skip" if args.sampler == "element" else "element"
         ro = solve(sampler=alt)
         tms = []
@@ -459,11 +457,12 @@ def run_ours(args):
     # storage precision forms of the stabilised path against the stored FP64 oracle value
     precision = None
     gold = _golden(w)
-    if logd and rank == 0 and gold is not None and (uot or args.sampler == "element"):
+    if logd and rank == 0 and gold is not None:
         precision = {}
         for k2 in ("f32", "bf16", "f16"):
-            rr = solve(kdtype=k2)
-            rr = solve(kdtype=k2, workspace=rr["workspace"])
+            # the stored oracle solve used the per-element stream
+            rr = solve(kdtype=k2, sampler="element")
+            rr = solve(kdtype=k2, sampler="element", workspace=rr["workspace"])
             ent = {"ms": round(rr["ms_sketch"] + rr["ms_iter"] + rr["ms_obj"], 3), "iters": rr["iters"],
                    "obj": rr["obj"], "n_absorb": rr["n_absorb"]}
             if gold is not None:
@@ -507,7 +506,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
-    line["config"]["sampler"] = "element" if uot else args.sampler
+    line["config"]["sampler"] = args.sampler
     if other is not None:
         line["other_sampler"] = other
     if precision is not None:
@@ -515,7 +514,7 @@ def run_ours(args):
     if args.warm_start:
         line["warm_start"] = _warm_start_leg(args, w, S, x, y, a, b, kd, logd, last)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+        line["cpu_baseline"] = cpu_baseline(w, args.sampler)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -579,11 +578,12 @@ def _oracle_problem(w, rows=None):
     return oracle.OracleProblem(f(a), f(w.b), w.eps, s, w.lam, x=f(x), y=f(w.y), seed=w.seed)
 
 
-def _oracle_solve(w):
+def _oracle_solve(w, sampler="element"):
     import oracle
     P = _oracle_problem(w)
     t0 = time.perf_counter()
-    r = oracle.spar_sink(P, tol=TOL, max_iter=20000, log_domain=bool(_log_domain(w)))
+    r = oracle.spar_sink(P, tol=TOL, max_iter=20000, log_domain=bool(_log_domain(w)),
+                         sketch=P.sparsify(sampler=sampler))
     return (time.perf_counter() - t0) * 1e3, r
 
 
@@ -591,7 +591,7 @@ def _oracle_solve(w):
 FULL_ORACLE_MAX_PAIRS = 1.0e9
 
 
-def _oracle_sampled(w, rows, iters, gold_iters):
+def _oracle_sampled(w, rows, iters, gold_iters, sampler="element"):
     """Bounded oracle sample of a large workload: the sketch (cost maximum,
     count and fill passes) of the first `rows` rows against all m columns,
     `iters` iterations and the objective on that partial sketch.  Returns the
@@ -600,7 +600,7 @@ def _oracle_sampled(w, rows, iters, gold_iters):
     import oracle
     P = _oracle_problem(w, rows)
     t0 = time.perf_counter()
-    sk = P.sparsify()
+    sk = P.sparsify(sampler=sampler)
     t1 = time.perf_counter()
     it = oracle.spar_sink(P, tol=0.0, max_iter=iters, log_domain=bool(_log_domain(w)), sketch=sk)
     t2 = time.perf_counter()
@@ -621,21 +621,21 @@ def _threads():
         return os.cpu_count() or 1
 
 
-def _baseline_sample(w):
+def _baseline_sample(w, sampler="element"):
     if float(w.n) * w.m <= FULL_ORACLE_MAX_PAIRS:
-        ms, r = _oracle_solve(w)
-        return ms, (f"one complete FP64 oracle solve of {w.name} (sketch, {r['info']['iters']} iterations to "
-                    f"1e-5, objective) on the host cores, OpenMP over rows")
+        ms, r = _oracle_solve(w, sampler)
+        return ms, (f"one complete FP64 oracle solve of {w.name} ({sampler} sampler sketch, {r['info']['iters']} "
+                    f"iterations to 1e-5, objective) on the host cores, OpenMP over rows")
     gold = _golden(w)
     gi = gold["iters"] if gold else 200
     rows = max(256, int(4.0e8 / w.m))
-    return _oracle_sampled(w, rows, 5, gi)
+    return _oracle_sampled(w, rows, 5, gi, sampler)
 
 
-def cpu_baseline(w):
+def cpu_baseline(w, sampler="element"):
     import oracle
     oracle.build_oracle()
-    ms, desc = _baseline_sample(w)
+    ms, desc = _baseline_sample(w, sampler)
     return {"value": round(ms, 1), "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", _threads())),
             "kind": "oracle", "sample": desc}
 
@@ -675,7 +675,7 @@ def run_reference(args):
     t_start = time.perf_counter()
     for k in range(args.steps):
         t0 = time.perf_counter()
-        ms, desc = _baseline_sample(w)
+        ms, desc = _baseline_sample(w, args.sampler)
         times.append(ms)
         descs.append(desc)
         if (time.perf_counter() - t_start) + (time.perf_counter() - t0) > budget_s:
@@ -690,6 +690,7 @@ def run_reference(args):
             "config": _config(w, "n/a (CPU)", args.kdtype or w.dtype), "impl": "reference",
             "cpu_baseline": {"value": round(val, 1), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": round(val, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    line["config"]["sampler"] = args.sampler
     print(json.dumps(line), flush=True)
 
 
@@ -705,8 +706,8 @@ def main():
     ap.add_argument("--dense-cap", type=int, default=0,
                     help="stop dense Sinkhorn after this many iterations and extrapolate (0: run to tolerance)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sampler", default="element", choices=["element", "skip"],
-                    help="sketch draws: one decision per element, or geometric skips (balanced OT only)")
+    ap.add_argument("--sampler", default="skip", choices=["element", "skip"],
+                    help="sketch draws: geometric skips with thinning (default), or one decision per element")
     ap.add_argument("--n", type=int, default=None, help="profiling: the workload's family at another size")
     ap.add_argument("--solve-only", action="store_true", help="profiling: two solves, no timing loop")
     ap.add_argument("--warm-start", action="store_true", help="also train and time the learned warm start")

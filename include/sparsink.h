@@ -106,14 +106,15 @@ typedef struct {
                           same sketch bit for bit. */
   int32_t sampler;     /* How the sketch draws Eq. (pois).  SPS_SAMPLER_ELEMENT (0): one
                           Philox decision per element (n m work; every (i, j) tested).
-                          SPS_SAMPLER_SKIP (1), balanced OT only (lambda = +inf; else
-                          SPS_ERR_INVALID_ARG): the separable probabilities of Eq. (pij-ot)
-                          let every row draw its kept columns by geometric gaps over a bound
-                          q_i = min(1, r_i max_j c_j) followed by thinning with p_ij / q_i --
-                          the same law (each element kept independently with probability
-                          p*_ij) from a different random stream, with work proportional to the
-                          sampled count.  sketch_mode does not apply to it; spar_sink_batched
-                          accepts SPS_SAMPLER_ELEMENT only. */
+                          SPS_SAMPLER_SKIP (1): every row draws its kept columns by geometric
+                          gaps over a row bound q_i >= p_ij (OT: r_i max_j c_j; UOT:
+                          (s/Z) A_i max_j B_j, since the exponential factor is at most 1)
+                          followed by thinning with p_ij / q_i -- the same law (each element
+                          kept independently with probability p*_ij) from a different random
+                          stream, with work proportional to the sampled count (the UOT
+                          normaliser Z is still an exact sum over all pairs).  sketch_mode
+                          does not apply to it; spar_sink_batched accepts SPS_SAMPLER_ELEMENT
+                          only. */
 } sps_params;
 
 #define SPS_SKETCH_SINGLE 0

@@ -220,10 +220,7 @@ static sps_status validate(const sps_problem* P, const sps_params* Q, int op) {
   if (Q->gather_mode < SPS_GATHER_AUTO || Q->gather_mode > SPS_GATHER_STAGED) { set_error("unknown gather_mode %d", Q->gather_mode); return SPS_ERR_INVALID_ARG; }
   if (Q->sketch_mode != SPS_SKETCH_SINGLE && Q->sketch_mode != SPS_SKETCH_TWO_PASS) { set_error("unknown sketch_mode %d", Q->sketch_mode); return SPS_ERR_INVALID_ARG; }
   if (Q->sampler != SPS_SAMPLER_ELEMENT && Q->sampler != SPS_SAMPLER_SKIP) { set_error("unknown sampler %d", Q->sampler); return SPS_ERR_INVALID_ARG; }
-  if (op != SPS_OP_DENSE && Q->sampler == SPS_SAMPLER_SKIP && !isinf(Q->lambda)) {
-    set_error("the skip sampler needs the separable probabilities of balanced OT (lambda = +inf)");
-    return SPS_ERR_INVALID_ARG;
-  }
+
   if (op != SPS_OP_DENSE && (double)Q->s + 8.0 * sqrt(Q->s) + 1024.0 > 2147483647.0 &&
       (double)P->n * (double)P->m > 2147483647.0) {
     set_error("sample budget too large for int32 indices"); return SPS_ERR_CAPACITY;

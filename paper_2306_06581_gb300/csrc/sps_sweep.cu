@@ -439,10 +439,12 @@ SweepGeo sweep_geometry(int n, int m) {
 }
 
 // ---------------------------------------------------------------------------
-// Skip sampler for the separable OT probabilities p_ij = r_i c_j (Eq. pij-ot):
-// the law of one Bernoulli(p*_ij) decision per element (Eq. pois) with work
-// proportional to the sampled count.  Row i bounds every p_ij by q_i =
-// min(1, fl(r_i cmax)); candidates form a Bernoulli(q_i) process generated by
+// Skip sampler: the law of one Bernoulli(p*_ij) decision per element
+// (Eq. pois) with work proportional to the sampled count.  Row i bounds every
+// p_ij by q_i: OT (Eq. pij-ot) p_ij = fl(r_i c_j), q_i = min(1, fl(r_i cmax));
+// UOT (Eq. pij-uot) p_ij = fl(scale fl(fl(A_i B_j) E(-D_ij kappa))), q_i =
+// min(1, fl(scale fl(A_i cmax))) (E <= 1; rounding is monotone), cmax =
+// max_j of the column factors.  Candidates form a Bernoulli(q_i) process generated by
 // geometric gaps G = floor(log U / log(1 - q_i)), U = ((w >> 8) + 1) 2^-24
 // on (0, 1]; a candidate j is kept when V < fl(p_ij / q_i), V = (w' >> 8)
 // 2^-24.  Candidate t of row i reads Philox at counter (t >> 1, i, pid,
@@ -459,12 +461,13 @@ __global__ void k_colf_max(const float* __restrict__ colf, int m, SketchScalars*
   if ((threadIdx.x & 31) == 0 && c > 0.0f) atomicMax(reinterpret_cast<int*>(&sc->cmax32), __float_as_int(c));
 }
 
-template <int MODE, typename V>
+template <int MODE, bool UOT, typename V>
 __global__ void __launch_bounds__(256) k_skip(SweepArgs A) {
   if (A.ctrl->status != SPS_OK) return;
   const ProbDev& pd = A.pd;
   const int n = pd.n, m = pd.m, d = pd.d;
   const float cmax = A.sc->cmax32;
+  const float kappa = A.sc->kappa32, scale = A.sc->scale32;
   const bool lv32 = MODE == SK_FILL && A.logval != nullptr && !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64;
   float k_hi = 0.0f, k_lo = 0.0f;
   if (lv32) {
@@ -474,7 +477,7 @@ __global__ void __launch_bounds__(256) k_skip(SweepArgs A) {
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float r = A.rowf[i];
-    const float q = __fmul_rn(r, cmax);
+    const float q = UOT ? __fmul_rn(scale, __fmul_rn(r, cmax)) : __fmul_rn(r, cmax);
     int cnt = 0;
     int pos = 0, pend = 0;
     if (MODE == SK_FILL) { pos = A.row_ptr[i]; pend = A.row_ptr[i + 1]; }
@@ -497,7 +500,14 @@ __global__ void __launch_bounds__(256) k_skip(SweepArgs A) {
         }
         if (j >= m) break;
         const int jj = (int)j;
-        const float p = __fmul_rn(r, A.colf[jj]);
+        float Dd = 0.0f;
+        float p;
+        if (UOT) {
+          Dd = raw32(pd.cv, i, jj);
+          p = __fmul_rn(scale, __fmul_rn(__fmul_rn(r, A.colf[jj]), spec_exp(-__fmul_rn(Dd, kappa))));
+        } else {
+          p = __fmul_rn(r, A.colf[jj]);
+        }
         const float acc = full ? p : __fdiv_rn(p, q);
         const float Vu = __fmul_rn(__uint2float_rn(h >> 8), 5.9604644775390625e-08f);
         if (!(Vu < acc)) continue;
@@ -516,7 +526,7 @@ __global__ void __launch_bounds__(256) k_skip(SweepArgs A) {
             A.logval[pos] = __fsub_rn(-ce, logf(ps));
           } else {
             reinterpret_cast<V*>(A.val)[pos] =
-                from_d<V>(ValMath<V>::value(pd, *A.sc, i, jj, raw32(pd.cv, i, jj), ps));
+                from_d<V>(ValMath<V>::value(pd, *A.sc, i, jj, UOT ? Dd : raw32(pd.cv, i, jj), ps));
             if (A.logval) {
               const double C64 = raw64(pd.cv, i, jj) / A.sc->dn64;
               A.logval[pos] = (float)(-C64 / pd.eps - (double)logf(ps));
@@ -667,7 +677,8 @@ static void skip_fill_v(const ProbDev& pd, const Layout& L, char* ws, int grid, 
   A.logval = L.logval ? at<float>(ws, L.logval) : nullptr;
   A.tmp_row = at<int>(ws, L.tmp_row);
   A.tmp_src = at<int>(ws, L.tmp_src);
-  k_skip<SK_FILL, V><<<grid, 256, 0, st>>>(A);
+  if (pd.is_ot) k_skip<SK_FILL, false, V><<<grid, 256, 0, st>>>(A);
+  else k_skip<SK_FILL, true, V><<<grid, 256, 0, st>>>(A);
 }
 
 sps_status launch_skip_sample(const ProbDev& pd, const Layout& L, char* ws, sps_dtype kd, cudaStream_t st) {
@@ -677,7 +688,8 @@ sps_status launch_skip_sample(const ProbDev& pd, const Layout& L, char* ws, sps_
   const int grid = std::max(1, std::min(152 * 8, (pd.n + 255) / 256));
   cudaMemsetAsync(A.col_cnt, 0, sizeof(int) * (size_t)pd.m, st);
   k_colf_max<<<std::max(1, std::min(1024, (pd.m + 255) / 256)), 256, 0, st>>>(A.colf, pd.m, A.sc);
-  k_skip<SK_COUNT, float><<<grid, 256, 0, st>>>(A);
+  if (pd.is_ot) k_skip<SK_COUNT, false, float><<<grid, 256, 0, st>>>(A);
+  else k_skip<SK_COUNT, true, float><<<grid, 256, 0, st>>>(A);
   launch_scan_counts(A.cnt_row, at<int>(ws, L.row_ptr), pd.n, A.col_cnt, at<int>(ws, L.col_ptr),
                      at<int>(ws, L.col_cur), pd.m, (long long)L.cap, A.ctrl, st);
   switch (kd) {

@@ -223,8 +223,8 @@ def spar_sink_uot(a, b, x=None, y=None, C_=None, *, eps, lam, s, tol=1e-6, max_i
                   seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL,
                   check_every=0, init_alpha=None, init_beta=None, log_domain=0, absorb_tau=0.0, gather_mode=0, sketch_mode=0, workspace=None,
                   device=None, raise_on_error=True, sampler="element"):
-    """Alg. 4: importance-sparsified Sinkhorn for UOT with KL penalty lam
-    (the skip sampler is refused: the UOT probabilities are not separable)."""
+    """Alg. 4: importance-sparsified Sinkhorn for UOT with KL penalty lam.
+    sampler="skip" draws the sketch by geometric gaps with thinning."""
     M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
     dev = M.keep[0].device
     kd = kdtype or dtype

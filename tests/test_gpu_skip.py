@@ -1,4 +1,4 @@
-"""GPU parity of the skip sampler (balanced OT, geometric gaps with thinning)
+"""GPU parity of the skip sampler (geometric gaps with thinning)
 against the oracle's restatement of the same stream:
 
 - pattern (CSR, CSC, csr_pos) bit-exact, values within the element
@@ -8,7 +8,8 @@ against the oracle's restatement of the same stream:
 - 200000 points (the 8-component mixture workload): nnz equal to the
   oracle's count and sampled rows bit-exact, in the configuration the
   benchmark runs;
-- the skip sampler with lambda < inf is refused before any launch.
+- UOT (Eq. pij-uot): patterns bit-exact and the Alg. 4 objective within
+  1e-5 of the oracle's on its own skip sketch.
 """
 import math
 
@@ -107,7 +108,23 @@ def test_skip_200k_rows_and_count(S, orc):
         assert np.allclose(val[rp[i]:rp[i + 1]], r["val"], rtol=2e-5, atol=1e-37)
 
 
-def test_skip_refused_for_uot(S):
-    w = inputs.small_problem(n=20, m=20, d=2, seed=1)
-    with pytest.raises(S.SpsError):
-        S.spar_sink_uot(w.a, w.b, w.x, w.y, eps=0.1, lam=1.0, s=50.0, sampler="skip")
+@pytest.mark.parametrize("n,m,d,lam", [(300, 517, 3, 1.0), (257, 129, 10, 0.5), (7, 5, 2, 2.0)])
+def test_skip_uot_pattern_bit_exact(S, orc, n, m, d, lam):
+    w = inputs.small_problem(n=n, m=m, d=d, seed=n + m, mass_b=1.5)
+    x, y, a, b = _round32(w)
+    s = max(10.0, 0.08 * n * m)
+    g = S.sparsify_kernel(a, b, x, y, eps=0.1, s=s, lam=lam, dtype="f32", seed=5, problem_id=2, sampler="skip")
+    o = orc.OracleProblem(a, b, 0.1, s, lam, x=x, y=y, seed=5, pid=2).sparsify(sampler="skip")
+    _check_pattern(g, o)
+    assert np.allclose(g["val"].cpu().numpy(), o["val"], rtol=2e-6, atol=0)
+
+
+def test_skip_uot_solve_matches_oracle(S, orc):
+    w = inputs.uot_n20000(n=3000)
+    x, y, a, b = _round32(w)
+    r = S.spar_sink_uot(a, b, x, y, eps=w.eps, lam=w.lam, s=w.s, tol=1e-5, dtype="f32", seed=w.seed,
+                        sampler="skip")
+    P = orc.OracleProblem(a, b, w.eps, w.s, w.lam, x=x, y=y, seed=w.seed)
+    o = orc.spar_sink(P, tol=1e-5, sketch=P.sparsify(sampler="skip"))
+    assert r["nnz"] == o["sketch"]["nnz"]
+    assert abs(r["obj"] - o["obj"]) <= 1e-5 * abs(o["obj"])
