@@ -448,8 +448,7 @@ SweepGeo sweep_geometry(int n, int m) {
 // geometric gaps G = floor(log U / log(1 - q_i)), U = ((w >> 8) + 1) 2^-24
 // on (0, 1]; a candidate j is kept when V < fl(p_ij / q_i), V = (w' >> 8)
 // 2^-24.  Candidate t of row i reads Philox at counter (t >> 1, i, pid,
-// 0x5B1E), words 2 (t & 1) and 2 (t & 1) + 1.  One thread per row (rows are
-// independent; the gaps of a row form a chain); COUNT writes the row counts
+// 0x5B1E), words 2 (t & 1) and 2 (t & 1) + 1.  COUNT writes the row counts
 // and the column counts, FILL the CSR entries and the CSC scatter.
 // ---------------------------------------------------------------------------
 enum { SK_COUNT = 0, SK_FILL = 1 };
@@ -461,11 +460,18 @@ __global__ void k_colf_max(const float* __restrict__ colf, int m, SketchScalars*
   if ((threadIdx.x & 31) == 0 && c > 0.0f) atomicMax(reinterpret_cast<int*>(&sc->cmax32), __float_as_int(c));
 }
 
+// One warp per row.  The gaps of a row's candidates depend only on their
+// draws, so a warp computes 64 candidates at a time (lane l: candidates
+// base + 2l and base + 2l + 1, which share one Philox call) and places them by
+// a prefix sum of (1 + G); the row's candidate sequence, its stop and the
+// order of the kept elements are those of the one-at-a-time definition.
 template <int MODE, bool UOT, typename V>
 __global__ void __launch_bounds__(256) k_skip(SweepArgs A) {
   if (A.ctrl->status != SPS_OK) return;
   const ProbDev& pd = A.pd;
   const int n = pd.n, m = pd.m, d = pd.d;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const float cmax = A.sc->cmax32;
   const float kappa = A.sc->kappa32, scale = A.sc->scale32;
   const bool lv32 = MODE == SK_FILL && A.logval != nullptr && !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64;
@@ -475,7 +481,8 @@ __global__ void __launch_bounds__(256) k_skip(SweepArgs A) {
     k_hi = __double2float_rn(k64);
     k_lo = __double2float_rn(k64 - (double)k_hi);
   }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
     const float r = A.rowf[i];
     const float q = UOT ? __fmul_rn(scale, __fmul_rn(r, cmax)) : __fmul_rn(r, cmax);
     int cnt = 0;
@@ -484,67 +491,110 @@ __global__ void __launch_bounds__(256) k_skip(SweepArgs A) {
     if (q > 0.0f) {
       const bool full = q >= 1.0f;
       const float L = full ? 0.0f : spec_log1m(q);
-      long long j = -1;
-      uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
-      for (uint32_t t = 0;; ++t) {
-        if ((t & 1u) == 0u) w4 = skip_words4(pd.seed, pd.pid, (uint32_t)i, t >> 1);
-        const uint32_t g = (t & 1u) ? w4.z : w4.x;
-        const uint32_t h = (t & 1u) ? w4.w : w4.y;
-        if (full) {
-          j += 1;
-        } else {
-          const float U = __fmul_rn(__uint2float_rn((g >> 8) + 1u), 5.9604644775390625e-08f);
-          const float ratio = __fdiv_rn(spec_log(U), L);
-          if (!(ratio < (float)m)) break;
-          j += 1 + (long long)floorf(ratio);
+      long long jprev = -1;
+      for (uint32_t call0 = 0;; call0 += 32) {
+        const uint4 w4 = skip_words4(pd.seed, pd.pid, (uint32_t)i, call0 + (uint32_t)lane);
+        // gaps of the lane's two candidates; an invalid gap ends the row there
+        bool ok0 = true, ok1 = true;
+        long long st0 = 1, st1 = 1;
+        if (!full) {
+          const float r0 = __fdiv_rn(spec_log(__fmul_rn(__uint2float_rn((w4.x >> 8) + 1u), 5.9604644775390625e-08f)), L);
+          const float r1 = __fdiv_rn(spec_log(__fmul_rn(__uint2float_rn((w4.z >> 8) + 1u), 5.9604644775390625e-08f)), L);
+          ok0 = r0 < (float)m;
+          ok1 = r1 < (float)m;
+          st0 = ok0 ? 1 + (long long)floorf(r0) : 0;
+          st1 = ok1 ? 1 + (long long)floorf(r1) : 0;
         }
-        if (j >= m) break;
-        const int jj = (int)j;
-        float Dd = 0.0f;
-        float p;
-        if (UOT) {
-          Dd = raw32(pd.cv, i, jj);
-          p = __fmul_rn(scale, __fmul_rn(__fmul_rn(r, A.colf[jj]), spec_exp(-__fmul_rn(Dd, kappa))));
-        } else {
-          p = __fmul_rn(r, A.colf[jj]);
+        // first invalid candidate of the 64 (64: none)
+        const unsigned bad = __ballot_sync(0xffffffffu, !ok0 || !ok1);
+        int tstop = 64;
+        if (bad) {
+          const int fl = __ffs(bad) - 1;
+          const bool b0 = __shfl_sync(0xffffffffu, !ok0, fl);
+          tstop = 2 * fl + (b0 ? 0 : 1);
         }
-        const float acc = full ? p : __fdiv_rn(p, q);
-        const float Vu = __fmul_rn(__uint2float_rn(h >> 8), 5.9604644775390625e-08f);
-        if (!(Vu < acc)) continue;
+        // positions: jprev + inclusive prefix of the steps in candidate order
+        const long long tot = st0 + st1;
+        long long inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        const long long j0 = jprev + (inc - tot) + st0;
+        const long long j1 = j0 + st1;
+        const bool in0 = 2 * lane < tstop && j0 < m;
+        const bool in1 = 2 * lane + 1 < tstop && j1 < m;
+        bool acc[2] = {false, false};
+        float pv[2] = {0.0f, 0.0f}, Dv[2] = {0.0f, 0.0f};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const bool in = e == 0 ? in0 : in1;
+          if (!in) continue;
+          const int jj = (int)(e == 0 ? j0 : j1);
+          float p;
+          if (UOT) {
+            Dv[e] = raw32(pd.cv, i, jj);
+            p = __fmul_rn(scale, __fmul_rn(__fmul_rn(r, A.colf[jj]), spec_exp(-__fmul_rn(Dv[e], kappa))));
+          } else {
+            p = __fmul_rn(r, A.colf[jj]);
+          }
+          const float a_ = full ? p : __fdiv_rn(p, q);
+          const uint32_t h = e == 0 ? w4.y : w4.w;
+          acc[e] = __fmul_rn(__uint2float_rn(h >> 8), 5.9604644775390625e-08f) < a_;
+          pv[e] = p;
+        }
+        const unsigned m0 = __ballot_sync(0xffffffffu, acc[0]), m1 = __ballot_sync(0xffffffffu, acc[1]);
         if (MODE == SK_COUNT) {
-          ++cnt;
-          atomicAdd(&A.col_cnt[jj], 1);
+          cnt += __popc(m0) + __popc(m1);
+#pragma unroll
+          for (int e = 0; e < 2; ++e)
+            if (acc[e]) atomicAdd(&A.col_cnt[(int)(e == 0 ? j0 : j1)], 1);
         } else {
-          if (pos >= pend) {   // count and fill disagree: never write out of range
-            A.ctrl->sketch_fault = 1;
-            break;
-          }
-          const float ps = p < 1.0f ? p : 1.0f;
-          A.col_idx[pos] = jj;
-          if (lv32) {
-            const float ce = cost_over_eps_df(pd.cv.x32 + (int64_t)i * d, pd.cv.y32 + (int64_t)jj * d, d, k_hi, k_lo);
-            A.logval[pos] = __fsub_rn(-ce, logf(ps));
-          } else {
-            reinterpret_cast<V*>(A.val)[pos] =
-                from_d<V>(ValMath<V>::value(pd, *A.sc, i, jj, UOT ? Dd : raw32(pd.cv, i, jj), ps));
-            if (A.logval) {
-              const double C64 = raw64(pd.cv, i, jj) / A.sc->dn64;
-              A.logval[pos] = (float)(-C64 / pd.eps - (double)logf(ps));
+          int wpos = pos + __popc(m0 & lt) + __popc(m1 & lt);
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            if (!acc[e]) continue;
+            const int jj = (int)(e == 0 ? j0 : j1);
+            if (wpos >= pend) {   // count and fill disagree: never write out of range
+              A.ctrl->sketch_fault = 1;
+              continue;
             }
+            const float ps = pv[e] < 1.0f ? pv[e] : 1.0f;
+            A.col_idx[wpos] = jj;
+            if (lv32) {
+              const float ce =
+                  cost_over_eps_df(pd.cv.x32 + (int64_t)i * d, pd.cv.y32 + (int64_t)jj * d, d, k_hi, k_lo);
+              A.logval[wpos] = __fsub_rn(-ce, logf(ps));
+            } else {
+              reinterpret_cast<V*>(A.val)[wpos] =
+                  from_d<V>(ValMath<V>::value(pd, *A.sc, i, jj, UOT ? Dv[e] : raw32(pd.cv, i, jj), ps));
+              if (A.logval) {
+                const double C64 = raw64(pd.cv, i, jj) / A.sc->dn64;
+                A.logval[wpos] = (float)(-C64 / pd.eps - (double)logf(ps));
+              }
+            }
+            const int slot = atomicAdd(&A.col_cur[jj], 1);
+            if (slot < A.col_end[jj]) {
+              A.tmp_row[slot] = i;
+              A.tmp_src[slot] = wpos;
+            } else {
+              A.ctrl->sketch_fault = 1;
+            }
+            ++wpos;
           }
-          const int slot = atomicAdd(&A.col_cur[jj], 1);
-          if (slot < A.col_end[jj]) {
-            A.tmp_row[slot] = i;
-            A.tmp_src[slot] = pos;
-          } else {
-            A.ctrl->sketch_fault = 1;
-          }
-          ++pos;
+          pos += __popc(m0) + __popc(m1);
         }
+        // the row ends at an invalid gap or once a position reaches m
+        const long long jlast = __shfl_sync(0xffffffffu, j1, 31);
+        if (tstop < 64 || jlast >= m) break;
+        jprev = jlast;
       }
     }
-    if (MODE == SK_COUNT) A.cnt_row[i] = cnt;
-    else if (pos != pend) A.ctrl->sketch_fault = 1;
+    if (lane == 0) {
+      if (MODE == SK_COUNT) A.cnt_row[i] = cnt;
+      else if (pos != pend) A.ctrl->sketch_fault = 1;
+    }
   }
 }
 
@@ -685,7 +735,7 @@ sps_status launch_skip_sample(const ProbDev& pd, const Layout& L, char* ws, sps_
   SweepArgs A = base_args(pd, L, ws);
   A.col_cnt = at<int>(ws, L.col_cnt);
   A.cnt_row = at<int>(ws, L.row_cnt);
-  const int grid = std::max(1, std::min(152 * 8, (pd.n + 255) / 256));
+  const int grid = std::max(1, std::min(152 * 8, (pd.n + 7) / 8));   // one warp per row
   cudaMemsetAsync(A.col_cnt, 0, sizeof(int) * (size_t)pd.m, st);
   k_colf_max<<<std::max(1, std::min(1024, (pd.m + 255) / 256)), 256, 0, st>>>(A.colf, pd.m, A.sc);
   if (pd.is_ot) k_skip<SK_COUNT, false, float><<<grid, 256, 0, st>>>(A);
