@@ -317,31 +317,27 @@ __device__ __forceinline__ void load8i(const int* p, int (&o)[8]) {
 }
 
 // One aligned group of 8 elements starting at w: the products of those inside
-// [E0, E1) added to their rows' sums.
-__device__ __forceinline__ void group8(int w, int E0, int E1, const int (&id)[8], const float (&vv)[8], int j0, int jn,
-                                       const float* xs, const int* segs, int nr, float* acc) {
+// [E0, E1) added to their rows' sums.  An element of the chunk-major copy
+// carries its block-local row in the high 16 bits and its chunk-local index
+// in the low 16 bits, so consecutive elements of one row are summed in a
+// register and each row change costs one shared atomic.
+__device__ __forceinline__ void group8(int w, int E0, int E1, const int (&id)[8], const float (&vv)[8], int jn,
+                                       const float* xs, float* acc) {
   const int u0 = max(0, E0 - w), u1 = min(8, E1 - w);
   if (u0 >= u1) return;
-  // row of element w + u0: the largest k with segs[k] <= w + u0 (empty rows share bounds)
-  const int g0 = w + u0;
-  int lo = 0, hi = nr - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (segs[mid] <= g0) lo = mid; else hi = mid - 1;
-  }
-  int k = lo, kend = segs[lo + 1];
+  int k = -1;
   float s = 0.0f;
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     if (u >= u0 && u < u1) {
-      while (w + u >= kend) {   // next row (at most nr - 1 steps in all)
-        atomicAdd(&acc[k], s);
+      const int r = (int)((unsigned)id[u] >> 16);
+      const int q = id[u] & 0xffff;
+      if (r != k) {
+        if (k >= 0) atomicAdd(&acc[k], s);
         s = 0.0f;
-        ++k;
-        kend = segs[k + 1];
+        k = r;
       }
-      const int q = id[u] - j0;
-      if ((unsigned)q < (unsigned)jn) s = fmaf(vv[u], xs[q], s);
+      if (q < jn) s = fmaf(vv[u], xs[q], s);
     }
   }
   atomicAdd(&acc[k], s);
@@ -352,9 +348,8 @@ __device__ __forceinline__ void group8(int w, int E0, int E1, const int (&id)[8]
 // over the chunk-major copy: the block's elements of chunk c are one
 // contiguous range, streamed as aligned groups of 8 per thread, two groups in
 // registers that take turns (one is used while the other loads, with no copy
-// between them).  A thread finds the row of a group's first element by binary
-// search over the block's segment bounds (staged in shared memory) and adds
-// each row's partial product to acc with a shared atomic, so the order of the
+// between them).  Each element names its block-local row (group8), and row
+// partial products go to acc with shared atomics, so the order of the
 // additions within a row is not fixed.  The chunk of x arrives by cp.async.
 template <typename V>
 __device__ __forceinline__ void staged_pass_cm(const int* __restrict__ idx, const V* val, const float* x, int nx,
@@ -375,13 +370,13 @@ __device__ __forceinline__ void staged_pass_cm(const int* __restrict__ idx, cons
     }
     const int bc = base[c];
     // a block past the last row (r0 >= rows) owns nothing and reads no bounds
-    if (nr > 0)
-      for (int k = t; k <= nr; k += T) segs[k] = bc + ofs[(size_t)c * ld + r0 + k];
-    else if (t == 0)
-      segs[0] = 0;
+    int E0 = 0, E1 = 0;
+    if (nr > 0) {
+      E0 = bc + ofs[(size_t)c * ld + r0];
+      E1 = bc + ofs[(size_t)c * ld + r0 + nr];
+    }
     cp_async_wait_all();
     __syncthreads();
-    int E0 = segs[0], E1 = segs[nr];
     if (E0 < 0 || E1 < E0 || (long long)E1 > limit) {   // inconsistent bounds: skip the chunk
       if (t == 0) oob(ctrl, 2, E1);
       E1 = E0 = 0;
@@ -393,11 +388,11 @@ __device__ __forceinline__ void staged_pass_cm(const int* __restrict__ idx, cons
     if (w < E1) { load8i(idx + w, ia); load8<V>(val + w, va); }
     while (w < E1) {
       if (w + S < E1) { load8i(idx + w + S, ib); load8<V>(val + w + S, vb); }
-      group8(w, E0, E1, ia, va, j0, jn, xs, segs, nr, acc);
+      group8(w, E0, E1, ia, va, jn, xs, acc);
       w += S;
       if (w >= E1) break;
       if (w + S < E1) { load8i(idx + w + S, ia); load8<V>(val + w + S, va); }
-      group8(w, E0, E1, ib, vb, j0, jn, xs, segs, nr, acc);
+      group8(w, E0, E1, ib, vb, jn, xs, acc);
       w += S;
     }
   }
@@ -444,8 +439,10 @@ __global__ void k_cm_base(int rows, int J, const int* ofs, int* base) {
   base[J] = b;
 }
 
+// The copy's element: (i mod rpb) << 16 | (index - c W), the row local to its
+// block (rpb rows a block) and the index local to its chunk.
 __global__ void k_cm_copy(int rows, const int* seg, int J, const int* ofs, const int* base, const int* idx,
-                          int* cm_idx, int* perm, long long limit, Ctrl* ctrl) {
+                          int* cm_idx, int* perm, long long limit, Ctrl* ctrl, int rpb, int W) {
   const int lane = threadIdx.x & 31;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += (gridDim.x * blockDim.x) >> 5) {
     for (int c = 0; c < J; ++c) {
@@ -457,7 +454,7 @@ __global__ void k_cm_copy(int rows, const int* seg, int J, const int* ofs, const
           oob(ctrl, 3, (long long)dst + e);
           continue;
         }
-        cm_idx[dst + e] = idx[src + e];
+        cm_idx[dst + e] = ((i % rpb) << 16) | (idx[src + e] - c * W);
         perm[src + e] = dst + e;
       }
     }
@@ -885,9 +882,11 @@ void first_iteration_v(const LogArgs& A, const IterCfg& ic, const void* al0, con
     k_cm_base<<<1, 32, 0, st>>>(A.n, A.Jr, A.cm_ofs_r, (int*)A.cm_base_r);
     k_cm_base<<<1, 32, 0, st>>>(A.m, A.Jc, A.cm_ofs_c, (int*)A.cm_base_c);
     k_cm_copy<<<grid1((int64_t)A.n * 32, kT), kT, 0, st>>>(A.n, A.seg_r, A.Jr, A.cm_ofs_r, A.cm_base_r, A.col_idx,
-                                                          (int*)A.cm_idx_r, (int*)A.cm_perm_r, A.nnz_lim, A.ctrl);
+                                                          (int*)A.cm_idx_r, (int*)A.cm_perm_r, A.nnz_lim, A.ctrl,
+                                                          A.rows_pb, A.W);
     k_cm_copy<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.seg_c, A.Jc, A.cm_ofs_c, A.cm_base_c, A.row_idx,
-                                                          (int*)A.cm_idx_c, (int*)A.cm_perm_c, A.nnz_lim, A.ctrl);
+                                                          (int*)A.cm_idx_c, (int*)A.cm_perm_c, A.nnz_lim, A.ctrl,
+                                                          A.cols_pb, A.W);
   }
   k_absorb_all<V><<<grid1((int64_t)std::max(A.n, A.m) * 32, kT), kT, 0, st>>>(A, 1);
   (void)ic;
