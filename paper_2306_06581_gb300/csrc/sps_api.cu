@@ -122,10 +122,8 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
     L->col_ptr = take((size_t)(m + 1) * 4);
     L->col_cur = take((size_t)m * 4);
     L->cnt2 = take((size_t)sweep_geometry(n, m).nchunk * n * 4);
-    // pruned cost maximum for large low-dimensional point problems: below 1e8 pairs the full
-    // sweep is short, and above d = 4 the three-coordinate grid leaves the boxes too wide to prune
-    // (measured at n = 20000, d = 10: 0.55 ms slower than the full sweep)
-    if (P->cost_norm == SPS_COST_MAXNORM && !P->C && P->d >= 1 && P->d <= 4 && (double)n * (double)m > 1e8)
+    // pruned cost maximum for large point problems (below 1e8 pairs the full sweep is short)
+    if (P->cost_norm == SPS_COST_MAXNORM && !P->C && P->d >= 1 && P->d <= 16 && (double)n * (double)m > 1e8)
       L->cmx = take(cost_max_scratch_bytes(n, m, P->d));
     // + 16: staged passes read aligned groups of 8, the ring copies aligned groups of 16
     L->col_idx = take(((size_t)cap + 16) * 4);

@@ -1,5 +1,6 @@
 // sps_costmax.cu -- the cost divisor max_ij D_ij (section 5.1 divides the
-// squared Euclidean cost by its maximum) without visiting every pair.
+// squared Euclidean cost by its maximum) without visiting every pair
+// (the grid-bucketed bounds below for d <= 4, radial bounds for larger d).
 //
 // D_ij is the binary32 spec distance (fl(x_ik - y_jk), then fma-accumulated
 // in k order: raw32()).  A maximum is exact, so any algorithm that evaluates
@@ -318,11 +319,161 @@ __global__ void k_cm_eval_list(CmArgs A) {
   for (int p = blockIdx.x; p < np; p += gridDim.x) eval_pair(A, A.pairs[2 * p], A.pairs[2 * p + 1]);
 }
 
+// ---------------------------------------------------------------------------
+// Radial variant (any d): with c the centre of the bounding box of x and y,
+// |x_i - y_j| <= |x_i - c| + |y_j - c|.  A pair whose spec distance reaches
+// an exact value L found so far needs |x_i - c| >= sqrt(L) - max_j |y_j - c|
+// and |y_j - c| >= sqrt(L) - max_i |x_i - c| (both with a relative margin of
+// 2^-10, far above the binary32 rounding of the radii); L is the maximum over
+// the farthest x against all y and all x against the farthest y.  Only the
+// pairs of the two selected sets are evaluated; if that product exceeds a
+// quarter of n m the full sweep runs instead.
+// ---------------------------------------------------------------------------
+struct NmState {
+  int ext_lo[16], ext_hi[16];
+  float c[16];
+  unsigned long long far_x, far_y;   // (radius bits << 32) | index of the largest radius
+  int nx_sel, ny_sel;
+  int overflow;
+};
+
+struct NmArgs {
+  const float* x;
+  const float* y;
+  int n, m, d;
+  NmState* st;
+  float* rx;   // [n]
+  float* ry;   // [m]
+  int* sx;     // [n] selected x
+  int* sy;     // [m] selected y
+  SketchScalars* sc;
+  long long budget;
+};
+
+constexpr float kRadMargin = 9.765625e-04f;   // 2^-10
+
+__global__ void k_nm_init(NmArgs A) {
+  const int t = threadIdx.x;
+  if (t < 16) { A.st->ext_lo[t] = 0x7fffffff; A.st->ext_hi[t] = (int)0x80000000; }
+  if (t == 0) { A.st->far_x = 0ull; A.st->far_y = 0ull; A.st->nx_sel = 0; A.st->ny_sel = 0; A.st->overflow = 0; }
+}
+
+__global__ void k_nm_extent(NmArgs A) {
+  const int d = A.d;
+  for (int k = 0; k < d; ++k) {
+    int lo = 0x7fffffff, hi = (int)0x80000000;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < A.n + A.m;
+         p += (long long)gridDim.x * blockDim.x) {
+      const float v = p < A.n ? A.x[p * d + k] : A.y[(p - A.n) * d + k];
+      const int o = ord_of(v);
+      lo = min(lo, o);
+      hi = max(hi, o);
+    }
+    for (int s2 = 16; s2 > 0; s2 >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, s2));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, s2));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&A.st->ext_lo[k], lo);
+      atomicMax(&A.st->ext_hi[k], hi);
+    }
+  }
+}
+
+__global__ void k_nm_radii(NmArgs A) {
+  const int d = A.d;
+  float c[16];
+  for (int k = 0; k < d; ++k) c[k] = 0.5f * (float_of(A.st->ext_lo[k]) + float_of(A.st->ext_hi[k]));
+  if (blockIdx.x == 0 && threadIdx.x < d) A.st->c[threadIdx.x] = c[threadIdx.x];
+  unsigned long long bx = 0ull, by = 0ull;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < A.n + A.m;
+       p += (long long)gridDim.x * blockDim.x) {
+    const bool isx = p < A.n;
+    const int idx = isx ? (int)p : (int)(p - A.n);
+    const float* pt = isx ? A.x + (long long)idx * d : A.y + (long long)idx * d;
+    float acc = 0.0f;
+    for (int k = 0; k < d; ++k) {
+      const float t = pt[k] - c[k];
+      acc = fmaf(t, t, acc);
+    }
+    const float r = sqrtf(acc);
+    const unsigned long long key = ((unsigned long long)__float_as_uint(r) << 32) | (unsigned)idx;
+    if (isx) { A.rx[idx] = r; bx = key > bx ? key : bx; }
+    else { A.ry[idx] = r; by = key > by ? key : by; }
+  }
+  for (int s2 = 16; s2 > 0; s2 >>= 1) {
+    const unsigned long long ox = __shfl_xor_sync(0xffffffffu, bx, s2), oy = __shfl_xor_sync(0xffffffffu, by, s2);
+    bx = ox > bx ? ox : bx;
+    by = oy > by ? oy : by;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bx) atomicMax(&A.st->far_x, bx);
+    if (by) atomicMax(&A.st->far_y, by);
+  }
+}
+
+__device__ __forceinline__ float spec_dist(const float* xi, const float* yj, int d) {
+  float acc = 0.0f;
+  for (int k = 0; k < d; ++k) {
+    const float t = __fsub_rn(xi[k], yj[k]);
+    acc = __fmaf_rn(t, t, acc);
+  }
+  return acc;
+}
+
+// The farthest x against all y and all x against the farthest y, exactly.
+__global__ void k_nm_lower(NmArgs A) {
+  const int d = A.d;
+  const int ix = (int)(A.st->far_x & 0xffffffffull), iy = (int)(A.st->far_y & 0xffffffffull);
+  const float* xf = A.x + (long long)ix * d;
+  const float* yf = A.y + (long long)iy * d;
+  float best = 0.0f;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < A.n + A.m;
+       p += (long long)gridDim.x * blockDim.x) {
+    best = fmaxf(best, p < A.n ? spec_dist(A.x + p * d, yf, d) : spec_dist(xf, A.y + (p - A.n) * d, d));
+  }
+  for (int s2 = 16; s2 > 0; s2 >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, s2));
+  if ((threadIdx.x & 31) == 0 && best > 0.0f) atomic_max_nonneg_f(&A.sc->dmax32, best);
+}
+
+__global__ void k_nm_select(NmArgs A) {
+  const float L = sqrtf(A.sc->dmax32) * (1.0f - kRadMargin);
+  const float Rx = __uint_as_float((unsigned)(A.st->far_x >> 32)) * (1.0f + kRadMargin);
+  const float Ry = __uint_as_float((unsigned)(A.st->far_y >> 32)) * (1.0f + kRadMargin);
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < A.n + A.m;
+       p += (long long)gridDim.x * blockDim.x) {
+    if (p < A.n) {
+      if (A.rx[p] * (1.0f + kRadMargin) >= L - Ry) A.sx[atomicAdd(&A.st->nx_sel, 1)] = (int)p;
+    } else {
+      const int j = (int)(p - A.n);
+      if (A.ry[j] * (1.0f + kRadMargin) >= L - Rx) A.sy[atomicAdd(&A.st->ny_sel, 1)] = j;
+    }
+  }
+}
+
+__global__ void k_nm_pairs(NmArgs A) {
+  const int nx = A.st->nx_sel, ny = A.st->ny_sel, d = A.d;
+  if ((long long)nx * ny > A.budget) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.st->overflow = 1;
+    return;
+  }
+  float best = 0.0f;
+  const long long tot = (long long)nx * ny;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(q / ny), b = (int)(q % ny);
+    best = fmaxf(best, spec_dist(A.x + (long long)A.sx[a] * d, A.y + (long long)A.sy[b] * d, d));
+  }
+  for (int s2 = 16; s2 > 0; s2 >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, s2));
+  if ((threadIdx.x & 31) == 0 && best > 0.0f) atomic_max_nonneg_f(&A.sc->dmax32, best);
+}
+
 }  // namespace
 
 size_t cost_max_scratch_bytes(int n, int m, int d) {
-  return 1024 + 512 + sizeof(int) * (2 * (size_t)(kMaxCells + 1) + 2 * (size_t)kMaxCells + (size_t)n + m) +
-         sizeof(float) * 2 * (size_t)kMaxCells * 2 * d + sizeof(int) * 2 * (size_t)kMaxPairs;
+  const size_t grid = 1024 + 512 + sizeof(int) * (2 * (size_t)(kMaxCells + 1) + 2 * (size_t)kMaxCells + (size_t)n + m) +
+                      sizeof(float) * 2 * (size_t)kMaxCells * 2 * d + sizeof(int) * 2 * (size_t)kMaxPairs;
+  const size_t radial = 1024 + 512 + (sizeof(float) + sizeof(int)) * ((size_t)n + m);
+  return d > 4 ? radial : grid;
 }
 
 // Scratch layout: CmState (padded to 1 KB), counts, cursors, permutation,
@@ -330,6 +481,27 @@ size_t cost_max_scratch_bytes(int n, int m, int d) {
 // overflowed (the caller then runs the full sweep, gated on it).
 sps_status launch_cost_max_pruned(const float* x, const float* y, int n, int m, int d, SketchScalars* sc,
                                   char* scratch, const int** overflow_flag, cudaStream_t st) {
+  const int gp = (int)std::min<long long>(152 * 8, ((long long)n + m + 255) / 256);
+  if (d > 4) {
+    NmArgs B;
+    B.x = x; B.y = y; B.n = n; B.m = m; B.d = d; B.sc = sc;
+    char* q = scratch;
+    B.st = reinterpret_cast<NmState*>(q); q += 1024;
+    B.rx = reinterpret_cast<float*>(q); q += sizeof(float) * (size_t)n;
+    B.ry = reinterpret_cast<float*>(q); q += sizeof(float) * (size_t)m;
+    B.sx = reinterpret_cast<int*>(q); q += sizeof(int) * (size_t)n;
+    B.sy = reinterpret_cast<int*>(q);
+    B.budget = (long long)n * m / 4;
+    k_nm_init<<<1, 32, 0, st>>>(B);
+    k_nm_extent<<<gp, 256, 0, st>>>(B);
+    k_nm_radii<<<gp, 256, 0, st>>>(B);
+    k_nm_lower<<<gp, 256, 0, st>>>(B);
+    k_nm_select<<<gp, 256, 0, st>>>(B);
+    k_nm_pairs<<<152 * 8, 256, 0, st>>>(B);
+    add_launches(6);
+    *overflow_flag = &B.st->overflow;
+    return cuda_fail(cudaGetLastError(), "radial cost max");
+  }
   CmArgs A;
   A.x = x; A.y = y; A.n = n; A.m = m; A.d = d;
   A.sc = sc;
@@ -341,7 +513,6 @@ sps_status launch_cost_max_pruned(const float* x, const float* y, int n, int m, 
   p = scratch + ((p - scratch + 255) & ~(size_t)255);
   A.box = reinterpret_cast<float*>(p); p += sizeof(float) * 2 * (size_t)kMaxCells * 2 * d;
   A.pairs = reinterpret_cast<int*>(p);
-  const int gp = (int)std::min<long long>(152 * 8, ((long long)n + m + 255) / 256);
   k_cm_init<<<1, 1024, 0, st>>>(A);
   k_cm_extent<<<gp, 256, 0, st>>>(A);
   k_cm_params<<<1, 1, 0, st>>>(A);

@@ -1,5 +1,6 @@
-"""GPU: the cost divisor max_ij D_ij found by bucketed bounds (used above 1e8
-pairs for d <= 4) equals the full sweep's exact maximum.  Checked through the UOT
+"""GPU: the cost divisor max_ij D_ij found without the full sweep (above 1e8
+pairs: grid-bucketed box bounds for d <= 4, radial bounds for larger d)
+equals the full sweep's exact maximum.  Checked through the UOT
 sampling pattern, which depends on the divisor bit for bit (kappa =
 1 / (D_max (2 lam + eps))), and through the OT values, against the oracle's
 full n x m maximum.
@@ -43,6 +44,24 @@ def test_heavy_tailed_uot_pattern(S, orc):
     w = inputs.uot_n20000(n=11000)
     x, y, a, b = _r32(w.x[:, :4]), _r32(w.y[:, :4]), _r32(w.a), _r32(w.b)
     _check_uot(S, orc, x, y, a, b, 16.0 * 11000 * math.log(11000))
+
+
+def test_heavy_tailed_uot_pattern_d10(S, orc):
+    # the 20000-point family itself (d = 10) at 11000 points: the radial bounds
+    w = inputs.uot_n20000(n=11000)
+    x, y, a, b = _r32(w.x), _r32(w.y), _r32(w.a), _r32(w.b)
+    _check_uot(S, orc, x, y, a, b, 16.0 * 11000 * math.log(11000))
+
+
+def test_gaussian_d6_uot_pattern(S, orc):
+    # light tails in d = 6: many points near the largest radius (the radial sets stay large)
+    rng = np.random.default_rng(8)
+    n = 10500
+    x = rng.standard_normal((n, 6))
+    y = rng.standard_normal((n, 6)) + 0.3
+    a = rng.uniform(0, 1, n)
+    b = rng.uniform(0, 1, n)
+    _check_uot(S, orc, _r32(x), _r32(y), _r32(a / a.sum()), _r32(b / b.sum() * 1.5), 8.0 * n * math.log(n))
 
 
 def test_sphere_uot_pattern(S, orc):
