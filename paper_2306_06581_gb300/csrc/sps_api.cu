@@ -61,10 +61,10 @@ static void plan_staging(int n, int m, int mode, Layout* L, Take& take) {
     return;
   }
   const int big = std::max(n, m);
-  const size_t acc = (size_t)((big + nsm - 1) / nsm);   // row sums and segment bounds of one block
-  if (acc * 8 + 16 + 8192 * 4 > kStageSmem) return;
+  const size_t acc = (size_t)((big + nsm - 1) / nsm);   // row sums of one block
+  if (acc * 4 + 16 + 8192 * 4 > kStageSmem) return;
   if (acc >= 65536) return;   // the chunk-major copy packs block-local rows into 16 bits
-  const int wcap = std::min<int>(kStageWMax, (int)(((kStageSmem - acc * 8 - 16) / 4) / 1024 * 1024));
+  const int wcap = std::min<int>(kStageWMax, (int)(((kStageSmem - acc * 4 - 16) / 4) / 1024 * 1024));
   int J = (big + wcap - 1) / wcap;
   if (mode == SPS_GATHER_STAGED) J = std::max(J, std::min(4, (big + 1023) / 1024));   // forced: several chunks
   const int W = (int)(((big + J - 1) / J + 1023) / 1024 * 1024);

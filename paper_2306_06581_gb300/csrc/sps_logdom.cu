@@ -354,7 +354,7 @@ __device__ __forceinline__ void group8(int w, int E0, int E1, const int (&id)[8]
 template <typename V>
 __device__ __forceinline__ void staged_pass_cm(const int* __restrict__ idx, const V* val, const float* x, int nx,
                                                const int* __restrict__ ofs, const int* __restrict__ base, int ld,
-                                               int r0, int nr, int W, int J, float* xs, float* acc, int* segs,
+                                               int r0, int nr, int W, int J, float* xs, float* acc,
                                                long long limit, Ctrl* ctrl) {
   const int T = blockDim.x, t = threadIdx.x;
   for (int c = 0; c < J; ++c) {
@@ -471,10 +471,9 @@ __device__ __forceinline__ void log_row_phase_staged(const LogArgs& A, int t, fl
   const int r0 = blockIdx.x * A.rows_pb;
   const int nr = max(0, min(A.n, r0 + A.rows_pb) - r0);
   float* acc = dsm + A.W;
-  int* segs = reinterpret_cast<int*>(acc + max(A.rows_pb, A.cols_pb));
   for (int k = threadIdx.x; k < nr; k += blockDim.x) acc[k] = 0.0f;
   staged_pass_cm<V>(A.cm_idx_r, (const V*)A.val, v, A.m, A.cm_ofs_r, A.cm_base_r, A.n + 1, r0, nr, A.W, A.Jr, dsm, acc,
-                    segs, A.nnz_lim, A.ctrl);
+                    A.nnz_lim, A.ctrl);
   float res = 0.0f, unr = 0.0f, mlog = 0.0f;
   for (int k = threadIdx.x; k < nr; k += blockDim.x) {
     const int i = r0 + k;
@@ -492,10 +491,9 @@ __device__ __forceinline__ void log_col_phase_staged(const LogArgs& A, int t, fl
   const int c0 = blockIdx.x * A.cols_pb;
   const int nc = max(0, min(A.m, c0 + A.cols_pb) - c0);
   float* acc = dsm + A.W;
-  int* segs = reinterpret_cast<int*>(acc + max(A.rows_pb, A.cols_pb));
   for (int k = threadIdx.x; k < nc; k += blockDim.x) acc[k] = 0.0f;
   staged_pass_cm<V>(A.cm_idx_c, (const V*)A.valT, u, A.n, A.cm_ofs_c, A.cm_base_c, A.m + 1, c0, nc, A.W, A.Jc, dsm,
-                    acc, segs, A.nnz_lim, A.ctrl);
+                    acc, A.nnz_lim, A.ctrl);
   float unb = 0.0f, mlog = 0.0f;
   for (int k = threadIdx.x; k < nc; k += blockDim.x) {
     const int j = c0 + k;
@@ -670,7 +668,7 @@ bool coop_log(LogArgs A, int iters, int row_only, cudaStream_t st) {
   size_t smem = 0;
   if (STG) {
     // one block per SM owns a fixed row range and column range
-    smem = sizeof(float) * ((size_t)A.W + 2 * (size_t)std::max(A.rows_pb, A.cols_pb) + 1);
+    smem = sizeof(float) * ((size_t)A.W + (size_t)std::max(A.rows_pb, A.cols_pb) + 1);
     if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       cudaGetLastError();
       return false;

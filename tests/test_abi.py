@@ -70,6 +70,23 @@ def test_invalid_params_rejected(S, kw, frag):
     assert frag in S.last_error()
 
 
+def test_sampler_and_modes_validated(S):
+    P = _prob(S)
+    Q = S.make_params(0.1, math.inf, 1000.0, sampler=2)
+    assert S.sps_workspace_bytes(P, Q, 1) == 0
+    assert "sampler" in S.last_error()
+    Q = S.make_params(0.1, math.inf, 1000.0, sketch_mode=5)
+    assert S.sps_workspace_bytes(P, Q, 1) == 0
+    assert "sketch_mode" in S.last_error()
+    # the skip sampler needs no padded single-pass slots: its workspace is smaller
+    big = _prob(S, n=4000, m=4000)
+    el = S.sps_workspace_bytes(big, S.make_params(0.1, math.inf, 2e5, sampler="element"), 1)
+    sk = S.sps_workspace_bytes(big, S.make_params(0.1, math.inf, 2e5, sampler="skip"), 1)
+    assert 0 < sk < el
+    # both samplers for UOT as well
+    assert S.sps_workspace_bytes(big, S.make_params(0.1, 1.0, 2e5, sampler="skip"), 1) > 0
+
+
 def test_invalid_problem_rejected(S):
     Q = S.make_params(0.1, math.inf, 1000.0)
     assert S.sps_workspace_bytes(_prob(S, n=0), Q, 1) == 0
