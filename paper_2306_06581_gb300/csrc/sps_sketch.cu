@@ -303,14 +303,16 @@ __device__ __forceinline__ V gather_val(const V* val, int src, long long nnz, Ct
   return val[src];
 }
 
+// Elements off + lane + 32 k (k < Q) of a column staged in sm[0 .. L): each
+// one's rank among the column's rows places it.
 template <int Q, typename V>
-__device__ __forceinline__ void rank_place(const int* sm, int L, int s0, int lane, const int* tmp_src,
+__device__ __forceinline__ void rank_place(const int* sm, int L, int off, int s0, int lane, const int* tmp_src,
                                            const V* val, int* row_idx, int* csr_pos, V* valT,
                                            long long nnz, Ctrl* ctrl, const float* lv, float* lvT) {
   int r[Q], src[Q], rank[Q];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    const int e = lane + 32 * k;
+    const int e = off + lane + 32 * k;
     r[k] = e < L ? sm[e] : 0x7fffffff;
     src[k] = e < L ? tmp_src[s0 + e] : 0;
     rank[k] = 0;
@@ -322,7 +324,7 @@ __device__ __forceinline__ void rank_place(const int* sm, int L, int s0, int lan
   }
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    const int e = lane + 32 * k;
+    const int e = off + lane + 32 * k;
     if (e < L) {
       row_idx[s0 + rank[k]] = r[k];
       csr_pos[s0 + rank[k]] = src[k];
@@ -332,8 +334,10 @@ __device__ __forceinline__ void rank_place(const int* sm, int L, int s0, int lan
   }
 }
 
+// Eight elements a lane per pass keep the kernel at four or more blocks per SM
+// (one 32-element-a-lane variant for long columns had needed 166 registers).
 template <typename V>
-__global__ void __launch_bounds__(32 * kSortWarps) k_csc_sort(int m, const int* __restrict__ col_ptr,
+__global__ void __launch_bounds__(32 * kSortWarps, 4) k_csc_sort(int m, const int* __restrict__ col_ptr,
                                                               const int* __restrict__ tmp_row,
                                                               const int* __restrict__ tmp_src,
                                                               const V* __restrict__ val, int* row_idx,
@@ -355,9 +359,12 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_csc_sort(int m, const int* 
       __syncwarp();
       for (int e = lane; e < L; e += 32) sm[e] = tmp_row[s0 + e];
       __syncwarp();
-      if (L <= 64) rank_place<2>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl, lv, lvT);
-      else if (L <= 256) rank_place<8>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl, lv, lvT);
-      else rank_place<32>(sm, L, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl, lv, lvT);
+      if (L <= 64) {
+        rank_place<2>(sm, L, 0, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl, lv, lvT);
+      } else {
+        for (int off = 0; off < L; off += 256)
+          rank_place<8>(sm, L, off, s0, lane, tmp_src, val, row_idx, csr_pos, valT, nnz, ctrl, lv, lvT);
+      }
     } else {
       for (int e = lane; e < L; e += 32) {
         const int re = tmp_row[s0 + e];
