@@ -71,7 +71,6 @@ __global__ void k_cm_init(CmArgs A) {
 
 __global__ void k_cm_extent(CmArgs A) {
   const int d = A.d;
-  const long long nx = (long long)A.n * d, ny = (long long)A.m * d;
   for (int k = 0; k < d; ++k) {
     int lo = 0x7fffffff, hi = (int)0x80000000;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < A.n + A.m;
@@ -90,8 +89,6 @@ __global__ void k_cm_extent(CmArgs A) {
       atomicMax(&A.st->ext_hi[k], hi);
     }
   }
-  (void)nx;
-  (void)ny;
 }
 
 // Grid: the (up to) three coordinates of largest extent, the same number of
