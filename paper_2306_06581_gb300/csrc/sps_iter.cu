@@ -998,11 +998,15 @@ int units_grid_dispatch(const IterCfg& ic, int n, int m, int cap) {
   }
 }
 
+// Set by launch_iter_init when it enqueued this solve's work units (the unit
+// kernel runs only on a partition of the current sketch).
+thread_local bool g_units_ready = false;
+
 // Enqueue `iters` iterations; returns the number of kernels launched.
 template <typename V, typename T>
 int iterate_vt(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, int iters, cudaStream_t st) {
   const IterArgs A = make_args(pd, L, ws, ic);
-  if (ic.persistent && A.unit_r && A.unit_c) {
+  if (ic.persistent && A.unit_r && A.unit_c && g_units_ready) {
     const bool ok = ic.uot ? coop_units<V, T, true>(A, iters, st) : coop_units<V, T, false>(A, iters, st);
     if (ok) return 1;
   }
@@ -1070,10 +1074,12 @@ sps_status launch_iter_init(const ProbDev& pd, const Layout& L, char* ws, const 
     k_iter_init<float><<<std::max(g, 1), kThreads, 0, st>>>(pd.n, pd.m, at<float>(ws, L.u), at<float>(ws, L.v),
         (const float*)init_alpha, (const float*)init_beta, ic.eps, at<Ctrl>(ws, L.ctrl));
   add_launches(1);
+  g_units_ready = false;
   if (ic.persistent && L.unit_r && L.unit_c) {
     // work units for the grid the persistent kernel will get
     const int grid = units_grid_dispatch(ic, pd.n, pd.m, L.nblk_rows);
     if (grid > 0) {
+      g_units_ready = true;
       const int W = grid * kUnitWarps - 1;
       k_units<<<1, 1024, 0, st>>>(at<int>(ws, L.row_ptr), pd.n, W, at<int>(ws, L.unit_r));
       k_units<<<1, 1024, 0, st>>>(at<int>(ws, L.col_ptr), pd.m, W, at<int>(ws, L.unit_c));
