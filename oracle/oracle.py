@@ -46,13 +46,13 @@ class Problem(C.Structure):
                 ("x", C.c_void_p), ("y", C.c_void_p), ("C", C.c_void_p),
                 ("cost_norm", C.c_int32), ("cost_scale", C.c_double), ("a", C.c_void_p), ("b", C.c_void_p),
                 ("eps", C.c_double), ("lam", C.c_double), ("s", C.c_double),
-                ("seed", C.c_uint64), ("pid", C.c_uint32)]
+                ("seed", C.c_uint64), ("pid", C.c_uint32), ("cost_kind", C.c_int32), ("eta", C.c_double)]
 
 
 class Scalars(C.Structure):
     _fields_ = [("dmax64", C.c_double), ("dmax32", C.c_float), ("sum1", C.c_double),
                 ("sum2", C.c_double), ("scale32", C.c_float), ("s32", C.c_float),
-                ("gamma32", C.c_float), ("kappa32", C.c_float)]
+                ("gamma32", C.c_float), ("kappa32", C.c_float), ("inv2eta32", C.c_float), ("g2_32", C.c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -77,6 +77,7 @@ def load():
             _lib.orc_draw24.argtypes = [u64, u32, u32, u32]
             _lib.orc_draw24.restype = u32
             _lib.orc_exp32_vec.argtypes = [P, P, i64]
+            _lib.orc_cos32_vec.argtypes = [P, P, i64]
             _lib.orc_log32_vec.argtypes = [P, P, i64]
             _lib.orc_exact_sum_f32.argtypes = [P, i64]
             _lib.orc_exact_sum_f32.restype = f64
@@ -160,6 +161,15 @@ def log32(x):
     return y
 
 
+def cos32(z):
+    """Spec cos in binary32 on [0, pi/2] (the WFR decision path)."""
+    lib = load()
+    z = _c(np.ravel(z), np.float32)
+    y = np.empty_like(z)
+    lib.orc_cos32_vec(_ptr(z), _ptr(y), z.size)
+    return y
+
+
 def log1m32(q):
     """Spec log(1 - q) in binary32, 0 < q < 1 (skip sampler gaps)."""
     lib = load()
@@ -191,7 +201,9 @@ class OracleProblem:
     """Holds the numpy arrays of one problem alive for the C struct."""
 
     def __init__(self, a, b, eps, s, lam=math.inf, x=None, y=None, C_=None, cost_norm=1,
-                 seed=0x5EED, pid=0, cost_scale=1.0):
+                 seed=0x5EED, pid=0, cost_scale=1.0, cost_kind="sqeuclid", eta=0.0):
+        """cost_kind: "sqeuclid" (squared Euclidean, or the matrix C_) or "wfr"
+        (Wasserstein-Fisher-Rao with parameter eta; raw cost, cost_norm = 0)."""
         self.a = _c(a, np.float64)
         self.b = _c(b, np.float64)
         self.x = _c(x, np.float64)
@@ -203,9 +215,10 @@ class OracleProblem:
         self.cost_norm = int(cost_norm)
         self.cost_scale = float(cost_scale)
         self.seed, self.pid = int(seed), int(pid)
+        self.cost_kind, self.eta = (1 if cost_kind == "wfr" else 0), float(eta)
         self.struct = Problem(self.n, self.m, self.d, _ptr(self.x), _ptr(self.y), _ptr(self.C),
                               self.cost_norm, self.cost_scale, _ptr(self.a), _ptr(self.b), self.eps,
-                              self.lam, self.s, self.seed, self.pid)
+                              self.lam, self.s, self.seed, self.pid, self.cost_kind, self.eta)
         self._factors = None
 
     @property
@@ -434,7 +447,7 @@ def dense_sinkhorn(prob: OracleProblem, tol=1e-6, max_iter=1000, stop_rule=STOP_
             "terms": terms, "obj": r1, "K": K, "C": Cn}
 
 
-__all__ = ["build_oracle", "load", "philox4x32_10", "draw24", "exp32", "log32", "log1m32", "skip_words",
+__all__ = ["build_oracle", "load", "philox4x32_10", "draw24", "exp32", "log32", "log1m32", "skip_words", "cos32",
            "exact_sum_f32",
            "OracleProblem", "sinkhorn_sparse", "sinkhorn_dense", "sinkhorn_log_sparse",
            "objective_terms", "spar_sink", "dense_sinkhorn", "STOP_RESIDUAL", "STOP_DELTA_UV"]

@@ -11,6 +11,7 @@
  * compiler invented would change it.  Explicit fmaf() calls are part of the
  * spec and stay fused.
  */
+#define _DEFAULT_SOURCE
 #include "sparsink_oracle.h"
 
 #include <math.h>
@@ -142,6 +143,24 @@ float orc_log32(float x) {
 void orc_exp32_vec(const float* x, float* y, int64_t n) {
   for (int64_t k = 0; k < n; ++k) y[k] = orc_exp32(x[k]);
 }
+/* cos z for 0 <= z <= pi/2: 1 - z^2/2! + z^4/4! - ... to z^14/14! in w = z^2
+ * (the next term is below 7e-11 at z = pi/2), Horner form. */
+float orc_cos32(float z) {
+  const float w = z * z;
+  float p = (float)(-1.0 / 87178291200.0);
+  p = fmaf(p, w, (float)(1.0 / 479001600.0));
+  p = fmaf(p, w, (float)(-1.0 / 3628800.0));
+  p = fmaf(p, w, (float)(1.0 / 40320.0));
+  p = fmaf(p, w, (float)(-1.0 / 720.0));
+  p = fmaf(p, w, (float)(1.0 / 24.0));
+  p = fmaf(p, w, -0.5f);
+  return fmaf(p, w, 1.0f);
+}
+
+void orc_cos32_vec(const float* z, float* y, int64_t n) {
+  for (int64_t k = 0; k < n; ++k) y[k] = orc_cos32(z[k]);
+}
+
 void orc_log32_vec(const float* x, float* y, int64_t n) {
   for (int64_t k = 0; k < n; ++k) y[k] = orc_log32(x[k]);
 }
@@ -274,13 +293,40 @@ static double cost_divisor(const orc_problem* P, const orc_scalars* S) {
   return 1.0;
 }
 
+static int is_wfr(const orc_problem* P) { return P->cost_kind == 1; }
+
+/* Wasserstein-Fisher-Rao cost (section 2.2) from the squared distance D:
+ * C = -log cos_+^2(sqrt(D) / (2 eta)), +inf where sqrt(D) / (2 eta) >= pi/2. */
+static double wfr_cost64(const orc_problem* P, double D) {
+  const double z = sqrt(D) / (2.0 * P->eta);
+  if (z >= 0.5 * M_PI) return INFINITY;
+  return -2.0 * log(cos(z));
+}
+
+/* The cost of the value path: WFR, or the raw cost over its divisor. */
+static double cost64(const orc_problem* P, const orc_scalars* S, int32_t i, int32_t j) {
+  const double d = raw_cost64(P, i, j);
+  return is_wfr(P) ? wfr_cost64(P, d) : d / cost_divisor(P, S);
+}
+
+/* binary32 decision factor K_ij^{eps/(2lam+eps)} = exp(-C_ij/(2lam+eps)).
+ * Squared Euclidean: E(-D kappa).  WFR: with z = fl(fl(sqrt D) inv2eta),
+ * 0 for z >= fl(pi/2), else E(fl(g2 L(cos z))) (cos^2 to the power
+ * 1/(2lam+eps)), 0 when the spec cos is not positive. */
+static float uot_factor(const orc_problem* P, const orc_scalars* S, float dd) {
+  if (!is_wfr(P)) return orc_exp32(-(dd * S->kappa32));
+  const float z = sqrtf(dd) * S->inv2eta32;
+  if (!(z < (float)(0.5 * M_PI))) return 0.0f;
+  const float c = orc_cos32(z);
+  if (!(c > 0.0f)) return 0.0f;
+  return orc_exp32(S->g2_32 * orc_log32(c));
+}
+
 /* UOT weight w_ij = (A_i B_j) E(-D_ij kappa): the numerator of Eq. (pij-uot),
  * since K_ij^{eps/(2lam+eps)} = exp(-C_ij/(2lam+eps)). */
 static float uot_weight(const orc_problem* P, const float* rowf, const float* colf,
                         const orc_scalars* S, int32_t i, int32_t j) {
-  float dd = raw_cost32(P, i, j);
-  float t = dd * S->kappa32;
-  float e = orc_exp32(-t);
+  const float e = uot_factor(P, S, raw_cost32(P, i, j));
   return (rowf[i] * colf[j]) * e;
 }
 
@@ -295,6 +341,8 @@ static int check_problem(const orc_problem* P) {
   if (!P->C && (P->d < 1 || !P->x || !P->y)) return -1;
   if (!(P->eps > 0.0) || !(P->s > 0.0) || !(P->lambda > 0.0)) return -1;
   if (P->cost_norm == 2 && !(P->cost_scale > 0.0)) return -1;
+  if (P->cost_kind != 0 && P->cost_kind != 1) return -1;
+  if (is_wfr(P) && (P->C || P->cost_norm != 0 || !(P->eta > 0.0))) return -1;
   if (!P->a || !P->b) return -1;
   for (int32_t i = 0; i < P->n; ++i) if (!(P->a[i] >= 0.0) || isinf(P->a[i])) return -1;
   for (int32_t j = 0; j < P->m; ++j) if (!(P->b[j] >= 0.0) || isinf(P->b[j])) return -1;
@@ -342,6 +390,8 @@ int orc_factors(const orc_problem* P, float* rowf, float* colf, orc_scalars* S) 
   double t = 2.0 * P->lambda + P->eps;
   S->gamma32 = (float)(P->lambda / t);
   S->kappa32 = (float)(1.0 / (cost_divisor(P, S) * t));
+  S->inv2eta32 = is_wfr(P) ? (float)(1.0 / (2.0 * P->eta)) : 0.0f;
+  S->g2_32 = (float)(2.0 / t);
   for (int32_t i = 0; i < n; ++i) {
     float a32 = (float)P->a[i];
     rowf[i] = a32 > 0.0f ? orc_exp32(S->gamma32 * orc_log32(a32)) : 0.0f;
@@ -396,8 +446,7 @@ int64_t orc_count(const orc_problem* P, const float* rowf, const float* colf,
 /* Value of a sampled element (i, j) with p* = ps, written at position c. */
 static void emit_elem(const orc_problem* P, const orc_scalars* S, int32_t i, int32_t j, float ps, int32_t c,
                       int32_t* cols, double* val, double* logval, float* pstar, double* cost) {
-  double d64 = raw_cost64(P, i, j);
-  double Cn = d64 / cost_divisor(P, S);
+  double Cn = cost64(P, S, i, j);
   double Kij = exp(-Cn / P->eps);
   if (cols) cols[c] = j;
   if (val) val[c] = Kij / (double)ps;
@@ -592,11 +641,9 @@ int orc_dense_kernel(const orc_problem* P, double* K, double* Cn) {
       float d = raw_cost32(P, i, j);
       if (d > S.dmax32) S.dmax32 = d;
     }
-  const double dv = cost_divisor(P, &S);
   for (int32_t i = 0; i < P->n; ++i)
     for (int32_t j = 0; j < P->m; ++j) {
-      double d = raw_cost64(P, i, j);
-      double c = d / dv;
+      double c = cost64(P, &S, i, j);
       if (Cn) Cn[(int64_t)i * P->m + j] = c;
       if (K) K[(int64_t)i * P->m + j] = exp(-c / P->eps);
     }

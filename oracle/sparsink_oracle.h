@@ -58,6 +58,9 @@ float orc_exp32(float x);
 float orc_log32(float x);
 /* vectorised forms for tests */
 void orc_exp32_vec(const float* x, float* y, int64_t n);
+/* binary32 spec cos on [0, pi/2] (Taylor series in z^2 to z^14, Horner form). */
+float orc_cos32(float z);
+void orc_cos32_vec(const float* z, float* y, int64_t n);
 void orc_log32_vec(const float* x, float* y, int64_t n);
 
 /* Exact sum of non-negative finite binary32 values, rounded once to the
@@ -82,6 +85,10 @@ typedef struct {
   double s;             /* expected sample budget */
   uint64_t seed;
   uint32_t pid;         /* problem id: third Philox counter word */
+  int32_t cost_kind;    /* 0: squared Euclidean (or C); 1: Wasserstein-Fisher-Rao
+                           C_ij = -log cos_+^2(d_ij / (2 eta)), d_ij the Euclidean distance of
+                           the points (section 2.2); needs points and cost_norm = 0 */
+  double eta;           /* WFR: eta > 0 (transport blocked where d_ij >= pi eta) */
 } orc_problem;
 
 /* Scalars shared by every element's decision and value. */
@@ -94,6 +101,8 @@ typedef struct {
   float s32;         /* fl32(s) */
   float gamma32;     /* UOT exponent lam/(2lam+eps) */
   float kappa32;     /* UOT: 1/(Dnorm (2lam+eps)) */
+  float inv2eta32;   /* WFR: fl32(1/(2 eta)) */
+  float g2_32;       /* WFR UOT: fl32(2/(2lam+eps)), K^{eps/(2lam+eps)} = cos^{g2} */
 } orc_scalars;
 
 /* Row and column factors of the decision.  OT: r[i], c[j] with
