@@ -3,7 +3,7 @@
 // output line.
 //
 // Iteration t -> t+1 has two phases:
-//   row phase  q = K~ v^t (CSR; LPR lanes per row), u^{t+1} = (a / q)^phi, and
+//   row phase  q = K~ v^t (CSR), u^{t+1} = (a / q)^phi, and
 //              -- fused, at no extra pass -- the stopping residual of the pair
 //              (u^t, v^t):
 //                  rho_t = sum over reachable i of | (u^t_i)^{1/phi} q_i - a_i |
@@ -16,12 +16,17 @@
 // (v_j = 0): they carry mass no plan on the sketch can move, are left out of
 // the residual, and their mass is reported.
 //
-// Two executions of the same phases:
-//   - a persistent cooperative kernel that runs a whole chunk of iterations in
-//     one launch, with two grid barriers per iteration (bounded spin waits);
-//     block 0 reduces the block partials in a fixed order and decides;
+// Three executions of the same phases:
+//   - k_iterate_units: a persistent cooperative kernel over fixed nnz-balanced
+//     work units (element rings filled by bulk copies, the gathered vector
+//     staged in shared memory, a counting grid barrier; warp 0 of block 0
+//     reduces the block partials in a fixed order and decides) -- the path a
+//     solve takes;
+//   - k_iterate: a persistent cooperative kernel with LPR lanes per row, two
+//     grid barriers per iteration (bounded spin waits), block 0 deciding --
+//     used when the unit kernel's launch is refused;
 //   - one kernel per phase (the last block to finish reduces the partials),
-//     used for the final residual and when a cooperative launch is refused.
+//     used for the final residual and when no cooperative launch is possible.
 #include <cuda_runtime.h>
 #include <math.h>
 

@@ -293,14 +293,6 @@ template <> __device__ __forceinline__ void load8<__half>(const __half* p, float
   }
 }
 
-// The sparse products of one block's rows [r0, r0 + nr) with x staged in
-// shared memory chunk by chunk (J chunks of W entries of x, x of length nx),
-// over the chunk-major copy: the block's elements of chunk c are one
-// contiguous range, streamed as aligned groups of 8 per thread with the next
-// group loaded before the current one is used.  A thread finds the row of its
-// first element by binary search over the block's segment bounds (staged in
-// shared memory) and adds each row's partial product to acc with a shared
-// atomic, so the order of the additions within a row is not fixed.
 // 16-byte asynchronous copy global -> shared through L2 (cp.async.cg), and the
 // wait for all of this thread's copies.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
