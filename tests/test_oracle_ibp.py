@@ -68,6 +68,27 @@ def test_fixed_point_marginals(ibpo):
     assert abs(q.sum() - 1.0) < 1e-8
 
 
+def test_fixed_point_marginals_rectangular(ibpo, orc):
+    # measures on their own supports (n_k != n): K_k is n x n_k and not symmetric
+    n, eps = 30, 0.1
+    x = _support(n, 2, 12)
+    rng = np.random.default_rng(13)
+    Ks, bs = [], []
+    for k, nk in enumerate((40, 25, 35)):
+        y = _support(nk, 2, 20 + k) * 0.8 + 0.1
+        b = rng.uniform(0.2, 1.0, nk)
+        b /= b.sum()
+        K, _ = orc.OracleProblem(np.full(n, 1.0 / n), b, eps, 1.0, math.inf, x=x, y=y).dense_kernel()
+        Ks.append(K)
+        bs.append(b)
+    q, info = ibpo.ibp(Ks, bs, [0.5, 0.2, 0.3], tol=1e-12, max_iter=100000)
+    assert info["delta"] <= 1e-12
+    for k in range(3):
+        u, v = info["u"][k], info["v"][k]
+        assert np.allclose(v * (Ks[k].T @ u), bs[k], rtol=1e-9, atol=1e-14)
+        assert np.allclose(u * (Ks[k] @ v), q, rtol=1e-7, atol=1e-12)
+
+
 def _ot_eps(q, b, C, eps):
     """OT_eps(q, b) = min <T, C> - eps H(T), H(T) = -sum T (log T - 1), by Sinkhorn
     iterations in log form run to convergence (the definition, written out)."""

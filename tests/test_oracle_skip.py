@@ -138,7 +138,7 @@ def test_uot_inclusion_frequencies(orc):
     b = rng.uniform(0.05, 1.5, m)
     x = rng.standard_normal((n, 2))
     y = rng.standard_normal((m, 2)) + 0.5
-    s, K = 30.0, 2500
+    s, K = 100.0, 2500   # s / Z > 1: a row bound without the factor s / Z would be too small
     D = ((x[:, None, :] - y[None, :, :]) ** 2).sum(-1)
     C = D / D.astype(np.float32).max()
     g = lam / (2 * lam + eps)
