@@ -59,6 +59,29 @@ def test_uot_probability_tends_to_ot(orc):
         assert abs(Puot.pstar_raw(i, j) / Pot.pstar_raw(i, j) - 1) < 1e-5
 
 
+def test_inclusion_rate_over_many_decisions(orc):
+    # one sketch of 4.2e6 decisions: the kept count is a sum of independent
+    # Bernoulli(p*) (sd ~ 1e3), so a 1% bias in the keep rule shows at ~10 sd;
+    # p* from the FP64 definitions (within ~1e-6 of the binary32 spec)
+    n, m = 2000, 2100
+    for lam in (math.inf, 1.0):
+        w = inputs.small_problem(n=n, m=m, d=3, seed=17, mass_b=1.0 if math.isinf(lam) else 1.5)
+        s = 0.3 * n * m
+        eps = 0.1
+        P = orc.OracleProblem(w.a, w.b, eps, s, lam, x=w.x, y=w.y, seed=77)
+        _, nnz = P.count()
+        if math.isinf(lam):
+            q = np.outer(np.sqrt(w.a), np.sqrt(w.b))
+        else:
+            x32, y32 = w.x.astype(np.float32).astype(np.float64), w.y.astype(np.float32).astype(np.float64)
+            D = ((x32[:, None, :] - y32[None, :, :]) ** 2).sum(-1)
+            g = lam / (2 * lam + eps)
+            q = np.outer(w.a, w.b) ** g * np.exp(-(D / D.max()) / (2 * lam + eps))
+        p = np.minimum(1.0, s * q / q.sum())
+        sd = math.sqrt((p * (1 - p)).sum())
+        assert abs(nnz - p.sum()) < 5 * sd + 1e-5 * p.sum(), (lam, nnz, p.sum(), sd)
+
+
 def test_unbiased_and_expected_nnz(orc):
     n, m = 10, 12
     w = inputs.small_problem(n=n, m=m, d=2, seed=6, eps=0.5)
