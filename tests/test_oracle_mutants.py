@@ -1,0 +1,90 @@
+"""The pins catch plausible mistakes: each case plants one mistake in a copy
+of the oracle (on the CPU, in a temporary directory), runs the pins that
+should notice it, and expects them to fail.  The product code is not
+involved."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CASES = [
+    # (what, file in oracle/ ["#k": the k-th occurrence of the text, else its only one],
+    #  correct text, planted text, pins)
+    ("OT factor without the square root of a", "sparsink_oracle.c",
+     "for (int32_t i = 0; i < n; ++i) sa[i] = sqrtf((float)P->a[i]);",
+     "for (int32_t i = 0; i < n; ++i) sa[i] = (float)P->a[i];", "test_oracle_sampler.py"),
+    ("UOT exponent lam / (lam + eps) in the probabilities", "sparsink_oracle.c",
+     "S->gamma32 = (float)(P->lambda / t);", "S->gamma32 = (float)(P->lambda / (P->lambda + P->eps));",
+     "test_oracle_sampler.py"),
+    ("keep rule inflated by 1%", "sparsink_oracle.c", "return u < praw;", "return u <= praw * 1.01f;",
+     "test_oracle_sampler.py"),
+    ("value K p* instead of K / p*", "sparsink_oracle.c", "if (val) val[c] = Kij / (double)ps;",
+     "if (val) val[c] = Kij * (double)ps;", "test_oracle_sampler.py"),
+    ("Alg. 2 exponent lam / (2 lam + eps), scaling iterations", "sparsink_oracle.c#1",
+     "const double phi = isinf(lambda) ? 1.0 : lambda / (lambda + eps);",
+     "const double phi = isinf(lambda) ? 1.0 : lambda / (2.0 * lambda + eps);", "test_oracle_sinkhorn.py"),
+    ("Alg. 2 exponent lam / (2 lam + eps), log-domain iterations", "sparsink_oracle.c#2",
+     "const double phi = isinf(lambda) ? 1.0 : lambda / (lambda + eps);",
+     "const double phi = isinf(lambda) ? 1.0 : lambda / (2.0 * lambda + eps);", "test_oracle_sinkhorn.py"),
+    ("entropy without the -1", "sparsink_oracle.c", "ne += T * (lt - 1.0);", "ne += T * lt;",
+     "test_oracle_sinkhorn.py"),
+    ("KL term sign", "sparsink_oracle.c", "return x * log(x / y) - x + y;", "return x * log(x / y) + x - y;",
+     "test_oracle_sinkhorn.py"),
+    ("skip sampler: gap rate log q instead of log(1 - q)", "sparsink_oracle.c",
+     "const float L = full ? 0.0f : orc_log1m32(q);", "const float L = full ? 0.0f : orc_log32(q);",
+     "test_oracle_skip.py"),
+    ("skip sampler: acceptance p instead of p / q", "sparsink_oracle.c",
+     "const float acc = full ? p : p / q;", "const float acc = p;", "test_oracle_skip.py"),
+    ("skip sampler: one word for gap and acceptance", "sparsink_oracle.c",
+     "const float V = (float)(w[1] >> 8) * 0x1p-24f;", "const float V = (float)(w[0] >> 8) * 0x1p-24f;",
+     "test_oracle_skip.py"),
+    ("WFR: cos instead of cos^2", "sparsink_oracle.c", "return -2.0 * log(cos(z));", "return -log(cos(z));",
+     "test_oracle_wfr.py"),
+    ("WFR: decision angle d / eta", "sparsink_oracle.c",
+     "S->inv2eta32 = is_wfr(P) ? (float)(1.0 / (2.0 * P->eta)) : 0.0f;",
+     "S->inv2eta32 = is_wfr(P) ? (float)(1.0 / P->eta) : 0.0f;", "test_oracle_wfr.py"),
+    ("IBP: arithmetic instead of geometric mean", "ibp_oracle.py",
+     "logq += w[k] * np.log(np.where(Kv[k] > 0, Kv[k], 1.0))",
+     "logq += w[k] * np.where(Kv[k] > 0, Kv[k], 1.0)", "test_oracle_ibp.py"),
+    ("IBP: K instead of K^T for v", "ibp_oracle.py",
+     "vs[k] = _safe_div(np.asarray(bs[k], np.float64), Ks[k].T @ us[k])",
+     "vs[k] = _safe_div(np.asarray(bs[k], np.float64), Ks[k] @ us[k])", "test_oracle_ibp.py"),
+]
+
+
+def _copy(tmp_path):
+    for sub in ("oracle", "paper_2306_06581_gb300", "tests"):
+        shutil.copytree(os.path.join(ROOT, sub), os.path.join(tmp_path, sub),
+                        ignore=shutil.ignore_patterns("*.so", "*.o", "_build", "__pycache__", "*.tmp"))
+
+
+def _pins(tmp_path, files):
+    return subprocess.run([sys.executable, "-m", "pytest", *[os.path.join("tests", f) for f in files], "-q", "-x",
+                           "-m", "not gpu", "-p", "no:cacheprovider", "-W", "ignore::RuntimeWarning"],
+                          cwd=tmp_path, capture_output=True, text=True, timeout=600)
+
+
+def test_unchanged_copy_passes(tmp_path):
+    # the control: in the copy, with nothing planted, every pin above passes (so a failure below is the mistake's)
+    _copy(tmp_path)
+    r = _pins(tmp_path, sorted({c[4] for c in CASES}))
+    assert r.returncode == 0, (r.stdout[-2000:], r.stderr[-2000:])
+
+
+@pytest.mark.parametrize("what,fn,good,bad,pins", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_is_caught(tmp_path, what, fn, good, bad, pins):
+    _copy(tmp_path)
+    fn, _, k = fn.partition("#")
+    path = os.path.join(tmp_path, "oracle", fn)
+    src = open(path).read()
+    parts = src.split(good)
+    # the correct text is where the case expects it: once, or at least k times for "#k"
+    assert len(parts) > int(k) if k else len(parts) == 2, what
+    k = int(k or 1)
+    open(path, "w").write(good.join(parts[:k]) + bad + good.join(parts[k:]))
+    r = _pins(tmp_path, [pins])
+    assert r.returncode == 1 and " failed" in r.stdout, (what, r.stdout[-2000:], r.stderr[-2000:])
