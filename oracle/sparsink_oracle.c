@@ -171,7 +171,7 @@ void orc_log32_vec(const float* x, float* y, int64_t n) {
  * 64-bit words (carry-save), so any order of additions gives the same
  * integer; the result is rounded once to binary64.
  * Pinned against Python's math.fsum (a correctly rounded sum) by
- * tests/test_oracle_exactsum.py.
+ * tests/test_oracle_specmath.py.
  * ====================================================================== */
 #define SA_DIGITS 12
 typedef struct {

@@ -47,6 +47,16 @@ CASES = [
     ("WFR: decision angle d / eta", "sparsink_oracle.c",
      "S->inv2eta32 = is_wfr(P) ? (float)(1.0 / (2.0 * P->eta)) : 0.0f;",
      "S->inv2eta32 = is_wfr(P) ? (float)(1.0 / P->eta) : 0.0f;", "test_oracle_wfr.py"),
+    ("Philox: nine rounds", "sparsink_oracle.c", "for (int r = 0; r < 10; ++r) {",
+     "for (int r = 0; r < 9; ++r) {", "test_oracle_rng.py"),
+    ("exact sum: ties not to even", "sparsink_oracle.c", "if (round_bit && (sticky || (mant & 1u))) {",
+     "if (round_bit && sticky) {", "test_oracle_specmath.py"),
+    ("exact sum: sticky scan skips a bit", "sparsink_oracle.c", "for (int p = hb - 54; p >= 0 && !sticky; --p)",
+     "for (int p = hb - 55; p >= 0 && !sticky; --p)", "test_oracle_specmath.py"),
+    ("KL(0 | y) taken as 0", "sparsink_oracle.c", "if (x == 0.0) return y;", "if (x == 0.0) return 0.0;",
+     "test_oracle_sinkhorn.py"),
+    ("log-sum-exp without its shift back", "sparsink_oracle.c", "  return mx + log(acc);", "  return log(acc);",
+     "test_oracle_sinkhorn.py"),
     ("IBP: arithmetic instead of geometric mean", "ibp_oracle.py",
      "logq += w[k] * np.log(np.where(Kv[k] > 0, Kv[k], 1.0))",
      "logq += w[k] * np.where(Kv[k] > 0, Kv[k], 1.0)", "test_oracle_ibp.py"),

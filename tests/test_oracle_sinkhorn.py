@@ -167,6 +167,7 @@ def test_objective_terms_against_scipy(orc):
     rng = np.random.default_rng(6)
     n, m = 5, 4
     T = rng.uniform(0, 0.1, (n, m)); T[1, 2] = 0.0
+    T[3, :] = 0.0                      # a row with no mass: KL(0 | a_3) = a_3
     C = rng.uniform(0, 1, (n, m))
     a = rng.uniform(0.05, 0.5, n); b = rng.uniform(0.05, 0.5, m)
     ps = rng.uniform(0.1, 1, (n, m)).astype(np.float32)
@@ -178,6 +179,7 @@ def test_objective_terms_against_scipy(orc):
     assert abs(t["transport"] - (T * C).sum()) < 1e-15
     assert abs(t["neg_entropy"] - (-(special.entr(T).sum() + T.sum()))) < 1e-14
     assert abs(t["kl_a"] - special.kl_div(T.sum(1), a).sum()) < 1e-14
+    assert abs(t["kl_a"] - (special.kl_div(np.delete(T.sum(1), 3), np.delete(a, 3)).sum() + a[3])) < 1e-14
     assert abs(t["kl_b"] - special.kl_div(T.sum(0), b).sum()) < 1e-14
     assert abs(t["logp"] - (T * np.log(ps.astype(np.float64))).sum()) < 1e-14
 

@@ -70,6 +70,36 @@ def test_exact_sum_matches_fsum(orc):
         assert orc.exact_sum_f32(x) == math.fsum(x.astype(np.float64).tolist())
 
 
+def test_exact_sum_rounding_at_ties(orc):
+    # sums that land exactly halfway between two doubles, or just beyond it
+    # with the only extra bit one or many places below the rounding bit:
+    # fsum rounds to nearest, ties to even
+    u = 2.0 ** -52
+    cases = [
+        [1.0, u / 2],                         # tie, even neighbour below: stays 1
+        [1.0, u, u / 2],                      # tie, odd mantissa: rounds up to 1 + 2u
+        [1.0, u / 2, u / 4],                  # above the tie by the next bit: rounds up
+        [1.0, u / 2, 2.0 ** -149],            # above the tie by the smallest subnormal: rounds up
+        # 2^53 - 1 + 1/2: a tie whose rounding carries into the next binade
+        [2.0 ** 52, 2.0 ** 52 - 2.0 ** 28, 2.0 ** 28 - 16, 15.0, 0.5],
+        [2.0 ** 100, 2.0 ** 47],              # tie far above 1
+        [2.0 ** 100, 2.0 ** 48, 2.0 ** 47],
+    ]
+    for c in cases:
+        x = np.array(c, np.float64).astype(np.float32)
+        assert np.array_equal(x.astype(np.float64), np.array(c)), c     # every term is a binary32
+        assert orc.exact_sum_f32(x) == math.fsum(c), c
+    rng = np.random.default_rng(5)
+    ties = 0
+    for _ in range(3000):
+        # 1 plus multiples of 2^-60: the bits below the double's last one are often all zero
+        k = rng.integers(0, 1 << 10, 3)
+        c = [1.0] + [float(v) * 2.0 ** -60 for v in k]
+        ties += (int(sum(k)) & 0x7F) == 0x40
+        assert orc.exact_sum_f32(np.array(c, np.float32)) == math.fsum(c)
+    assert ties > 5
+
+
 def test_exact_sum_order_independent(orc):
     rng = np.random.default_rng(3)
     x = np.exp(rng.uniform(-60, 20, 20001)).astype(np.float32)
