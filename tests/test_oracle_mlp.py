@@ -2,6 +2,12 @@
 - the analytic gradient equals central finite differences of the loss (FP64);
 - the gauge fix keeps alpha_i + beta_j and balances sum a alpha = sum b beta;
 - Adam under a constant gradient moves every weight by lr g / (|g| + eps) per step;
+- the predictions do not change when all points are scaled by c and the cost
+  maximum by c^2, nor when every point of either side is split into two equal
+  halves (the mass features n a_i and the pooled mean see the same values);
+- a network with constant output c has loss = the a-weighted mean of
+  (c - target)^2 over eps^2, minimised at the weighted mean of the finite
+  targets with the weighted variance over eps^2 as its value;
 - the parameter count equals the library's."""
 import ctypes
 import math
@@ -55,6 +61,50 @@ def test_loss_is_zero_at_the_prediction():
     al, be = M.predict(w, d, x, a, y, b, cm)
     L, g = M.loss_grad(w, d, x, a, y, b, cm, al, be, 0.1)
     assert L == 0.0 and not g.any()
+
+
+def test_predictions_invariant_to_scale_and_splitting():
+    d = 3
+    x, a, y, b, cm, _, _ = _tiny(6, d=d, n=11, m=8)
+    w = np.random.default_rng(7).normal(0, 0.3, M.count(d))
+    al, be = M.predict(w, d, x, a, y, b, cm)
+    c = 3.7
+    al2, be2 = M.predict(w, d, c * x, a, c * y, b, c * c * cm)
+    assert np.allclose(al2, al, rtol=1e-12, atol=1e-13) and np.allclose(be2, be, rtol=1e-12, atol=1e-13)
+    # every target point split in two halves: the source side's predictions stay
+    al3, be3 = M.predict(w, d, x, a, np.repeat(y, 2, 0), np.repeat(b / 2, 2), cm)
+    assert np.allclose(al3, al, rtol=1e-12, atol=1e-13)
+    assert np.allclose(be3, np.repeat(be, 2), rtol=1e-12, atol=1e-13)
+    # and every source point split: each copy predicts what the original did
+    al4, be4 = M.predict(w, d, np.repeat(x, 2, 0), np.repeat(a / 2, 2), y, b, cm)
+    assert np.allclose(al4, np.repeat(al, 2), rtol=1e-12, atol=1e-13)
+    assert np.allclose(be4, be, rtol=1e-12, atol=1e-13)
+    # the predictions do depend on the masses (the features are not constant)
+    al5, _ = M.predict(w, d, x, np.roll(a, 1), y, b, cm)
+    assert np.abs(al5 - al).max() > 1e-6
+
+
+def test_constant_network_loss_is_weighted_variance():
+    d = 2
+    x, a, y, b, cm, ta, tb = _tiny(8, d=d)
+    eps = 0.07
+    o = M.layout(d)
+    n1, k3 = o["size"], o["b3"][0]
+    fa, fb = np.isfinite(ta), np.isfinite(tb)
+    ma, mb = np.average(ta[fa], weights=a[fa]), np.average(tb[fb], weights=b[fb])
+    va = np.cov(ta[fa], aweights=a[fa], bias=True)
+    vb = np.cov(tb[fb], aweights=b[fb], bias=True)
+
+    def loss(c_alpha):
+        w = np.zeros(M.count(d))          # every layer zero: both outputs are their bias b3
+        w[k3], w[n1 + k3] = c_alpha, mb
+        return M.loss_grad(w, d, x, a, y, b, cm, ta, tb, eps)[0]
+
+    assert loss(ma) == pytest.approx((va + vb) / eps ** 2, rel=1e-12)
+    for h in (0.01, 0.1):
+        # symmetric about the weighted mean, and above the minimum by h^2 / eps^2
+        assert loss(ma - h) == pytest.approx(loss(ma + h), rel=1e-12)
+        assert loss(ma + h) - loss(ma) == pytest.approx(h * h / eps ** 2, rel=1e-9)
 
 
 def test_gauge_fix():

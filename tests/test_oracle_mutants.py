@@ -57,6 +57,12 @@ CASES = [
      "test_oracle_sinkhorn.py"),
     ("log-sum-exp without its shift back", "sparsink_oracle.c", "  return mx + log(acc);", "  return log(acc);",
      "test_oracle_sinkhorn.py"),
+    ("network: points scaled by 1 / cost_max", "mlp_oracle.py", "s = 1.0 / np.sqrt(cost_max)",
+     "s = 1.0 / cost_max", "test_oracle_mlp.py"),
+    ("network: mass feature a_i without n", "mlp_oracle.py", "(len(sw) * np.asarray(sw, np.float64))[:, None]",
+     "(np.asarray(sw, np.float64))[:, None]", "test_oracle_mlp.py"),
+    ("network: loss not weighted by a", "mlp_oracle.py", "a = np.where(fin, np.asarray(sw, np.float64), 0.0)",
+     "a = np.where(fin, 1.0, 0.0)", "test_oracle_mlp.py"),
     ("IBP: arithmetic instead of geometric mean", "ibp_oracle.py",
      "logq += w[k] * np.log(np.where(Kv[k] > 0, Kv[k], 1.0))",
      "logq += w[k] * np.where(Kv[k] > 0, Kv[k], 1.0)", "test_oracle_ibp.py"),
