@@ -32,6 +32,11 @@ CASES = [
      "const double phi = isinf(lambda) ? 1.0 : lambda / (2.0 * lambda + eps);", "test_oracle_sinkhorn.py"),
     ("entropy without the -1", "sparsink_oracle.c", "ne += T * (lt - 1.0);", "ne += T * lt;",
      "test_oracle_sinkhorn.py"),
+    ("transport term <T, sqrt C>", "sparsink_oracle.c", "tr += T * cost[k];", "tr += T * sqrt(cost[k]);",
+     "test_oracle_gaussian.py"),
+    ("FP64 cost over the first coordinate only", "sparsink_oracle.c",
+     "for (int k = 0; k < P->d; ++k) {\n    double t = P->x", "for (int k = 0; k < 1; ++k) {\n    double t = P->x",
+     "test_oracle_gaussian.py"),
     ("KL term sign", "sparsink_oracle.c", "return x * log(x / y) - x + y;", "return x * log(x / y) + x - y;",
      "test_oracle_sinkhorn.py"),
     ("skip sampler: gap rate log q instead of log(1 - q)", "sparsink_oracle.c",
