@@ -46,7 +46,8 @@ class Problem(C.Structure):
                 ("x", C.c_void_p), ("y", C.c_void_p), ("C", C.c_void_p),
                 ("cost_norm", C.c_int32), ("cost_scale", C.c_double), ("a", C.c_void_p), ("b", C.c_void_p),
                 ("eps", C.c_double), ("lam", C.c_double), ("s", C.c_double),
-                ("seed", C.c_uint64), ("pid", C.c_uint32), ("cost_kind", C.c_int32), ("eta", C.c_double)]
+                ("seed", C.c_uint64), ("pid", C.c_uint32), ("cost_kind", C.c_int32), ("eta", C.c_double),
+                ("probs", C.c_int32)]
 
 
 class Scalars(C.Structure):
@@ -201,9 +202,11 @@ class OracleProblem:
     """Holds the numpy arrays of one problem alive for the C struct."""
 
     def __init__(self, a, b, eps, s, lam=math.inf, x=None, y=None, C_=None, cost_norm=1,
-                 seed=0x5EED, pid=0, cost_scale=1.0, cost_kind="sqeuclid", eta=0.0):
+                 seed=0x5EED, pid=0, cost_scale=1.0, cost_kind="sqeuclid", eta=0.0, probs="paper"):
         """cost_kind: "sqeuclid" (squared Euclidean, or the matrix C_) or "wfr"
-        (Wasserstein-Fisher-Rao with parameter eta; raw cost, cost_norm = 0)."""
+        (Wasserstein-Fisher-Rao with parameter eta; raw cost, cost_norm = 0).
+        probs: "paper" (Eq. (pij-ot) / (pij-uot)) or "uniform" (p_ij = 1/(n m), the
+        Rand-Sink control)."""
         self.a = _c(a, np.float64)
         self.b = _c(b, np.float64)
         self.x = _c(x, np.float64)
@@ -216,9 +219,10 @@ class OracleProblem:
         self.cost_scale = float(cost_scale)
         self.seed, self.pid = int(seed), int(pid)
         self.cost_kind, self.eta = (1 if cost_kind == "wfr" else 0), float(eta)
+        self.probs = {"paper": 0, "uniform": 1}[probs]
         self.struct = Problem(self.n, self.m, self.d, _ptr(self.x), _ptr(self.y), _ptr(self.C),
                               self.cost_norm, self.cost_scale, _ptr(self.a), _ptr(self.b), self.eps,
-                              self.lam, self.s, self.seed, self.pid, self.cost_kind, self.eta)
+                              self.lam, self.s, self.seed, self.pid, self.cost_kind, self.eta, self.probs)
         self._factors = None
 
     @property
@@ -411,7 +415,7 @@ def spar_sink(prob: OracleProblem, tol=1e-6, max_iter=1000, log_domain=False, st
     else:
         u, v, info = sinkhorn_sparse(sk, a, b, prob.eps, prob.lam, tol, max_iter, stop_rule)
         logu, logv = _log_or_neginf(u), _log_or_neginf(v)
-        logT = logu[rows] + np.log(sk["val"]) + logv[sk["col_idx"]]
+        logT = logu[rows] + _log_or_neginf(sk["val"]) + logv[sk["col_idx"]]   # K~ = 0 where WFR blocks
     terms = objective_terms(sk["row_ptr"], sk["col_idx"], logT, sk["cost"], sk["pstar"], a, b)
     r1, r2 = _objective(terms, prob.eps, prob.lam)
     return {"sketch": sk, "alpha": prob.eps * logu, "beta": prob.eps * logv, "info": info,

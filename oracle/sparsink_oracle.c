@@ -282,6 +282,10 @@ static double raw_cost64(const orc_problem* P, int32_t i, int32_t j) {
 
 static int is_ot(const orc_problem* P) { return isinf(P->lambda) && P->lambda > 0; }
 
+/* Probabilities that factor as p*_ij = min(1, r_i c_j): Eq. (pij-ot), or the
+ * equal probabilities of the Rand-Sink control. */
+static int separable(const orc_problem* P) { return is_ot(P) || P->probs == 1; }
+
 /* Divisor of the raw cost: C = D / divisor.  With cost_norm = 1 it is the
  * maximum of the binary32 raw costs over all pairs (a maximum is exact, so
  * every implementation of the spec finds the same number); with cost_norm = 2
@@ -332,7 +336,7 @@ static float uot_weight(const orc_problem* P, const float* rowf, const float* co
 
 float orc_pstar_raw(const orc_problem* P, const float* rowf, const float* colf,
                     const orc_scalars* S, int32_t i, int32_t j) {
-  if (is_ot(P)) return rowf[i] * colf[j];
+  if (separable(P)) return rowf[i] * colf[j];
   return S->scale32 * uot_weight(P, rowf, colf, S, i, j);
 }
 
@@ -343,6 +347,7 @@ static int check_problem(const orc_problem* P) {
   if (P->cost_norm == 2 && !(P->cost_scale > 0.0)) return -1;
   if (P->cost_kind != 0 && P->cost_kind != 1) return -1;
   if (is_wfr(P) && (P->C || P->cost_norm != 0 || !(P->eta > 0.0))) return -1;
+  if (P->probs != 0 && P->probs != 1) return -1;
   if (!P->a || !P->b) return -1;
   for (int32_t i = 0; i < P->n; ++i) if (!(P->a[i] >= 0.0) || isinf(P->a[i])) return -1;
   for (int32_t j = 0; j < P->m; ++j) if (!(P->b[j] >= 0.0) || isinf(P->b[j])) return -1;
@@ -369,6 +374,13 @@ int orc_factors(const orc_problem* P, float* rowf, float* colf, orc_scalars* S) 
   S->dmax32 = dmax32;
   S->dmax64 = dmax64;
   S->s32 = (float)P->s;
+  if (P->probs == 1) {
+    /* Rand-Sink: p_ij = 1/(n m) for every element; p*_ij = min(1, s p_ij) */
+    S->scale32 = (float)(1.0 / ((double)n * (double)m));
+    for (int32_t i = 0; i < n; ++i) rowf[i] = S->s32 * S->scale32;
+    for (int32_t j = 0; j < m; ++j) colf[j] = 1.0f;
+    return 0;
+  }
   if (is_ot(P)) {
     /* Eq. (pij-ot): p_ij = sqrt(a_i) sqrt(b_j) / (sum sqrt(a) sum sqrt(b)) */
     float* sa = (float*)malloc(sizeof(float) * (size_t)n);
@@ -528,7 +540,7 @@ int32_t orc_skip_row(const orc_problem* P, const float* rowf, const float* colf,
                      float cmax, int32_t i, int32_t* cols, double* val, double* logval, float* pstar,
                      double* cost) {
   const float r = rowf[i];
-  const float q = is_ot(P) ? r * cmax : S->scale32 * (r * cmax);
+  const float q = separable(P) ? r * cmax : S->scale32 * (r * cmax);
   if (!(q > 0.0f)) return 0;
   const int full = q >= 1.0f;
   const float L = full ? 0.0f : orc_log1m32(q);

@@ -89,6 +89,8 @@ typedef struct {
                            C_ij = -log cos_+^2(d_ij / (2 eta)), d_ij the Euclidean distance of
                            the points (section 2.2); needs points and cost_norm = 0 */
   double eta;           /* WFR: eta > 0 (transport blocked where d_ij >= pi eta) */
+  int32_t probs;        /* 0: Eq. (pij-ot) / Eq. (pij-uot); 1: equal probabilities p_ij = 1/(n m)
+                           for every element (the Rand-Sink control of section 5), any lambda */
 } orc_problem;
 
 /* Scalars shared by every element's decision and value. */
@@ -106,7 +108,8 @@ typedef struct {
 } orc_scalars;
 
 /* Row and column factors of the decision.  OT: r[i], c[j] with
- * p*_ij = min(1, r_i c_j).  UOT: A[i], B[j] with w_ij = A_i B_j E(-D_ij kappa)
+ * p*_ij = min(1, r_i c_j).  Equal probabilities (probs = 1, OT or UOT):
+ * r_i = fl(fl(s) fl(1/(n m))), c_j = 1, with the same rule.  UOT: A[i], B[j] with w_ij = A_i B_j E(-D_ij kappa)
  * and p*_ij = min(1, scale32 w_ij).  Returns 0 on success, <0 on bad input. */
 int orc_factors(const orc_problem* P, float* rowf, float* colf, orc_scalars* S);
 

@@ -52,6 +52,9 @@ CASES = [
     ("WFR: decision angle d / eta", "sparsink_oracle.c",
      "S->inv2eta32 = is_wfr(P) ? (float)(1.0 / (2.0 * P->eta)) : 0.0f;",
      "S->inv2eta32 = is_wfr(P) ? (float)(1.0 / P->eta) : 0.0f;", "test_oracle_wfr.py"),
+    ("equal probabilities without the budget s", "sparsink_oracle.c",
+     "for (int32_t i = 0; i < n; ++i) rowf[i] = S->s32 * S->scale32;",
+     "for (int32_t i = 0; i < n; ++i) rowf[i] = S->scale32;", "test_oracle_randsink.py"),
     ("Philox: nine rounds", "sparsink_oracle.c", "for (int r = 0; r < 10; ++r) {",
      "for (int r = 0; r < 9; ++r) {", "test_oracle_rng.py"),
     ("exact sum: ties not to even", "sparsink_oracle.c", "if (round_bit && (sticky || (mant & 1u))) {",
