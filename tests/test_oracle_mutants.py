@@ -63,6 +63,14 @@ CASES = [
      "for (int p = hb - 55; p >= 0 && !sticky; --p)", "test_oracle_specmath.py"),
     ("KL(0 | y) taken as 0", "sparsink_oracle.c", "if (x == 0.0) return y;", "if (x == 0.0) return 0.0;",
      "test_oracle_sinkhorn.py"),
+    ("UOT stopping residual without the power 1/phi", "sparsink_oracle.c",
+     "double ui = (phi == 1.0) ? u[i] : pow(u[i], 1.0 / phi);", "double ui = u[i];", "test_oracle_sinkhorn.py"),
+    ("log-domain UOT stopping residual without 1/phi", "sparsink_oracle.c#1",
+     "res += fabs(exp(alpha[i] * ie / phi + L[i]) - a[i]);", "res += fabs(exp(alpha[i] * ie + L[i]) - a[i]);",
+     "test_oracle_sinkhorn.py"),
+    ("log-domain residual of a capped run without 1/phi", "sparsink_oracle.c#2",
+     "res += fabs(exp(alpha[i] * ie / phi + L[i]) - a[i]);", "res += fabs(exp(alpha[i] * ie + L[i]) - a[i]);",
+     "test_oracle_sinkhorn.py"),
     ("log-sum-exp without its shift back", "sparsink_oracle.c", "  return mx + log(acc);", "  return log(acc);",
      "test_oracle_sinkhorn.py"),
     ("network: points scaled by 1 / cost_max", "mlp_oracle.py", "s = 1.0 / np.sqrt(cost_max)",

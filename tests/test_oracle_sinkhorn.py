@@ -291,3 +291,54 @@ def test_dense_log_domain_small_eps_lp_sandwich(orc):
     assert abs(r["terms"]["transport"] - ot) < 5e-3
     T = np.exp((r["alpha"][:, None] + r["beta"][None]) / eps - C / eps)
     assert np.abs(T.sum(1) - a).sum() < 1e-11 and np.abs(T.sum(0) - b).sum() < 1e-11
+
+
+def _sketch_rows(sk):
+    return np.repeat(np.arange(sk["n"]), np.diff(sk["row_ptr"]))
+
+
+@pytest.mark.parametrize("lam", [1.0, 0.3])
+def test_uot_stopping_residual(orc, lam):
+    # Reading c-1: UOT marginals are penalised, not constrained, so the stopping
+    # residual is the fixed-point one of Alg. 2: u = (a / Kv)^phi holds exactly
+    # when u^{1/phi} (Kv) = a, with phi = lam / (lam + eps).  It is checked here
+    # from the returned pair, recomputed with numpy, not with the oracle's code.
+    rng = np.random.default_rng(11)
+    eps = 0.1
+    phi = lam / (lam + eps)
+    C = rng.uniform(0, 1, (18, 13))
+    a = rng.dirichlet(np.ones(18)); b = 1.5 * rng.dirichlet(np.ones(13))
+    K = np.exp(-C / eps)
+    u, v, info = orc.sinkhorn_dense(K, a, b, eps, lam=lam, tol=1e-9, max_iter=100000)
+    assert info["status"] == 0
+    res = np.abs(u ** (1 / phi) * (K @ v) - a).sum()
+    assert res <= 1e-9 and abs(res - info["residual"]) <= 1e-15
+    # the column side holds right after the v-update of the same iteration
+    assert np.abs(v ** (1 / phi) * (K.T @ u) - b).sum() < 1e-13
+    # the plain-OT residual of the same pair is far from zero: the marginals are not matched
+    assert np.abs(u * (K @ v) - a).sum() > 1e-3
+    # the first pair under tol is returned: the one before it is not
+    _, _, info2 = orc.sinkhorn_dense(K, a, b, eps, lam=lam, tol=1e-9, max_iter=info["iters"] - 1)
+    assert info2["status"] == 1 and info2["residual"] > 1e-9
+
+    # log-domain form on a sketch: the residual of (alpha, beta) with u = e^{alpha/eps}
+    w = inputs.small_problem(n=40, m=30, d=3, seed=12)
+    P = orc.OracleProblem(w.a, 1.5 * w.b, eps, 400.0, lam, x=w.x, y=w.y, seed=5)
+    sk = P.sparsify()
+    rows = _sketch_rows(sk)
+
+    def log_residual(al, be):
+        q = np.zeros(sk["n"])
+        np.add.at(q, rows, np.exp(sk["logval"] + be[sk["col_idx"]] / eps))
+        ok = q > 0
+        return np.abs(np.exp(al[ok] / (eps * phi)) * q[ok] - P.a[ok]).sum()
+
+    al, be, li = orc.sinkhorn_log_sparse(sk, P.a, P.b, eps, lam=lam, tol=1e-9, max_iter=100000)
+    assert li["status"] == 0
+    r = log_residual(al, be)
+    assert r <= 1e-9 and abs(r - li["residual"]) <= 1e-12
+    # a capped, unconverged run reports the same residual of its returned pair
+    al3, be3, li3 = orc.sinkhorn_log_sparse(sk, P.a, P.b, eps, lam=lam, tol=1e-9, max_iter=3)
+    assert li3["status"] == 1
+    r3 = log_residual(al3, be3)
+    assert r3 > 1e-6 and abs(r3 - li3["residual"]) <= 1e-12 * r3
