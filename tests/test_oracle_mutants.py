@@ -55,6 +55,24 @@ CASES = [
     ("equal probabilities without the budget s", "sparsink_oracle.c",
      "for (int32_t i = 0; i < n; ++i) rowf[i] = S->s32 * S->scale32;",
      "for (int32_t i = 0; i < n; ++i) rowf[i] = S->scale32;", "test_oracle_randsink.py"),
+    ("cost divisor: maximum over half of the columns", "sparsink_oracle.c",
+     "for (int32_t j = 0; j < m; ++j) {\n      float d32 = raw_cost32(P, i, j);",
+     "for (int32_t j = 0; j < m / 2; ++j) {\n      float d32 = raw_cost32(P, i, j);", "test_oracle_sampler.py"),
+    ("decision draw: counter words i and j >> 2 swapped", "sparsink_oracle.c",
+     "uint32_t ctr[4] = {j >> 2, i, pid, 0x5A17u};", "uint32_t ctr[4] = {i, j >> 2, pid, 0x5A17u};",
+     "test_oracle_rng.py"),
+    ("decision draw: word 0 of the block for every column", "sparsink_oracle.c",
+     "return out[j & 3u] >> 8;", "return out[0] >> 8;", "test_oracle_rng.py"),
+    ("UOT decision factor exp(+D kappa)", "sparsink_oracle.c",
+     "if (!is_wfr(P)) return orc_exp32(-(dd * S->kappa32));", "if (!is_wfr(P)) return orc_exp32(dd * S->kappa32);",
+     "test_oracle_sampler.py"),
+    ("UOT normaliser Z without the kernel factor", "sparsink_oracle.c",
+     "sa_add(&part, uot_weight(P, rowf, colf, S, i, j));", "sa_add(&part, rowf[i] * colf[j]);",
+     "test_oracle_sampler.py"),
+    ("sparse-problem value with -eps sum T log p*", "oracle.py",
+     'return r1, r1 + eps * terms["logp"]', 'return r1, r1 - eps * terms["logp"]', "test_oracle_sparsink.py"),
+    ("UOT objective with the KL term of a only", "oracle.py",
+     'r1 += lam * (terms["kl_a"] + terms["kl_b"])', 'r1 += lam * terms["kl_a"]', "test_oracle_sinkhorn.py"),
     ("Philox: nine rounds", "sparsink_oracle.c", "for (int r = 0; r < 10; ++r) {",
      "for (int r = 0; r < 9; ++r) {", "test_oracle_rng.py"),
     ("exact sum: ties not to even", "sparsink_oracle.c", "if (round_bit && (sticky || (mant & 1u))) {",
