@@ -33,7 +33,7 @@ def _rank_main(rank, world, port, out):
 
 def test_max_over_two_gloo_ranks():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of this (multi-threaded) process
     out = mgr.dict()
     mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world, start_method="spawn")
     assert dict(out) == {0: 13.0, 1: 13.0}
