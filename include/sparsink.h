@@ -65,11 +65,11 @@ typedef enum { SPS_F64 = 0, SPS_F32 = 1, SPS_BF16 = 2, SPS_F16 = 3 } sps_dtype;
  * given raw cost matrix. */
 typedef struct {
   int32_t n, m, d;
-  const void* x;      /* device, n*d, dtype; NULL when C is given */
-  const void* y;      /* device, m*d, dtype; NULL when C is given */
+  const void* x;      /* device, n*d, dtype; may be NULL when C is given (then ignored) */
+  const void* y;      /* device, m*d, dtype; may be NULL when C is given (then ignored) */
   const void* C;      /* device, n*m raw cost, dtype; NULL = squared Euclidean */
   int32_t cost_norm;  /* SPS_COST_* */
-  double cost_scale;  /* divisor for SPS_COST_SCALE */
+  double cost_scale;  /* divisor for SPS_COST_SCALE (finite, > 0) */
   const void* a;      /* device, n, dtype, a_i >= 0 */
   const void* b;      /* device, m, dtype, b_j >= 0 */
   sps_dtype dtype;    /* SPS_F32 or SPS_F64: type of x, y, C, a, b */
@@ -82,14 +82,16 @@ typedef struct {
   double s;            /* sample budget: E nnz(K~) <= s (Eq. pois), > 0 */
   double tol;          /* stopping tolerance */
   int32_t max_iter;    /* iteration cap (>= 1) */
-  int32_t check_every; /* iterations enqueued between convergence read-backs (0 = auto) */
+  int32_t check_every; /* iterations enqueued between convergence read-backs (0 = auto;
+                          negative: SPS_ERR_INVALID_ARG) */
   int32_t stop_rule;   /* SPS_STOP_* */
   uint64_t seed;       /* Philox key of the sampling stream */
   uint32_t problem_id; /* third Philox counter word (distinct streams per problem) */
   sps_dtype kdtype;    /* storage of K~ values: F64, F32, BF16 or F16.  F64 iterates in
                           FP64; the others iterate in FP32 */
   int32_t log_domain;  /* 1: stabilised (absorbing) iterations for small eps */
-  double absorb_tau;   /* absorb when max |log u~| or |log v~| exceeds this (0 = default 12) */
+  double absorb_tau;   /* absorb when max |log u~| or |log v~| exceeds this (0 = default 12;
+                          with log_domain, NaN, infinite or negative: SPS_ERR_INVALID_ARG) */
   const void* init_alpha; /* optional device warm start (n), iterate type, or NULL */
   const void* init_beta;  /* optional device warm start (m), iterate type, or NULL */
   int32_t gather_mode; /* stabilised iterations only: how the sparse products read the
@@ -260,7 +262,7 @@ typedef struct {
   const int32_t* dst;      /* HOST, n_pairs target set indices */
   const double* s;         /* HOST, n_pairs sample budgets (> 0) */
   int32_t cost_norm;       /* SPS_COST_RAW, SPS_COST_MAXNORM (max over the pair) or SPS_COST_SCALE */
-  double cost_scale;       /* divisor for SPS_COST_SCALE */
+  double cost_scale;       /* divisor for SPS_COST_SCALE (finite, > 0) */
   sps_dtype dtype;         /* F32 or F64 points and weights */
 } sps_batch;
 

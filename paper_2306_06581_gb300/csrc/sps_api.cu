@@ -215,7 +215,10 @@ static sps_status validate(const sps_problem* P, const sps_params* Q, int op) {
   if (Q->log_domain && op == SPS_OP_DENSE && Q->kdtype != SPS_F32) { set_error("dense log_domain iterates in F32"); return SPS_ERR_INVALID_ARG; }
   if (Q->log_domain && Q->kdtype == SPS_F64) { set_error("log_domain stores K' in F32, BF16 or F16"); return SPS_ERR_INVALID_ARG; }
   if (Q->log_domain && Q->stop_rule != SPS_STOP_RESIDUAL) { set_error("log_domain stops on the residual rule"); return SPS_ERR_INVALID_ARG; }
-  if (Q->log_domain && Q->absorb_tau < 0.0) { set_error("absorb_tau must be >= 0"); return SPS_ERR_INVALID_ARG; }
+  if (Q->log_domain && !(Q->absorb_tau >= 0.0 && isfinite(Q->absorb_tau))) {
+    set_error("absorb_tau must be finite and >= 0 (0 = default)"); return SPS_ERR_INVALID_ARG;
+  }
+  if (Q->check_every < 0) { set_error("check_every must be >= 0 (0 = automatic)"); return SPS_ERR_INVALID_ARG; }
   if (Q->gather_mode < SPS_GATHER_AUTO || Q->gather_mode > SPS_GATHER_STAGED) { set_error("unknown gather_mode %d", Q->gather_mode); return SPS_ERR_INVALID_ARG; }
   if (Q->sketch_mode != SPS_SKETCH_SINGLE && Q->sketch_mode != SPS_SKETCH_TWO_PASS) { set_error("unknown sketch_mode %d", Q->sketch_mode); return SPS_ERR_INVALID_ARG; }
   if (Q->sampler != SPS_SAMPLER_ELEMENT && Q->sampler != SPS_SAMPLER_SKIP) { set_error("unknown sampler %d", Q->sampler); return SPS_ERR_INVALID_ARG; }

@@ -799,7 +799,9 @@ sps_status validate_batch(const sps_batch* Bt, const sps_params* Q) {
   if (!Bt->set_off || !Bt->pts || !Bt->mass || !Bt->src || !Bt->dst || !Bt->s) { set_error("null batch array"); return SPS_ERR_INVALID_ARG; }
   if (Bt->dtype != SPS_F32 && Bt->dtype != SPS_F64) { set_error("batch inputs are F32 or F64"); return SPS_ERR_INVALID_ARG; }
   if (Bt->cost_norm < SPS_COST_RAW || Bt->cost_norm > SPS_COST_SCALE) { set_error("unknown cost_norm"); return SPS_ERR_INVALID_ARG; }
-  if (Bt->cost_norm == SPS_COST_SCALE && !(Bt->cost_scale > 0.0)) { set_error("cost_scale must be > 0"); return SPS_ERR_INVALID_ARG; }
+  if (Bt->cost_norm == SPS_COST_SCALE && !(Bt->cost_scale > 0.0 && isfinite(Bt->cost_scale))) {
+    set_error("cost_scale must be finite and > 0"); return SPS_ERR_INVALID_ARG;
+  }
   if (Bt->set_off[0] != 0) { set_error("set_off[0] must be 0"); return SPS_ERR_INVALID_ARG; }
   for (int k = 0; k < Bt->n_sets; ++k)
     if (Bt->set_off[k + 1] <= Bt->set_off[k]) { set_error("set %d is empty or offsets decrease", k); return SPS_ERR_INVALID_ARG; }
@@ -820,7 +822,9 @@ sps_status validate_batch(const sps_batch* Bt, const sps_params* Q) {
   if (!(Q->tol >= 0.0)) { set_error("tol must be >= 0"); return SPS_ERR_INVALID_ARG; }
   if (Q->kdtype != SPS_F32 && Q->kdtype != SPS_BF16 && Q->kdtype != SPS_F16) { set_error("batched K' is stored in F32, BF16 or F16"); return SPS_ERR_INVALID_ARG; }
   if (Q->stop_rule != SPS_STOP_RESIDUAL) { set_error("the batched solver stops on the residual rule"); return SPS_ERR_INVALID_ARG; }
-  if (Q->absorb_tau < 0.0) { set_error("absorb_tau must be >= 0"); return SPS_ERR_INVALID_ARG; }
+  if (!(Q->absorb_tau >= 0.0 && isfinite(Q->absorb_tau))) {
+    set_error("absorb_tau must be finite and >= 0 (0 = default)"); return SPS_ERR_INVALID_ARG;
+  }
   Plan L;
   if (!plan(Bt, Q, &L, nullptr)) { set_error("the batch's total sample capacity exceeds 2^31 elements"); return SPS_ERR_CAPACITY; }
   return SPS_OK;

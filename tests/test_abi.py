@@ -110,3 +110,73 @@ def test_binding_fails_loudly_without_library(S, tmp_path, monkeypatch):
     monkeypatch.setattr(S, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         S.lib()
+
+
+def test_iteration_controls_validated(S):
+    P = _prob(S)
+    Q = S.make_params(0.1, math.inf, 1000.0, check_every=-3)
+    assert S.sps_workspace_bytes(P, Q, 1) == 0
+    assert "check_every" in S.last_error()
+    assert S.sps_workspace_bytes(P, S.make_params(0.1, math.inf, 1000.0, check_every=0), 1) > 0
+    for tau in (float("nan"), math.inf, -1.0):
+        Q = S.make_params(0.01, math.inf, 1000.0, kdtype="f32", log_domain=1, absorb_tau=tau)
+        assert S.sps_workspace_bytes(P, Q, 1) == 0, tau
+        assert "absorb_tau" in S.last_error()
+    assert S.sps_workspace_bytes(P, S.make_params(0.01, math.inf, 1000.0, kdtype="f32", log_domain=1,
+                                                  absorb_tau=20.0), 1) > 0
+
+
+def _batch(S, sets=(100, 120, 80), pairs=((0, 1), (1, 2), (2, 0)), s=None, d=2, cost_norm=1, cost_scale=1.0,
+           dtype=1):
+    import numpy as np
+    off = np.concatenate([[0], np.cumsum(sets)]).astype(np.int64)
+    src = np.array([p[0] for p in pairs], np.int32)
+    dst = np.array([p[1] for p in pairs], np.int32)
+    sb = np.array(s if s is not None else [1000.0] * len(pairs), np.float64)
+    B = S.Batch(len(sets), d, off.ctypes.data, 256, 256, len(pairs), src.ctypes.data, dst.ctypes.data,
+                sb.ctypes.data, cost_norm, cost_scale, dtype)
+    return B, (off, src, dst, sb)
+
+
+def _batch_bytes(S, B, Q):
+    f = S.lib().sps_batch_workspace_bytes
+    f.argtypes = [C.c_void_p, C.c_void_p]
+    f.restype = C.c_size_t
+    return int(f(C.byref(B), C.byref(Q)))
+
+
+def test_batch_arguments_validated(S):
+    # spar_sink_batched's host-side checks, through its workspace-size call (no GPU needed)
+    Q = S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f32")
+    B, keep = _batch(S)
+    ok = _batch_bytes(S, B, Q)
+    assert ok > 0
+    # the workspace grows with the budgets
+    B2, keep2 = _batch(S, s=[4000.0] * 3)
+    assert _batch_bytes(S, B2, Q) > ok
+    bad = [
+        (dict(d=0), "d"), (dict(d=17), "d"),
+        (dict(sets=(100, 0, 80)), "empty"),
+        (dict(pairs=((0, 1), (1, 3))), "out of range"), (dict(pairs=((0, 1), (-1, 2))), "out of range"),
+        (dict(s=[1000.0, 0.0, 1000.0]), "budget"), (dict(s=[1000.0, float("nan"), 1000.0]), "budget"),
+        (dict(sets=(20000, 10000), pairs=((0, 1),)), "shared memory"),   # 2 n + m = 50000 > 49152
+        (dict(cost_norm=2, cost_scale=math.inf), "cost_scale"), (dict(cost_norm=2, cost_scale=0.0), "cost_scale"),
+        (dict(cost_norm=5), "cost_norm"), (dict(dtype=2), "F32 or F64"),
+    ]
+    for kw, frag in bad:
+        Bb, kb = _batch(S, **kw)
+        assert _batch_bytes(S, Bb, Q) == 0, kw
+        assert frag in S.last_error(), (kw, S.last_error())
+    # 2 n + m at the limit is accepted
+    Bl, kl = _batch(S, sets=(16384, 16384), pairs=((0, 1),))
+    assert _batch_bytes(S, Bl, Q) > 0
+    # parameters the batched solver does not take
+    for Qb, frag in [(S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f64"), "F32, BF16 or F16"),
+                     (S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f32", sampler="skip"), "sampler"),
+                     (S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f32", stop_rule=1), "residual"),
+                     (S.make_params(0.01, 1.0, 1.0, 1e-5, 0, kdtype="f32"), "max_iter"),
+                     (S.make_params(0.0, 1.0, 1.0, 1e-5, 100, kdtype="f32"), "eps"),
+                     (S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f32", absorb_tau=math.inf), "absorb_tau"),
+                     (S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f32", absorb_tau=float("nan")), "absorb_tau")]:
+        assert _batch_bytes(S, B, Qb) == 0, frag
+        assert frag in S.last_error(), (frag, S.last_error())
