@@ -325,7 +325,7 @@ typedef struct {
   const float* a; const float* b;   /* DEVICE weights */
   int32_t n, m, d;                  /* 1 <= d <= 16 */
   double cost_max;                  /* the cost divisor (sps_cost_max) */
-  double eps;                       /* training loss scale: errors are measured in units of eps */
+  double eps;                       /* training loss scale (finite, > 0): errors are measured in units of eps */
 } sps_mlp_instance;
 
 size_t sps_mlp_param_count(int32_t d);
@@ -350,7 +350,8 @@ sps_status sps_mlp_gauge_fix(const sps_mlp_instance* inst, float* alpha, float* 
 sps_status sps_mlp_grad(const float* params, const void* params_bf16, const sps_mlp_instance* inst,
                         const float* alpha_target, const float* beta_target, float* grad, float* loss_out,
                         void* ws, sps_stream stream);
-/* One Adam step (bias-corrected, step >= 1) on the FP32 master weights; refreshes the BF16 copy. */
+/* One Adam step (bias-corrected, step >= 1) on the FP32 master weights; refreshes the BF16 copy.
+ * lr must be finite and >= 0, beta1 and beta2 in [0, 1), eps finite and > 0 (else SPS_ERR_INVALID_ARG). */
 sps_status sps_mlp_adam(float* params, void* params_bf16, float* m1, float* m2, const float* grad, int32_t d,
                         int32_t step, float lr, float beta1, float beta2, float eps, sps_stream stream);
 

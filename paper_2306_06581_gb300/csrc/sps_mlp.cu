@@ -580,7 +580,7 @@ sps_status sps_mlp_grad(const float* params, const void* params_bf16, const sps_
                         void* ws, sps_stream stream) {
   SPS_TRY(check_inputs(I));
   if (!params || !params_bf16 || !alpha_target || !beta_target || !grad || !ws) { set_error("null argument"); return SPS_ERR_INVALID_ARG; }
-  if (!(I->eps > 0.0)) { set_error("eps must be > 0"); return SPS_ERR_INVALID_ARG; }
+  if (!(I->eps > 0.0) || !isfinite(I->eps)) { set_error("eps must be finite and > 0"); return SPS_ERR_INVALID_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   const Off o = offsets(I->d);
   const __nv_bfloat16* wb = (const __nv_bfloat16*)params_bf16;
@@ -611,6 +611,12 @@ sps_status sps_mlp_grad(const float* params, const void* params_bf16, const sps_
 sps_status sps_mlp_adam(float* params, void* params_bf16, float* m1, float* m2, const float* grad, int32_t d,
                         int32_t step, float lr, float beta1, float beta2, float eps, sps_stream stream) {
   if (!params || !params_bf16 || !m1 || !m2 || !grad || d < 1 || d > 16 || step < 1) { set_error("bad Adam arguments"); return SPS_ERR_INVALID_ARG; }
+  // the bias corrections 1 - beta^step must be positive and the denominator sqrt(v) + eps non-zero
+  if (!(lr >= 0.0f) || !isfinite(lr) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+      !(eps > 0.0f) || !isfinite(eps)) {
+    set_error("Adam needs a finite lr >= 0, 0 <= beta1, beta2 < 1 and a finite eps > 0");
+    return SPS_ERR_INVALID_ARG;
+  }
   const int count = 2 * offsets(d).size;
   const float c1 = (float)(1.0 - pow((double)beta1, step)), c2 = (float)(1.0 - pow((double)beta2, step));
   k_adam<<<grid_pts(count), 256, 0, (cudaStream_t)stream>>>(params, (__nv_bfloat16*)params_bf16, m1, m2, grad, count,

@@ -180,3 +180,32 @@ def test_batch_arguments_validated(S):
                      (S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f32", absorb_tau=float("nan")), "absorb_tau")]:
         assert _batch_bytes(S, B, Qb) == 0, frag
         assert frag in S.last_error(), (frag, S.last_error())
+
+
+def test_warm_start_arguments_validated(S):
+    # the warm-start calls refuse bad arguments before any launch (fake device pointers are never touched)
+    L = S._mlp_lib()
+    f = C.c_void_p(256)
+    assert S.mlp_param_count(0) == 0 and S.mlp_param_count(17) == 0 and S.mlp_param_count(3) > 0
+    good = dict(lr=1e-3, b1=0.9, b2=0.999, eps=1e-8)
+    for k, v in [("lr", float("nan")), ("lr", -1e-3), ("lr", math.inf), ("b1", 1.0), ("b1", -0.1),
+                 ("b2", 1.0), ("b2", float("nan")), ("eps", 0.0), ("eps", math.inf)]:
+        a = dict(good, **{k: v})
+        st = L.sps_mlp_adam(f, f, f, f, f, 3, 1, a["lr"], a["b1"], a["b2"], a["eps"], None)
+        assert st == S.SPS_ERR_INVALID_ARG, (k, v)
+        assert "Adam" in S.last_error()
+    assert L.sps_mlp_adam(f, f, f, f, f, 3, 0, 1e-3, 0.9, 0.999, 1e-8, None) == S.SPS_ERR_INVALID_ARG   # step 0
+    assert L.sps_mlp_adam(f, f, f, f, f, 17, 1, 1e-3, 0.9, 0.999, 1e-8, None) == S.SPS_ERR_INVALID_ARG  # d > 16
+    # instances: sizes, dimension, cost divisor and (for the gradient) the loss scale
+    def inst(**kw):
+        base = dict(x=256, y=256, a=256, b=256, n=10, m=12, d=3, cost_max=2.0, eps=0.1)
+        base.update(kw)
+        return S.MlpInstance(base["x"], base["y"], base["a"], base["b"], base["n"], base["m"], base["d"],
+                             base["cost_max"], base["eps"])
+    for kw in (dict(n=0), dict(d=17), dict(cost_max=0.0), dict(cost_max=math.inf), dict(x=None)):
+        assert L.sps_mlp_infer(f, C.byref(inst(**kw)), f, f, f, None) == S.SPS_ERR_INVALID_ARG, kw
+    for e in (0.0, math.inf, float("nan")):
+        st = L.sps_mlp_grad(f, f, C.byref(inst(eps=e)), f, f, f, None, f, None)
+        assert st == S.SPS_ERR_INVALID_ARG, e
+        assert "eps" in S.last_error()
+    assert L.sps_cost_max(f, 0, f, 5, 3, f, f, None) == S.SPS_ERR_INVALID_ARG
