@@ -209,3 +209,21 @@ def test_warm_start_arguments_validated(S):
         assert st == S.SPS_ERR_INVALID_ARG, e
         assert "eps" in S.last_error()
     assert L.sps_cost_max(f, 0, f, 5, 3, f, f, None) == S.SPS_ERR_INVALID_ARG
+
+
+def test_noalloc_refusals_need_no_device(S):
+    # spar_sink_ot_noalloc refuses bad arguments and problems larger than its fixed scratch array on the
+    # host, before it looks up the array or launches anything
+    f = S.lib().spar_sink_ot_noalloc
+    f.argtypes = [C.c_void_p] * 6
+    f.restype = C.c_int
+    res = S.Result()
+    out = C.c_void_p(256)
+    big = _prob(S, n=20000, m=20000, d=10)
+    Q = S.make_params(0.05, math.inf, 3.17e6, kdtype="f32")
+    assert S.sps_workspace_bytes(big, Q, 1) > 16 << 20
+    assert f(C.byref(big), C.byref(Q), out, out, C.byref(res), None) == S.SPS_ERR_WORKSPACE
+    assert "scratch" in S.last_error() and "spar_sink_ot" in S.last_error()
+    Qbad = S.make_params(-1.0, math.inf, 1000.0)
+    assert f(C.byref(_prob(S)), C.byref(Qbad), out, out, C.byref(res), None) == S.SPS_ERR_INVALID_ARG
+    assert "eps" in S.last_error()
