@@ -189,3 +189,28 @@ def test_dense_cost_input_equals_points(orc):
         # the point form accumulates in binary32, so patterns may differ on rare ties only
         assert abs(a["nnz"] - b["nnz"]) <= 2
         assert np.allclose(a["val"][:5], b["val"][:5], rtol=1e-12) or a["nnz"] != b["nnz"]
+
+
+@pytest.mark.parametrize("lam,kind", [(math.inf, "sqeuclid"), (1.0, "sqeuclid"), (0.5, "wfr"), (1.0, "uniform")])
+def test_row_samplers_equal_full_sketch(orc, lam, kind):
+    # The full-size GPU checks compare sampled rows with the oracle's per-row
+    # samplers (every decision of a row re-derived from its counters): each
+    # must reproduce its row of the full sketch exactly, for both samplers.
+    w = inputs.small_problem(n=90, m=110, d=3, seed=31)
+    kw = dict(x=w.x, y=w.y, seed=77, pid=2)
+    if kind == "wfr":
+        kw.update(cost_kind="wfr", eta=0.6, cost_norm=0)
+    if kind == "uniform":
+        kw.update(probs="uniform")
+    P = orc.OracleProblem(w.a, w.b * (1.0 if math.isinf(lam) else 1.5), 0.1, 1500.0, lam, **kw)
+    for sampler, row_fn, count_fn in (("element", P.sample_row, P.count), ("skip", P.skip_row, P.skip_count)):
+        sk = P.sparsify(sampler=sampler)
+        cnt, nnz = count_fn()
+        assert nnz == sk["nnz"] and np.array_equal(cnt, np.diff(sk["row_ptr"]))
+        assert sk["nnz"] > 0
+        for i in range(P.n):
+            lo, hi = sk["row_ptr"][i], sk["row_ptr"][i + 1]
+            r = row_fn(i)
+            assert np.array_equal(r["cols"], sk["col_idx"][lo:hi]), (sampler, i)
+            for key, skey in (("val", "val"), ("logval", "logval"), ("pstar", "pstar"), ("cost", "cost")):
+                assert np.array_equal(r[key], sk[skey][lo:hi]), (sampler, i, key)
