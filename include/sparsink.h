@@ -360,6 +360,22 @@ const char* sps_last_error(void);
 /* Library version string. */
 const char* sps_version(void);
 
+/* Failure-detection self-test of the bounded device waits (the paper has no
+ * counterpart: its algorithms have no device waits).  The persistent
+ * iteration kernels synchronise their blocks with a grid barrier whose wait
+ * gives up after a fixed number of polls (about a second or more), records
+ * the timeout in the solve's control block and returns, so that a solve
+ * reports an error instead of hanging and the CUDA context stays usable.
+ * This call makes that wait run out, without any fault: it runs the same
+ * barrier on a two-block grid in which one block never arrives.
+ * ws: DEVICE, at least 1024 bytes (caller-owned scratch, contents
+ * overwritten).  *wait_ms (HOST) receives the duration of the launch.
+ * Synchronises `stream`.  Returns SPS_ERR_CUDA with the message "... timed
+ * out ..." when the device recorded the timeout (the expected outcome),
+ * SPS_OK if the barrier completed anyway, SPS_ERR_INVALID_ARG /
+ * SPS_ERR_WORKSPACE for bad arguments (before any launch). */
+sps_status sps_selftest_barrier_timeout(void* ws, size_t ws_bytes, float* wait_ms, sps_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

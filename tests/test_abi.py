@@ -227,3 +227,14 @@ def test_noalloc_refusals_need_no_device(S):
     Qbad = S.make_params(-1.0, math.inf, 1000.0)
     assert f(C.byref(_prob(S)), C.byref(Qbad), out, out, C.byref(res), None) == S.SPS_ERR_INVALID_ARG
     assert "eps" in S.last_error()
+
+
+def test_barrier_selftest_refusals_need_no_device(S):
+    f = S.lib().sps_selftest_barrier_timeout
+    f.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    ms = C.c_float(0.0)
+    assert f(None, 4096, C.byref(ms), None) == S.SPS_ERR_INVALID_ARG
+    assert f(C.c_void_p(256), 4096, None, None) == S.SPS_ERR_INVALID_ARG
+    assert f(C.c_void_p(256), 64, C.byref(ms), None) == S.SPS_ERR_WORKSPACE
+    assert "workspace" in S.last_error()
