@@ -37,3 +37,37 @@ def test_spmv_bytes_definition():
     r2, c2 = bench._spmv_bytes({"nnz": nnz}, n, m, "bf16", 1)
     assert r2 < row and c2 < col   # two-byte values outweigh the extra stabilised vectors here
     assert math.isclose(row + col, 51483896, rel_tol=0)   # the figure the default line reports
+
+
+def test_workloads_and_their_modes():
+    names = {"uot_n20000": (20000, 1.0, 0), "ot_n1000": (1000, math.inf, 0), "ot_n200000": (200000, math.inf, 1),
+             "ot_n1000000": (1000000, math.inf, 1)}
+    assert set(bench.WORKLOADS) == set(names) | {"frames64"}
+    for name, (n, lam, logd) in names.items():
+        w = bench._workload(name)
+        assert w.n == n and w.lam == lam and bench._log_domain(w) == logd
+        cfg = bench._config(w, "flushed")
+        assert cfg["workload"] == w.name and cfg["n"] == n and cfg["log_domain"] == logd
+        assert cfg["lambda"] == (None if math.isinf(lam) else lam)
+    # --n re-draws the same family at another size
+    assert bench._workload("uot_n20000", 2000).n == 2000
+    with pytest.raises(SystemExit):
+        bench._workload("no_such_workload")
+
+
+def test_frames_batch_budgets():
+    sets, pairs, s = bench._frames_batch()
+    assert len(pairs) == 2016 and len(s) == 2016
+    for (i, j), sp in zip(pairs[:50], s[:50]):
+        nij = math.sqrt(len(sets[i][1]) * len(sets[j][1]))
+        assert sp == pytest.approx(8.0 * 1e-3 * nij * math.log(nij) ** 4)
+
+
+def test_peak_is_the_measured_copy_bandwidth():
+    peak, kind = bench._peaks()
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        import json
+        assert kind == "measured" and peak == json.load(open(path))["hbm_gbs"]
+    else:
+        assert (peak, kind) == (6800.0, "fallback")
