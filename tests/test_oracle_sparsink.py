@@ -60,3 +60,35 @@ def test_uot_spar_sink_close_to_dense(orc):
     sp = orc.spar_sink(P, tol=1e-10, max_iter=100000)
     de = orc.dense_sinkhorn(P, tol=1e-10, max_iter=100000)
     assert abs(sp["obj_sparse"] - de["obj"]) / abs(de["obj"]) < 0.05
+
+
+def test_sparse_problem_value_is_the_dual_optimum_on_the_support(orc):
+    # Reading c-3: obj_sparse (R2) is the entropic OT value of the sparse problem whose cost is
+    # C~ = C + eps log p* on the sampled support S and +inf elsewhere, since K~ = K / p* = exp(-C~/eps).
+    # Its concave dual max a.alpha + b.beta - eps sum_{(i,j) in S} exp((alpha_i + beta_j - C~_ij)/eps),
+    # maximised here by a generic quasi-Newton method, must equal R2; R1 differs by eps sum T log p*.
+    from scipy import optimize
+    n = 30
+    x, y, a, b = _setup(n, seed=4)
+    P = orc.OracleProblem(a, b, 0.1, 12 * n, math.inf, x=x, y=y, seed=3)
+    sp = orc.spar_sink(P, tol=1e-12, max_iter=100000)
+    sk = sp["sketch"]
+    assert sp["info"]["status"] == 0 and sp["info"]["unreach_a"] == 0.0 and np.isfinite(sp["beta"]).all()
+    rows = np.repeat(np.arange(n), np.diff(sk["row_ptr"]))
+    cols = sk["col_idx"]
+    Ct = sk["cost"] + 0.1 * np.log(sk["pstar"].astype(np.float64))
+    eps = 0.1
+
+    def neg_dual(z):
+        al, be = z[:n], z[n:]
+        E = np.exp((al[rows] + be[cols] - Ct) / eps)
+        g = a @ al + b @ be - eps * E.sum()
+        ga = a - np.bincount(rows, E, n)
+        gb = b - np.bincount(cols, E, n)
+        return -g, -np.concatenate([ga, gb])
+
+    opt = optimize.minimize(neg_dual, np.zeros(2 * n), jac=True, method="L-BFGS-B",
+                            options={"gtol": 1e-13, "ftol": 1e-16, "maxiter": 50000})
+    assert abs(-opt.fun - sp["obj_sparse"]) < 1e-8 * abs(sp["obj_sparse"])
+    assert abs(sp["obj_sparse"] - sp["obj"] - eps * sp["terms"]["logp"]) < 1e-12
+    assert abs(sp["terms"]["logp"]) > 1e-3          # the two readings differ on this sketch
