@@ -92,3 +92,35 @@ def test_sparse_problem_value_is_the_dual_optimum_on_the_support(orc):
     assert abs(-opt.fun - sp["obj_sparse"]) < 1e-8 * abs(sp["obj_sparse"])
     assert abs(sp["obj_sparse"] - sp["obj"] - eps * sp["terms"]["logp"]) < 1e-12
     assert abs(sp["terms"]["logp"]) > 1e-3          # the two readings differ on this sketch
+
+
+def test_sparse_uot_value_is_the_dual_optimum_on_the_support(orc):
+    # Readings c-3 and c-6 for Alg. 4: R2 of a UOT sketch equals the maximum of
+    # lam a.(1 - e^{-alpha/lam}) + lam b.(1 - e^{-beta/lam}) - eps sum_S exp((alpha_i + beta_j - C~_ij)/eps)
+    # over the sampled support S, with C~ = C + eps log p* (generic quasi-Newton maximiser).
+    from scipy import optimize
+    n, eps, lam = 30, 0.1, 0.7
+    x, y, a, b = _setup(n, seed=5)
+    b = 1.5 * b
+    P = orc.OracleProblem(a, b, eps, 12 * n, lam, x=x, y=y, seed=8)
+    sp = orc.spar_sink(P, tol=1e-12, max_iter=100000)
+    sk = sp["sketch"]
+    assert sp["info"]["status"] == 0 and np.isfinite(sp["alpha"]).all() and np.isfinite(sp["beta"]).all()
+    rows = np.repeat(np.arange(n), np.diff(sk["row_ptr"]))
+    cols = sk["col_idx"]
+    Ct = sk["cost"] + eps * np.log(sk["pstar"].astype(np.float64))
+
+    def neg_dual(z):
+        al, be = z[:n], z[n:]
+        E = np.exp((al[rows] + be[cols] - Ct) / eps)
+        ea, eb = np.exp(-al / lam), np.exp(-be / lam)
+        g = lam * a @ (1 - ea) + lam * b @ (1 - eb) - eps * E.sum()
+        ga = a * ea - np.bincount(rows, E, n)
+        gb = b * eb - np.bincount(cols, E, n)
+        return -g, -np.concatenate([ga, gb])
+
+    opt = optimize.minimize(neg_dual, np.zeros(2 * n), jac=True, method="L-BFGS-B",
+                            options={"gtol": 1e-13, "ftol": 1e-16, "maxiter": 50000})
+    assert abs(-opt.fun - sp["obj_sparse"]) < 1e-8 * abs(sp["obj_sparse"])
+    # the oracle's own potentials attain it
+    assert abs(-neg_dual(np.concatenate([sp["alpha"], sp["beta"]]))[0] - sp["obj_sparse"]) < 1e-9
