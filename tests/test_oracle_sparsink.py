@@ -124,3 +124,37 @@ def test_sparse_uot_value_is_the_dual_optimum_on_the_support(orc):
     assert abs(-opt.fun - sp["obj_sparse"]) < 1e-8 * abs(sp["obj_sparse"])
     # the oracle's own potentials attain it
     assert abs(-neg_dual(np.concatenate([sp["alpha"], sp["beta"]]))[0] - sp["obj_sparse"]) < 1e-9
+
+
+@pytest.mark.parametrize("lam", [math.inf, 0.7])
+def test_log_domain_sparse_value_is_the_dual_optimum(orc, lam):
+    # The same identity for the log-domain form at eps = 0.01 (where exp(-C/eps) spans ~43 orders of
+    # magnitude): R2 equals the maximum of the sparse problem's dual, found by L-BFGS from zero.
+    from scipy import optimize
+    n, eps = 40, 0.01
+    x, y, a, b = _setup(n, seed=6)
+    if not math.isinf(lam):
+        b = 1.5 * b
+    P = orc.OracleProblem(a, b, eps, 12 * n, lam, x=x, y=y, seed=9)
+    sp = orc.spar_sink(P, tol=1e-12, max_iter=200000, log_domain=True)
+    sk = sp["sketch"]
+    assert sp["info"]["status"] == 0 and np.isfinite(sp["alpha"]).all() and np.isfinite(sp["beta"]).all()
+    rows = np.repeat(np.arange(n), np.diff(sk["row_ptr"]))
+    cols = sk["col_idx"]
+    Ct = sk["cost"] + eps * np.log(sk["pstar"].astype(np.float64))
+
+    def neg_dual(z):
+        al, be = z[:n], z[n:]
+        E = np.exp((al[rows] + be[cols] - Ct) / eps)
+        if math.isinf(lam):
+            g = a @ al + b @ be - eps * E.sum()
+            ga, gb = a - np.bincount(rows, E, n), b - np.bincount(cols, E, n)
+        else:
+            ea, eb = np.exp(-al / lam), np.exp(-be / lam)
+            g = lam * a @ (1 - ea) + lam * b @ (1 - eb) - eps * E.sum()
+            ga, gb = a * ea - np.bincount(rows, E, n), b * eb - np.bincount(cols, E, n)
+        return -g, -np.concatenate([ga, gb])
+
+    opt = optimize.minimize(neg_dual, np.zeros(2 * n), jac=True, method="L-BFGS-B",
+                            options={"gtol": 1e-13, "ftol": 1e-16, "maxiter": 50000})
+    assert abs(-opt.fun - sp["obj_sparse"]) < 1e-9 * abs(sp["obj_sparse"])
