@@ -158,3 +158,34 @@ def test_log_domain_sparse_value_is_the_dual_optimum(orc, lam):
     opt = optimize.minimize(neg_dual, np.zeros(2 * n), jac=True, method="L-BFGS-B",
                             options={"gtol": 1e-13, "ftol": 1e-16, "maxiter": 50000})
     assert abs(-opt.fun - sp["obj_sparse"]) < 1e-9 * abs(sp["obj_sparse"])
+
+
+def test_wfr_uot_value_is_the_dual_optimum_with_unreachable_mass(orc):
+    # WFR cost (section 2.2) with eta = 0.25: transport is blocked beyond pi eta, a row and a column of the
+    # sketch are empty (reading c-4: their mass is unreachable).  Their KL terms lam a_i are the
+    # supremum of lam a_i (1 - e^{-alpha_i/lam}) as alpha_i grows, so R2 still equals the dual optimum.
+    from scipy import optimize
+    n, eps, lam = 30, 0.1, 0.7
+    x, y, a, b = _setup(n, seed=7)
+    b = 1.5 * b
+    P = orc.OracleProblem(a, b, eps, 12 * n, lam, x=x, y=y, seed=4, cost_kind="wfr", eta=0.25, cost_norm=0)
+    sp = orc.spar_sink(P, tol=1e-12, max_iter=100000)
+    sk = sp["sketch"]
+    assert sp["info"]["status"] == 0
+    assert sp["info"]["unreach_a"] > 0 and sp["info"]["unreach_b"] > 0
+    assert np.isfinite(sk["cost"]).all()
+    rows = np.repeat(np.arange(n), np.diff(sk["row_ptr"]))
+    cols = sk["col_idx"]
+    Ct = sk["cost"] + eps * np.log(sk["pstar"].astype(np.float64))
+
+    def neg_dual(z):
+        al, be = z[:n], z[n:]
+        E = np.exp((al[rows] + be[cols] - Ct) / eps)
+        ea, eb = np.exp(-al / lam), np.exp(-be / lam)
+        g = lam * a @ (1 - ea) + lam * b @ (1 - eb) - eps * E.sum()
+        ga, gb = a * ea - np.bincount(rows, E, n), b * eb - np.bincount(cols, E, n)
+        return -g, -np.concatenate([ga, gb])
+
+    opt = optimize.minimize(neg_dual, np.zeros(2 * n), jac=True, method="L-BFGS-B",
+                            options={"gtol": 1e-13, "ftol": 1e-16, "maxiter": 50000})
+    assert abs(-opt.fun - sp["obj_sparse"]) < 1e-9 * abs(sp["obj_sparse"])
