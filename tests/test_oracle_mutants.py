@@ -73,6 +73,12 @@ CASES = [
      'return r1, r1 + eps * terms["logp"]', 'return r1, r1 - eps * terms["logp"]', "test_oracle_sparsink.py"),
     ("UOT objective with the KL term of a only", "oracle.py",
      'r1 += lam * (terms["kl_a"] + terms["kl_b"])', 'r1 += lam * terms["kl_a"]', "test_oracle_sinkhorn.py"),
+    ("log-domain UOT update without the exponent phi", "sparsink_oracle.c",
+     "alpha[i] = L[i] > -INFINITY ? phi * (eps * log(a[i]) - eps * L[i]) : -INFINITY;",
+     "alpha[i] = L[i] > -INFINITY ? (eps * log(a[i]) - eps * L[i]) : -INFINITY;", "test_oracle_sparsink.py"),
+    ("sparse cost without the divisor in the value path", "sparsink_oracle.c",
+     "return is_wfr(P) ? wfr_cost64(P, d) : d / cost_divisor(P, S);",
+     "return is_wfr(P) ? wfr_cost64(P, d) : d;", "test_oracle_sparsink.py"),
     ("Philox: nine rounds", "sparsink_oracle.c", "for (int r = 0; r < 10; ++r) {",
      "for (int r = 0; r < 9; ++r) {", "test_oracle_rng.py"),
     ("exact sum: ties not to even", "sparsink_oracle.c", "if (round_bit && (sticky || (mant & 1u))) {",
