@@ -229,7 +229,6 @@ sps_status spar_sink_uot(const sps_problem* prob, const sps_params* prm, void* w
 sps_status spar_sink_ot_noalloc(const sps_problem* prob, const sps_params* prm, void* alpha_out,
                                 void* beta_out, sps_result* res, sps_stream stream);
 
-/* Thread-local message describing the last error on this thread. */
 /* ---------------- batches of problems over shared point sets ----------------
  * Many independent problems whose points come from a few shared sets, e.g.
  * all pairs of frames of an image sequence: pair p transports set src[p]
@@ -328,7 +327,11 @@ typedef struct {
   double eps;                       /* training loss scale (finite, > 0): errors are measured in units of eps */
 } sps_mlp_instance;
 
+/* Length of each parameter vector (FP32 and BF16 copies) for points of dimension d (both sides);
+ * 0 unless 1 <= d <= 16. */
 size_t sps_mlp_param_count(int32_t d);
+/* Bytes of the scratch `ws` that sps_cost_max, sps_mlp_infer, sps_mlp_gauge_fix and sps_mlp_grad take
+ * (caller-allocated device memory, independent of the instance size). */
 size_t sps_mlp_workspace_bytes(void);
 /* He-uniform initialisation from the Philox stream of `seed`; fills both copies. */
 sps_status sps_mlp_init(float* params, void* params_bf16, int32_t d, uint64_t seed, sps_stream stream);
@@ -355,6 +358,8 @@ sps_status sps_mlp_grad(const float* params, const void* params_bf16, const sps_
 sps_status sps_mlp_adam(float* params, void* params_bf16, float* m1, float* m2, const float* grad, int32_t d,
                         int32_t step, float lr, float beta1, float beta2, float eps, sps_stream stream);
 
+/* Thread-local message describing the last error on this thread (valid until the next call
+ * on this thread that fails). */
 const char* sps_last_error(void);
 
 /* Library version string. */
