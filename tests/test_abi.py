@@ -238,3 +238,17 @@ def test_barrier_selftest_refusals_need_no_device(S):
     assert f(C.c_void_p(256), 4096, None, None) == S.SPS_ERR_INVALID_ARG
     assert f(C.c_void_p(256), 64, C.byref(ms), None) == S.SPS_ERR_WORKSPACE
     assert "workspace" in S.last_error()
+
+
+def test_every_declaration_is_documented():
+    # each entry point in include/*.h carries its own comment (meaning, layout, ownership, errors)
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        lines = open(os.path.join(ROOT, "include", fn)).read().split("\n")
+        for k, line in enumerate(lines):
+            m = re.match(r"^(?:const\s+)?(?:size_t|sps_status|const char\*|char\*)\s+([a-z_][a-z0-9_]*)\s*\(", line)
+            if not m:
+                continue
+            above = "\n".join(lines[max(0, k - 3):k])
+            assert "*/" in above, f"{fn}: {m.group(1)} has no comment above its declaration"
