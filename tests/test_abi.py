@@ -242,6 +242,7 @@ def test_barrier_selftest_refusals_need_no_device(S):
 
 def test_every_declaration_is_documented():
     # each entry point in include/*.h carries its own comment (meaning, layout, ownership, errors)
+    seen = set()
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if not fn.endswith(".h"):
             continue
@@ -252,3 +253,5 @@ def test_every_declaration_is_documented():
                 continue
             above = "\n".join(lines[max(0, k - 3):k])
             assert "*/" in above, f"{fn}: {m.group(1)} has no comment above its declaration"
+            seen.add(m.group(1))
+    assert seen == _declared_functions()
