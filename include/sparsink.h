@@ -217,9 +217,12 @@ sps_status spar_sink_uot(const sps_problem* prob, const sps_params* prm, void* w
  * bytes, held by every GPU that loads the library until the process exits.
  * The call makes no device allocation (no cudaMalloc / cudaFree, no
  * allocating library routine); like every solver entry point it creates the
- * CUDA events that time its phases.  The first call on a device (with that
- * device current) looks up the array's device address with
- * cudaGetSymbolAddress; make that first call before any stream capture.
+ * CUDA events that time its phases.  The first call made on a device in a
+ * CUDA context (with that device current) looks up the array's device address
+ * with cudaGetSymbolAddress; later calls in the same context reuse it, and a
+ * new context (after cudaDeviceReset, say) gets its own lookup.  Make that
+ * first call before any stream capture begins.  Like spar_sink_ot, the call
+ * waits for its stream and reads the result back before it returns.
  * Problems whose sps_workspace_bytes(..., SPS_OP_SPAR_SINK) exceeds the array
  * are rejected with SPS_ERR_WORKSPACE before any launch.  All calls share the
  * array, which keeps the last call's contents (each call clears what must
