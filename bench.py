@@ -3,9 +3,12 @@
 A step is one complete Spar-Sink solve of the workload (sketch construction,
 scaling iterations until the stopping residual is <= 1e-5, objective), with
 the inputs resident in HBM; L2 is flushed (a 512 MB write) between timed steps.
-Default workload: UOT, lambda = 1, n = m = 20000 points in R^10 (3-component
-Gaussian mixture vs multivariate t with 3 degrees of freedom), eps = 0.05,
-s = 16 n ln n, FP32 values and iterates.
+Default workload: balanced OT, n = m = 1,000,000 points in R^3 from
+16-component Gaussian mixtures, eps = 0.01 (stabilised iterations with
+absorption), s = 16 n ln n, FP32 values and iterates, skip sampler.  The
+20000-point UOT workload (lambda = 1, R^10, eps = 0.05) is reported beside it
+under "other_workloads"; its sketch stays in L2, so its SpMV rate is labelled
+"l2-effective", not HBM.
 
 One JSON line on rank 0.  `value` is the time per solve (ms, lower is better);
 under torchrun every rank solves its own replica (weak scaling, no data-path
@@ -311,15 +314,35 @@ def _spmv_bytes(res, n, m, kdtype="f32", log_domain=0):
 
 def _traffic(name):
     """DRAM bytes per iteration of the iteration kernel from the committed ncu
-    summary of this workload (profiles/spmv_traffic_<name>.txt), or None."""
-    p = os.path.join(ROOT, "profiles", f"spmv_traffic_{name}.txt")
+    summary of this workload (profiles/spmv_traffic_<name>.txt): (bytes, the
+    summary's file name), or (None, None)."""
+    fn = f"spmv_traffic_{name}.txt"
+    p = os.path.join(ROOT, "profiles", fn)
     if not os.path.exists(p):
-        return None
+        return None, None
     with open(p) as f:
         for line in f:
             if line.startswith("bytes_per_iteration:"):
-                return float(line.split(":", 1)[1])
-    return None
+                return float(line.split(":", 1)[1]), "profiles/" + fn
+    return None, None
+
+
+def _bound(traffic, algorithmic):
+    """HBM-bound only when the DRAM traffic measured for the kernel is at least
+    half of its algorithmic bytes; a sketch that stays in L2 reads far less
+    from DRAM, and its rate is an L2-effective one."""
+    if traffic is None:
+        return "hbm (traffic not measured)"
+    return "hbm" if traffic >= 0.5 * algorithmic else "l2-effective"
+
+
+def _dense_cap(args, w):
+    """Dense Sinkhorn iterations allowed before the run stops and its time to
+    tolerance is extrapolated: --dense-cap if given (> 0), else 2 above 1e10
+    kernel entries (a dense iteration at n = m = 10^6 takes about 2 s), else no cap."""
+    if args.dense_cap > 0:
+        return args.dense_cap
+    return 2 if float(w.n) * w.m > 1e10 else 20000
 
 
 def _golden(w):
@@ -412,12 +435,12 @@ def run_ours(args):
     per_iter_ms = rf["ms_iter"] / max(rf["iters_enqueued"], 1)
     peak, peak_kind = _peaks()
     achieved = (row_b + col_b) / (per_iter_ms * 1e-3) / 1e9
-    traffic = _traffic(w.name)
+    traffic, traffic_src = _traffic(w.name)
 
     # dense Sinkhorn on the same GPU, same tolerance (log-sum-exp form for small
     # eps); with --dense-cap the run stops after that many iterations and the
     # time to tolerance is extrapolated at Spar-Sink's iteration count
-    cap = args.dense_cap if args.dense_cap > 0 else 20000
+    cap = _dense_cap(args, w)
     dkw = dict(eps=w.eps, lam=w.lam, tol=TOL, max_iter=cap, dtype=pdt, log_domain=logd, raise_on_error=False)
     dense = S.sinkhorn_dense(a, b, x, y, **dkw)
     dense = S.sinkhorn_dense(a, b, x, y, **dkw, workspace=dense["workspace"])
@@ -459,15 +482,16 @@ def run_ours(args):
     gold = _golden(w)
     if logd and rank == 0 and gold is not None:
         precision = {}
+        gs = gold.get("sampler", "element")   # the stream the stored oracle solve was sketched with
         for k2 in ("f32", "bf16", "f16"):
-            # the stored oracle solve used the per-element stream
-            rr = solve(kdtype=k2, sampler="element")
-            rr = solve(kdtype=k2, sampler="element", workspace=rr["workspace"])
+            rr = solve(kdtype=k2, sampler=gs)
+            rr = solve(kdtype=k2, sampler=gs, workspace=rr["workspace"])
             ent = {"ms": round(rr["ms_sketch"] + rr["ms_iter"] + rr["ms_obj"], 3), "iters": rr["iters"],
                    "obj": rr["obj"], "n_absorb": rr["n_absorb"]}
             if gold is not None:
                 ent["rel_err_vs_fp64_oracle"] = abs(rr["obj"] - gold["obj"]) / abs(gold["obj"])
                 ent["oracle_iters"] = gold["iters"]
+                ent["sampler"] = gs
             precision[k2] = ent
 
     # end to end through the public API with host buffers (pinned), copies inside
@@ -496,10 +520,12 @@ def run_ours(args):
         "iters": last["iters"], "nnz": last["nnz"], "residual": last["residual"], "obj": last["obj"],
         "obj_sparse": last["obj_sparse"], "n_absorb": last["n_absorb"],
         "dense_sinkhorn": dense_line,
-        "roofline": {"bound": "hbm", "kernel": "spmv half-iterations (row pass + column pass)",
+        "roofline": {"bound": _bound(traffic, row_b + col_b),
+                     "kernel": "spmv half-iterations (row pass + column pass)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                     "traffic": traffic, "algorithmic_bytes_per_iteration": row_b + col_b,
+                     "traffic": traffic, "traffic_source": traffic_src,
+                     "algorithmic_bytes_per_iteration": row_b + col_b,
                      "ms_per_iteration": round(per_iter_ms, 5), "iterations_timed": rf["iters_enqueued"]},
         "e2e": {"value": round(statistics.median(e2e), 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
@@ -511,6 +537,12 @@ def run_ours(args):
         line["other_sampler"] = other
     if precision is not None:
         line["precision_forms"] = precision
+    if rank == 0 and not args.no_other_workloads:
+        others = {}
+        for name in ("uot_n20000",):
+            if name != w.name.split("_d")[0]:
+                others[name] = _other_workload_leg(S, name, dev, flush_buf, args.sampler)
+        line["other_workloads"] = others
     if args.warm_start:
         line["warm_start"] = _warm_start_leg(args, w, S, x, y, a, b, kd, logd, last)
     if rank == 0 and not args.no_cpu_baseline:
@@ -519,6 +551,52 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _other_workload_leg(S, name, dev, flush_buf, sampler, steps=10):
+    """Time per solve of another named workload (inputs resident, L2 flushed
+    between solves), with the SpMV rate of a fixed 200-iteration run labelled
+    by the DRAM traffic measured for it."""
+    import torch
+    w = _workload(name)
+    pdt = _problem_dtype(w)
+    dt = torch.float64 if pdt == "f64" else torch.float32
+    x, y, a, b = (torch.tensor(z, dtype=dt, device=dev) for z in (w.x, w.y, w.a, w.b))
+    kd, logd = w.dtype, _log_domain(w)
+    kw = dict(eps=w.eps, s=w.s, tol=TOL, max_iter=20000, dtype=pdt, kdtype=kd, seed=w.seed, log_domain=logd,
+              sampler=sampler)
+    if math.isinf(w.lam):
+        run = lambda **e: S.spar_sink_ot(a, b, x, y, **dict(kw, **e))
+    else:
+        run = lambda **e: S.spar_sink_uot(a, b, x, y, lam=w.lam, **dict(kw, **e))
+    r = run()
+    ws = r["workspace"]
+    for _ in range(3):
+        run(workspace=ws)
+    st = torch.cuda.current_stream()
+    times = []
+    for _ in range(steps):
+        flush_buf.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        r = run(workspace=ws)
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    rf = run(tol=0.0, max_iter=200, check_every=200, workspace=ws)
+    row_b, col_b = _spmv_bytes(rf, w.n, w.m, kd, logd)
+    per = rf["ms_iter"] / max(rf["iters_enqueued"], 1)
+    peak, peak_kind = _peaks()
+    ach = (row_b + col_b) / (per * 1e-3) / 1e9
+    traffic, src = _traffic(w.name)
+    return {"workload": w.name, "ms": round(sum(times) / len(times), 4), "steps": steps,
+            "phases_ms": {"sketch": round(r["ms_sketch"], 4), "iterations": round(r["ms_iter"], 4),
+                          "objective": round(r["ms_obj"], 4)},
+            "iters": r["iters"], "nnz": r["nnz"], "obj": r["obj"],
+            "roofline": {"bound": _bound(traffic, row_b + col_b), "achieved": round(ach, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(ach / peak, 4), "peak_kind": peak_kind,
+                         "traffic": traffic, "traffic_source": src,
+                         "algorithmic_bytes_per_iteration": row_b + col_b, "ms_per_iteration": round(per, 5)}}
 
 
 def _warm_start_leg(args, w, S, x, y, a, b, kd, logd, cold):
@@ -621,23 +699,53 @@ def _threads():
         return os.cpu_count() or 1
 
 
-def _baseline_sample(w, sampler="element"):
-    if float(w.n) * w.m <= FULL_ORACLE_MAX_PAIRS:
+_THREADING = ("the oracle's cost maximum, UOT normaliser and sketch run on all host cores (OpenMP over rows); "
+              "its iterations and objective run on one thread")
+_THREADING_1 = "every part of the oracle runs on one thread (OpenMP limited to 1)"
+
+
+def _omp_set_threads(k):
+    """Thread count of the OpenMP runtime the oracle is linked with (False if
+    the runtime cannot be reached)."""
+    import ctypes
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(k))
+        return True
+    except (OSError, AttributeError):
+        return False
+
+
+def _baseline_sample(w, sampler="element", scale=1):
+    """The oracle timed on a bounded sample of the workload; scale > 1 shrinks
+    the sample (fewer rows) for the one-thread configuration."""
+    threading = _THREADING if scale == 1 else _THREADING_1
+    if float(w.n) * w.m <= FULL_ORACLE_MAX_PAIRS and scale == 1:
         ms, r = _oracle_solve(w, sampler)
         return ms, (f"one complete FP64 oracle solve of {w.name} ({sampler} sampler sketch, {r['info']['iters']} "
-                    f"iterations to 1e-5, objective) on the host cores, OpenMP over rows")
+                    f"iterations to 1e-5, objective); {threading}")
     gold = _golden(w)
     gi = gold["iters"] if gold else 200
-    rows = max(256, int(4.0e8 / w.m))
-    return _oracle_sampled(w, rows, 5, gi, sampler)
+    rows = max(256 // scale, int(4.0e8 / w.m) // scale, 16)
+    if float(w.n) * w.m <= FULL_ORACLE_MAX_PAIRS:
+        rows = max(16, w.n // (8 * scale))
+    est, desc = _oracle_sampled(w, rows, 5, gi, sampler)
+    return est, desc + "; " + threading
 
 
 def cpu_baseline(w, sampler="element"):
     import oracle
     oracle.build_oracle()
     ms, desc = _baseline_sample(w, sampler)
-    return {"value": round(ms, 1), "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", _threads())),
-            "kind": "oracle", "sample": desc}
+    out = {"value": round(ms, 1), "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", _threads())),
+           "kind": "oracle", "sample": desc}
+    # the same oracle on one thread, on a sample 8 times smaller, scaled the same way
+    if _omp_set_threads(1):
+        try:
+            ms1, desc1 = _baseline_sample(w, sampler, scale=8)
+            out["one_thread"] = {"value": round(ms1, 1), "unit": UNIT, "cores": 1, "sample": desc1}
+        finally:
+            _omp_set_threads(out["cores"])
+    return out
 
 
 def run_reference(args):
@@ -700,12 +808,14 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="uot_n20000", choices=WORKLOADS)
+    ap.add_argument("--workload", default="ot_n1000000", choices=WORKLOADS)
     ap.add_argument("--kdtype", default=None, choices=["f64", "f32", "bf16", "f16"],
                     help="storage type of the sketch values (default: the workload's)")
     ap.add_argument("--dense-cap", type=int, default=0,
-                    help="stop dense Sinkhorn after this many iterations and extrapolate (0: run to tolerance)")
+                    help="stop dense Sinkhorn after this many iterations and extrapolate "
+                         "(0: 2 above 1e10 kernel entries, else run to tolerance)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true", help="skip the 20000-point UOT leg")
     ap.add_argument("--sampler", default="skip", choices=["element", "skip"],
                     help="sketch draws: geometric skips with thinning (default), or one decision per element")
     ap.add_argument("--n", type=int, default=None, help="profiling: the workload's family at another size")

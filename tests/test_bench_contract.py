@@ -15,17 +15,37 @@ import bench  # noqa: E402
 from paper_2306_06581_gb300 import inputs  # noqa: E402
 
 
-@pytest.mark.parametrize("make,expect", [(inputs.uot_n20000, 1.6e6), (inputs.ot_n200000, 5.12e8)])
+@pytest.mark.parametrize("make,expect", [(inputs.uot_n20000, 1.6e6), (inputs.ot_n200000, 5.12e8),
+                                         (inputs.ot_n1000000, 3.5875e9)])
 def test_traffic_from_committed_profiles(make, expect):
     w = make()
-    assert bench._traffic(w.name) == pytest.approx(expect)
-    src = open(os.path.join(ROOT, "profiles", f"spmv_traffic_{w.name}.txt")).read()
+    traffic, src_name = bench._traffic(w.name)
+    assert traffic == pytest.approx(expect)
+    assert src_name == f"profiles/spmv_traffic_{w.name}.txt"
+    src = open(os.path.join(ROOT, src_name)).read()
     ref = src.split("source:", 1)[1].split()[0]
     assert os.path.exists(os.path.join(ROOT, ref)), ref
 
 
 def test_traffic_absent_is_null():
-    assert bench._traffic("no_such_workload") is None
+    assert bench._traffic("no_such_workload") == (None, None)
+
+
+def test_roofline_bound_label_follows_measured_traffic():
+    # the 20000-point UOT sketch stays in L2: 1.6 MB of DRAM per iteration against 51.5 MB algorithmic
+    assert bench._bound(1.6e6, 51483896) == "l2-effective"
+    # the 200000-point sketch streams from DRAM: 512 MB measured against 479 MB algorithmic
+    assert bench._bound(5.12e8, 479118184) == "hbm"
+    assert bench._bound(None, 1.0).startswith("hbm (traffic not measured")
+
+
+def test_dense_cap_is_automatic_only_for_large_problems():
+    class A:
+        dense_cap = 0
+    assert bench._dense_cap(A(), bench._workload("ot_n1000000", 200000)) == 2
+    assert bench._dense_cap(A(), bench._workload("uot_n20000")) == 20000
+    A.dense_cap = 5
+    assert bench._dense_cap(A(), bench._workload("uot_n20000")) == 5
 
 
 def test_spmv_bytes_definition():

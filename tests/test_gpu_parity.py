@@ -5,7 +5,9 @@
 - Spar-Sink / dense Sinkhorn, FP64: iterations within 1, potentials within
   1e-9, objective terms within 1e-10 relative;
 - FP32: objective within 1e-5 relative (the tolerance the method is held to
-  in FP32), iterations within max(3, 3%).
+  in FP32), iterations within max(3, 3%); potentials element by element after
+  the same fixed number of iterations on both sides, within the FP32 bound of
+  tests/parity_util.py (eps 10 N 2^-24, N the largest row or column count).
 Sizes span several row/column tiles with ragged tails.
 """
 import math
@@ -17,6 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2306_06581_gb300 import inputs  # noqa: E402
+from parity_util import compare_potentials, fixed_k, fp32_potential_bound, max_nnz  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -114,6 +117,13 @@ def test_spar_sink_uot_f32_matches_oracle(S, orc):
     assert abs(g["obj_sparse"] - o["obj_sparse"]) <= 1e-5 * abs(o["obj_sparse"])
     for k in ("kl_a", "kl_b", "mass", "transport"):
         assert abs(g[k] - o["terms"][k]) <= 1e-4 * abs(o["terms"][k]) + 1e-9, k
+    # potentials element by element after the oracle's iteration count on both sides (UOT: no gauge)
+    K = o["info"]["iters"]
+    run = lambda **e: S.spar_sink_uot(a, b, x, y, eps=w.eps, lam=w.lam, s=w.s, dtype="f32", **e)
+    gk, ok = fixed_k(run, orc, P, o["sketch"], K)
+    da, db = compare_potentials(gk["alpha"].cpu(), gk["beta"].cpu(), ok["alpha"], ok["beta"],
+                                fp32_potential_bound(w.eps, max_nnz(o["sketch"])))
+    print(f"UOT n=1500 FP32 potentials after {K} iterations: max |d alpha| {da:.2e}, |d beta| {db:.2e}")
 
 
 def test_spar_sink_ot_f32_matches_oracle(S, orc):
@@ -125,6 +135,14 @@ def test_spar_sink_ot_f32_matches_oracle(S, orc):
     assert g["status"] == o["info"]["status"] == 0
     assert abs(g["iters"] - o["info"]["iters"]) <= max(3, 0.03 * o["info"]["iters"])
     assert abs(g["obj"] - o["obj"]) <= 1e-5 * abs(o["obj"])
+    # potentials element by element after the oracle's iteration count on both sides
+    K = o["info"]["iters"]
+    P = _oracle_problem(orc, x, y, a, b, w.eps, math.inf, w.s)
+    run = lambda **e: S.spar_sink_ot(a, b, x, y, eps=w.eps, s=w.s, dtype="f32", **e)
+    gk, ok = fixed_k(run, orc, P, o["sketch"], K)
+    da, db = compare_potentials(gk["alpha"].cpu(), gk["beta"].cpu(), ok["alpha"], ok["beta"],
+                                fp32_potential_bound(w.eps, max_nnz(o["sketch"])))
+    print(f"OT n=3000 FP32 potentials after {K} iterations: max |d alpha| {da:.2e}, |d beta| {db:.2e}")
 
 
 @pytest.mark.parametrize("lam,dtype", [(math.inf, "f64"), (1.0, "f64"), (math.inf, "f32"), (1.0, "f32")])

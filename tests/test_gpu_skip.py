@@ -20,6 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2306_06581_gb300 import inputs  # noqa: E402
+from parity_util import compare_potentials, fixed_k, fp32_potential_bound, max_nnz  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -128,3 +129,11 @@ def test_skip_uot_solve_matches_oracle(S, orc):
     o = orc.spar_sink(P, tol=1e-5, sketch=P.sparsify(sampler="skip"))
     assert r["nnz"] == o["sketch"]["nnz"]
     assert abs(r["obj"] - o["obj"]) <= 1e-5 * abs(o["obj"])
+    # potentials element by element after the oracle's iteration count on both sides (UOT: no gauge)
+    K = o["info"]["iters"]
+    run = lambda **e: S.spar_sink_uot(a, b, x, y, eps=w.eps, lam=w.lam, s=w.s, dtype="f32", seed=w.seed,
+                                      sampler="skip", **e)
+    gk, ok = fixed_k(run, orc, P, o["sketch"], K)
+    da, db = compare_potentials(gk["alpha"].cpu(), gk["beta"].cpu(), ok["alpha"], ok["beta"],
+                                fp32_potential_bound(w.eps, max_nnz(o["sketch"])))
+    print(f"UOT n=3000 skip FP32 potentials after {K} iterations: max |d alpha| {da:.2e}, |d beta| {db:.2e}")
