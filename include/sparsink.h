@@ -61,8 +61,8 @@ typedef enum { SPS_F64 = 0, SPS_F32 = 1, SPS_BF16 = 2, SPS_F16 = 3 } sps_dtype;
 #define SPS_STOP_DELTA_UV 1 /* ||u^t - u^{t-1}||_1 + ||v^t - v^{t-1}||_1 <= tol (Alg. 1 / 2) */
 
 /* One OT/UOT problem (section 2): measures a (n) and b (m) on points x, y,
- * with the squared Euclidean raw cost ||x_i - y_j||^2 (section 5.1) or a
- * given raw cost matrix. */
+ * with the squared Euclidean raw cost ||x_i - y_j||^2 (section 5.1), a given
+ * raw cost matrix, or the Wasserstein-Fisher-Rao cost of section 2.2. */
 typedef struct {
   int32_t n, m, d;
   const void* x;      /* device, n*d, dtype; may be NULL when C is given (then ignored) */
@@ -73,7 +73,17 @@ typedef struct {
   const void* a;      /* device, n, dtype, a_i >= 0 */
   const void* b;      /* device, m, dtype, b_j >= 0 */
   sps_dtype dtype;    /* SPS_F32 or SPS_F64: type of x, y, C, a, b */
+  int32_t cost_kind;  /* SPS_COST_SQEUCLID (0): the raw cost above, normalised by cost_norm.
+                         SPS_COST_WFR (1): C_ij = -log cos_+^2(d_ij / (2 eta)) with d_ij the
+                         Euclidean distance of the points (section 2.2): K_ij = cos^2 where
+                         d_ij < pi eta, 0 (transport blocked) beyond.  Needs points (C = NULL)
+                         and cost_norm = SPS_COST_RAW; sinkhorn_dense and the batched solver
+                         take SPS_COST_SQEUCLID only.  Other values: SPS_ERR_INVALID_ARG. */
+  double eta;         /* SPS_COST_WFR: the length scale eta (finite, > 0); ignored otherwise */
 } sps_problem;
+
+#define SPS_COST_SQEUCLID 0
+#define SPS_COST_WFR 1
 
 /* Parameters of a solve. */
 typedef struct {
@@ -117,7 +127,17 @@ typedef struct {
                           normaliser Z is still an exact sum over all pairs).  sketch_mode
                           does not apply to it; spar_sink_batched accepts SPS_SAMPLER_ELEMENT
                           only. */
+  int32_t probs;       /* Sampling probabilities of Eq. (pois).  SPS_PROBS_PAPER (0):
+                          Eq. (pij-ot) for OT, Eq. (pij-uot) for UOT.  SPS_PROBS_EQUAL (1):
+                          p_ij = 1/(n m) for every element, p*_ij = min(1, s/(n m)) -- the
+                          equal-probability control (Rand-Sink) of section 5, for OT and UOT;
+                          the decision is then r_i c_j with r_i = fl(fl(s) fl(1/(n m))), c_j = 1.
+                          spar_sink_batched takes SPS_PROBS_PAPER only.  Other values:
+                          SPS_ERR_INVALID_ARG. */
 } sps_params;
+
+#define SPS_PROBS_PAPER 0
+#define SPS_PROBS_EQUAL 1
 
 #define SPS_SKETCH_SINGLE 0
 #define SPS_SKETCH_TWO_PASS 1

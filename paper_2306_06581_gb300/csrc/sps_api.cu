@@ -222,6 +222,16 @@ static sps_status validate(const sps_problem* P, const sps_params* Q, int op) {
   if (Q->gather_mode < SPS_GATHER_AUTO || Q->gather_mode > SPS_GATHER_STAGED) { set_error("unknown gather_mode %d", Q->gather_mode); return SPS_ERR_INVALID_ARG; }
   if (Q->sketch_mode != SPS_SKETCH_SINGLE && Q->sketch_mode != SPS_SKETCH_TWO_PASS) { set_error("unknown sketch_mode %d", Q->sketch_mode); return SPS_ERR_INVALID_ARG; }
   if (Q->sampler != SPS_SAMPLER_ELEMENT && Q->sampler != SPS_SAMPLER_SKIP) { set_error("unknown sampler %d", Q->sampler); return SPS_ERR_INVALID_ARG; }
+  if (Q->probs != SPS_PROBS_PAPER && Q->probs != SPS_PROBS_EQUAL) { set_error("unknown probs %d", Q->probs); return SPS_ERR_INVALID_ARG; }
+  if (P->cost_kind != SPS_COST_SQEUCLID && P->cost_kind != SPS_COST_WFR) {
+    set_error("unknown cost_kind %d", P->cost_kind); return SPS_ERR_INVALID_ARG;
+  }
+  if (P->cost_kind == SPS_COST_WFR) {
+    if (P->C) { set_error("the WFR cost is defined from points: give x, y and no cost matrix"); return SPS_ERR_INVALID_ARG; }
+    if (P->cost_norm != SPS_COST_RAW) { set_error("the WFR cost takes cost_norm = SPS_COST_RAW"); return SPS_ERR_INVALID_ARG; }
+    if (!(P->eta > 0.0) || !isfinite(P->eta)) { set_error("WFR eta must be > 0 and finite (eta=%g)", P->eta); return SPS_ERR_INVALID_ARG; }
+    if (op == SPS_OP_DENSE) { set_error("sinkhorn_dense takes the squared Euclidean cost only"); return SPS_ERR_INVALID_ARG; }
+  }
 
   if (op != SPS_OP_DENSE && (double)Q->s + 8.0 * sqrt(Q->s) + 1024.0 > 2147483647.0 &&
       (double)P->n * (double)P->m > 2147483647.0) {
@@ -229,6 +239,9 @@ static sps_status validate(const sps_problem* P, const sps_params* Q, int op) {
   }
   return SPS_OK;
 }
+
+// The sampling probabilities a solve uses (dense Sinkhorn samples nothing).
+static int op_probs(const sps_params* Q) { return Q->probs == SPS_PROBS_EQUAL ? SPS_PROBS_EQUAL : SPS_PROBS_PAPER; }
 
 static ProbDev make_probdev(const sps_problem* P, const sps_params* Q, const Layout& L, char* ws) {
   ProbDev pd;
@@ -250,6 +263,10 @@ static ProbDev make_probdev(const sps_problem* P, const sps_params* Q, const Lay
   pd.cost_norm = P->cost_norm; pd.cost_scale = P->cost_scale;
   pd.eps = Q->eps; pd.lam = Q->lambda; pd.s = Q->s;
   pd.is_ot = isinf(Q->lambda) ? 1 : 0;
+  pd.probs = op_probs(Q);
+  pd.sep = (pd.is_ot || pd.probs == SPS_PROBS_EQUAL) ? 1 : 0;
+  pd.cost_kind = P->cost_kind;
+  pd.eta = P->cost_kind == SPS_COST_WFR ? P->eta : 0.0;
   pd.seed = Q->seed; pd.pid = Q->problem_id;
   return pd;
 }

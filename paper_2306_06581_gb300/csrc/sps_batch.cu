@@ -795,6 +795,7 @@ sps_status validate_batch(const sps_batch* Bt, const sps_params* Q) {
   if (!Bt || !Q) { set_error("null batch or params"); return SPS_ERR_INVALID_ARG; }
   if (Bt->n_sets < 1 || Bt->n_pairs < 1) { set_error("empty batch"); return SPS_ERR_INVALID_ARG; }
   if (Q->sampler != SPS_SAMPLER_ELEMENT) { set_error("the batched solver draws one decision per element (sampler 0)"); return SPS_ERR_INVALID_ARG; }
+  if (Q->probs != SPS_PROBS_PAPER) { set_error("the batched solver samples with Eq. (pij-ot) / Eq. (pij-uot) only (probs 0)"); return SPS_ERR_INVALID_ARG; }
   if (Bt->d < 1 || Bt->d > 16) { set_error("batch points need 1 <= d <= 16 (d=%d)", Bt->d); return SPS_ERR_INVALID_ARG; }
   if (!Bt->set_off || !Bt->pts || !Bt->mass || !Bt->src || !Bt->dst || !Bt->s) { set_error("null batch array"); return SPS_ERR_INVALID_ARG; }
   if (Bt->dtype != SPS_F32 && Bt->dtype != SPS_F64) { set_error("batch inputs are F32 or F64"); return SPS_ERR_INVALID_ARG; }

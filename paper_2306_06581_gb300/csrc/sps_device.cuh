@@ -76,6 +76,22 @@ __device__ __forceinline__ float spec_exp(float x) {
   return __fmul_rn(__fmul_rn(p, pow2f_small(k1)), pow2f_small(k2));
 }
 
+// cos z for 0 <= z <= pi/2 in the binary32 spec: the Taylor series
+// 1 - z^2/2! + z^4/4! - ... to z^14/14! in w = z^2 (the next term is below
+// 7e-11 at pi/2), Horner form with fused multiply-adds; the coefficients are
+// 1/k! rounded once to binary32.
+__device__ __forceinline__ float spec_cos(float z) {
+  const float w = __fmul_rn(z, z);
+  float p = (float)(-1.0 / 87178291200.0);
+  p = __fmaf_rn(p, w, (float)(1.0 / 479001600.0));
+  p = __fmaf_rn(p, w, (float)(-1.0 / 3628800.0));
+  p = __fmaf_rn(p, w, (float)(1.0 / 40320.0));
+  p = __fmaf_rn(p, w, (float)(-1.0 / 720.0));
+  p = __fmaf_rn(p, w, (float)(1.0 / 24.0));
+  p = __fmaf_rn(p, w, -0.5f);
+  return __fmaf_rn(p, w, 1.0f);
+}
+
 __device__ __forceinline__ float spec_log(float x) {
   if (x != x) return x;
   if (x < 0.0f) return __int_as_float(0x7fc00000);

@@ -59,6 +59,8 @@ struct SketchScalars {
   float dn32;         // value path: cost normaliser (binary32)
   double dn64;        // value path: cost normaliser (FP64)
   float cmax32;       // skip sampler: max_j of the column factors (exact)
+  float inv2eta32;    // WFR: fl32(1/(2 eta))
+  float g2_32;        // WFR UOT decision: fl32(2/(2 lam + eps)), K^{eps/(2 lam + eps)} = cos^{g2}
   ExactAcc acc1, acc2;
 };
 
@@ -134,7 +136,11 @@ struct ProbDev {
   int cost_norm;
   double cost_scale;
   double eps, lam, s;
-  int is_ot;
+  int is_ot;           // balanced OT (lam = +inf): Alg. 1 iterations
+  int sep;             // the decision factors as r_i c_j: Eq. (pij-ot), or the equal probabilities
+  int probs;           // SPS_PROBS_*
+  int cost_kind;       // SPS_COST_SQEUCLID / SPS_COST_WFR
+  double eta;          // WFR length scale
   uint64_t seed;
   uint32_t pid;
 };
@@ -227,9 +233,32 @@ void launch_csc_sort_f32(int m, const int* col_ptr, const int* tmp_row, const in
 
 template <typename T> T* at(char* ws, size_t off) { return reinterpret_cast<T*>(ws + off); }
 
+// The binary32 decision factor K_ij^{eps/(2 lam + eps)} = exp(-C_ij/(2 lam + eps))
+// of Eq. (pij-uot) from the raw squared distance D.  Squared Euclidean:
+// E(-fl(D kappa)).  WFR (section 2.2): with z = fl(fl(sqrt D) fl(1/(2 eta))),
+// 0 for z >= fl(pi/2) (transport blocked), else cos_+^2 to the power
+// 1/(2 lam + eps) = E(fl(g2 L(cos z))), 0 when the spec cos is not positive.
+__device__ __forceinline__ float uot_factor(int wfr, float D, float kappa, float inv2eta, float g2) {
+  if (!wfr) return spec_exp(-__fmul_rn(D, kappa));
+  const float z = __fmul_rn(__fsqrt_rn(D), inv2eta);
+  if (!(z < (float)(0.5 * 3.14159265358979323846))) return 0.0f;
+  const float c = spec_cos(z);
+  if (!(c > 0.0f)) return 0.0f;
+  return spec_exp(__fmul_rn(g2, spec_log(c)));
+}
+
+// The Wasserstein-Fisher-Rao cost (section 2.2) of the value path from the
+// FP64 squared distance: -2 log cos(sqrt(D) / (2 eta)), +inf where the angle
+// reaches pi/2.
+__device__ __forceinline__ double wfr_cost64(double D, double eta) {
+  const double z = sqrt(D) / (2.0 * eta);
+  if (z >= 0.5 * 3.14159265358979323846) return __longlong_as_double(0x7ff0000000000000LL);
+  return -2.0 * log(cos(z));
+}
+
 // p*_ij before clipping at 1, in the binary32 decision spec.
-//   OT  (Eq. pij-ot):  fl(r_i c_j)
-//   UOT (Eq. pij-uot): fl(scale fl(fl(A_i B_j) E(-fl(D_ij kappa))))
+//   separable (Eq. pij-ot, or equal probabilities): fl(r_i c_j)
+//   UOT (Eq. pij-uot): fl(scale fl(fl(A_i B_j) F(D_ij))), F = uot_factor
 // D receives the binary32 raw cost when it is computed (UOT).
 template <bool UOT>
 __device__ __forceinline__ float pstar_raw(const ProbDev& pd, const SketchScalars& sc, float ri,
@@ -237,8 +266,16 @@ __device__ __forceinline__ float pstar_raw(const ProbDev& pd, const SketchScalar
   if (!UOT) return __fmul_rn(ri, colf[j]);
   const float Dij = raw32(pd.cv, i, j);
   *D = Dij;
-  const float w = __fmul_rn(__fmul_rn(ri, colf[j]), spec_exp(-__fmul_rn(Dij, sc.kappa32)));
+  const float f = uot_factor(pd.cost_kind == SPS_COST_WFR, Dij, sc.kappa32, sc.inv2eta32, sc.g2_32);
+  const float w = __fmul_rn(__fmul_rn(ri, colf[j]), f);
   return __fmul_rn(sc.scale32, w);
+}
+
+// The cost of the value path at a sampled element, C_ij in FP64: the WFR cost
+// of the FP64 distance, or the raw FP64 cost over its divisor.
+__device__ __forceinline__ double value_cost64(const ProbDev& pd, const SketchScalars& sc, int i, int j) {
+  const double D = raw64(pd.cv, i, j);
+  return pd.cost_kind == SPS_COST_WFR ? wfr_cost64(D, pd.eta) : D / sc.dn64;
 }
 
 }  // namespace sps

@@ -772,7 +772,8 @@ __global__ void __launch_bounds__(kThreads) k_obj_rows(ProbDev pd, const SketchS
         const float p = pstar_raw<UOT>(pd, sc, ri, colf, i, j, &D);
         const T ps = p < 1.0f ? (T)p : (T)1;
         T C;
-        if (sizeof(T) == 8) C = (T)(raw64(pd.cv, i, j) / sc.dn64);
+        if (pd.cost_kind == SPS_COST_WFR) C = (T)value_cost64(pd, sc, i, j);
+        else if (sizeof(T) == 8) C = (T)(raw64(pd.cv, i, j) / sc.dn64);
         else C = (T)__fdiv_rn(UOT ? D : raw32(pd.cv, i, j), sc.dn32);
         rtr += Tij * C;
         rne += Tij * (log(Tij) - (T)1);
@@ -1054,7 +1055,7 @@ void objective_vt(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& i
   const T* u = at<T>(ws, L.u);
   const T* v = at<T>(ws, L.v);
   const int nb = L.nblk_rows;
-  if (ic.uot)
+  if (!pd.sep)   // the template selects the decision rule of p* (Eq. pij-uot or separable)
     k_obj_rows<V, T, true><<<nb, kThreads, 0, st>>>(pd, sc, at<float>(ws, L.rowf), at<float>(ws, L.colf),
         at<int>(ws, L.row_ptr), at<int>(ws, L.col_idx), at<V>(ws, L.val), u, v, at<T>(ws, L.a_it), ctrl, part, nb);
   else

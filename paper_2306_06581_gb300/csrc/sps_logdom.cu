@@ -790,7 +790,8 @@ __global__ void __launch_bounds__(kT) k_log_obj_rows(ProbDev pd, const SketchSca
         float D = 0.0f;
         const float p = pstar_raw<UOT>(pd, sc, ri, colf, i, j, &D);
         const float ps = p < 1.0f ? p : 1.0f;
-        const float C = __fdiv_rn(UOT ? D : raw32(pd.cv, i, j), sc.dn32);
+        const float C = pd.cost_kind == SPS_COST_WFR ? (float)value_cost64(pd, sc, i, j)
+                                                     : __fdiv_rn(UOT ? D : raw32(pd.cv, i, j), sc.dn32);
         rtr += T * C;
         rne += T * (z - 1.0f);
         rlp += T * logf(ps);
@@ -931,7 +932,7 @@ sps_status launch_log_objective(const ProbDev& pd, const Layout& L, char* ws, co
   double* part = at<double>(ws, L.part);
   const int nb = L.nblk_rows;
   const SketchScalars* sc = at<SketchScalars>(ws, L.scal);
-  if (ic.uot)
+  if (!pd.sep)   // the template selects the decision rule of p* (Eq. pij-uot or separable)
     k_log_obj_rows<true><<<nb, kT, 0, st>>>(pd, sc, A, at<float>(ws, L.rowf), at<float>(ws, L.colf), Ap, Bp, part, nb);
   else
     k_log_obj_rows<false><<<nb, kT, 0, st>>>(pd, sc, A, at<float>(ws, L.rowf), at<float>(ws, L.colf), Ap, Bp, part, nb);

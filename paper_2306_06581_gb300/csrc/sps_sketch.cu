@@ -191,13 +191,18 @@ __global__ void k_scalars(ProbDev pd, SketchScalars* sc, Ctrl* ctrl, int stage) 
     }
     sc->dn32 = dn32;
     sc->dn64 = dn64;
-    if (!pd.is_ot) {
+    if (pd.cost_kind == SPS_COST_WFR) sc->inv2eta32 = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, pd.eta)));
+    if (pd.probs == SPS_PROBS_EQUAL) {
+      // equal probabilities p_ij = 1/(n m): r_i = fl(fl(s) fl(1/(n m))), c_j = 1
+      sc->scale32 = __double2float_rn(__ddiv_rn(1.0, __dmul_rn((double)pd.n, (double)pd.m)));
+    } else if (!pd.is_ot) {
       const double t = __dadd_rn(__dmul_rn(2.0, pd.lam), pd.eps);
       sc->gamma32 = __double2float_rn(__ddiv_rn(pd.lam, t));
       double dn = 1.0;
       if (pd.cost_norm == SPS_COST_MAXNORM && sc->dmax32 > 0.0f) dn = (double)sc->dmax32;
       else if (pd.cost_norm == SPS_COST_SCALE) dn = pd.cost_scale;
       sc->kappa32 = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(dn, t)));
+      sc->g2_32 = __double2float_rn(__ddiv_rn(2.0, t));
     }
   } else if (stage == 1) {
     sc->sum1 = exact_round(&sc->acc1);
@@ -219,6 +224,15 @@ __global__ void k_ot_factors(ProbDev pd, SketchScalars* sc, const float* a32, co
   const float s32 = sc->s32, sc32 = sc->scale32;
   for (int64_t i = tid; i < pd.n; i += stride) rowf[i] = __fmul_rn(__fmul_rn(s32, __fsqrt_rn(a32[i])), sc32);
   for (int64_t j = tid; j < pd.m; j += stride) colf[j] = __fsqrt_rn(b32[j]);
+}
+
+// Equal probabilities (the Rand-Sink control): r_i = fl(s32 fl(1/(n m))), c_j = 1.
+__global__ void k_eq_factors(ProbDev pd, SketchScalars* sc, float* rowf, float* colf) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const float r = __fmul_rn(sc->s32, sc->scale32);
+  for (int64_t i = tid; i < pd.n; i += stride) rowf[i] = r;
+  for (int64_t j = tid; j < pd.m; j += stride) colf[j] = 1.0f;
 }
 
 // UOT: A_i = exp(g log a_i), B_j = exp(g log b_j) in the binary32 spec.
@@ -460,7 +474,9 @@ sps_status launch_factors(const ProbDev& pd, const Layout& L, char* ws, cudaStre
   float* colf = at<float>(ws, L.colf);
   k_scalars<<<1, 32, 0, st>>>(pd, sc, ctrl, 0);
   const int g = grid_for(std::max(pd.n, pd.m), kThreads);
-  if (pd.is_ot) {
+  if (pd.probs == SPS_PROBS_EQUAL) {
+    k_eq_factors<<<g, kThreads, 0, st>>>(pd, sc, rowf, colf);
+  } else if (pd.is_ot) {
     k_ot_sqrt_sums<<<g, kThreads, 0, st>>>(pd, sc, a32, b32);
     k_scalars<<<1, 32, 0, st>>>(pd, sc, ctrl, 1);
     k_ot_factors<<<g, kThreads, 0, st>>>(pd, sc, a32, b32, rowf, colf);

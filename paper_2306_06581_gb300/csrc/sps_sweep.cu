@@ -58,14 +58,17 @@ struct SweepArgs {
 };
 
 template <typename V> struct ValMath;
+// K~_ij = K_ij / p*_ij of a sampled element; the WFR cost always goes through
+// FP64 (its slope grows without bound at the blocking edge d = pi eta).
 template <> struct ValMath<double> {
   __device__ static double value(const ProbDev& pd, const SketchScalars& sc, int i, int j, float, float ps) {
-    const double C = __ddiv_rn(raw64(pd.cv, i, j), sc.dn64);
+    const double C = pd.cost_kind == SPS_COST_WFR ? value_cost64(pd, sc, i, j) : __ddiv_rn(raw64(pd.cv, i, j), sc.dn64);
     return exp(-C / pd.eps) / (double)ps;
   }
 };
 template <typename V> struct ValMath {
   __device__ static double value(const ProbDev& pd, const SketchScalars& sc, int i, int j, float D, float ps) {
+    if (pd.cost_kind == SPS_COST_WFR) return exp(-value_cost64(pd, sc, i, j) / pd.eps) / (double)ps;
     const float C = __fdiv_rn(D, sc.dn32);
     return (double)(expf(-C / (float)pd.eps) / ps);
   }
@@ -83,6 +86,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
   float* ct = smem;           // [kTJ]
   float* yT = smem + kTJ;     // [d][kTJ]
   const float kappa = A.sc->kappa32, scale = A.sc->scale32;
+  const int wfr = pd.cost_kind == SPS_COST_WFR;
+  const float inv2eta = A.sc->inv2eta32, g2 = A.sc->g2_32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.y;
   const int jc0 = c * A.chunk;
@@ -97,7 +102,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
   if (blockDim.x != kSweepThreads) return;  // the row mapping assumes 8 warps
   // log K~ in binary32 arithmetic when the points are binary32 (no FP64 copy, no dense cost)
   const bool lv32 = (MODE == SW_FILL ? A.logval != nullptr : MODE == SW_FUSED ? A.pad_lv != nullptr : false) &&
-                    !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64;
+                    !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64 && pd.cost_kind != SPS_COST_WFR;
   float k_hi = 0.0f, k_lo = 0.0f;
   if (lv32) {
     const double k64 = 1.0 / (A.sc->dn64 * pd.eps);   // one division per block
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
               if (j + e < jc1) {
                 float p;
                 if (UOT) {
-                  const float w = __fmul_rn(__fmul_rn(ri, cv[e]), spec_exp(-__fmul_rn(Dv[e], kappa)));
+                  const float w = __fmul_rn(__fmul_rn(ri, cv[e]), uot_factor(wfr, Dv[e], kappa, inv2eta, g2));
                   if (MODE == SW_Z) { exact_add(acc, &A.sc->acc1, Bz, w); zr[r] += w; continue; }
                   p = __fmul_rn(scale, w);
                 } else {
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A) {
                     val[pos] = from_d<V>(ValMath<V>::value(pd, sc, i, jj, Dd, ps));
                     if (lvo) {
                       // log K~ = -C/eps - log p*, C from the FP64 distance of the points
-                      const double C64 = raw64(pd.cv, i, jj) / sc.dn64;
+                      const double C64 = value_cost64(pd, sc, i, jj);
                       lvo[pos] = (float)(-C64 / pd.eps - (double)logf(ps));
                     }
                   }
@@ -442,8 +447,9 @@ SweepGeo sweep_geometry(int n, int m) {
 // Skip sampler: the law of one Bernoulli(p*_ij) decision per element
 // (Eq. pois) with work proportional to the sampled count.  Row i bounds every
 // p_ij by q_i: OT (Eq. pij-ot) p_ij = fl(r_i c_j), q_i = min(1, fl(r_i cmax));
-// UOT (Eq. pij-uot) p_ij = fl(scale fl(fl(A_i B_j) E(-D_ij kappa))), q_i =
-// min(1, fl(scale fl(A_i cmax))) (E <= 1; rounding is monotone), cmax =
+// UOT (Eq. pij-uot) p_ij = fl(scale fl(fl(A_i B_j) F(D_ij))) with F the
+// decision factor of the cost (E(-D_ij kappa), or the WFR cos power), q_i =
+// min(1, fl(scale fl(A_i cmax))) (F <= 1; rounding is monotone), cmax =
 // max_j of the column factors.  Candidates form a Bernoulli(q_i) process generated by
 // geometric gaps G = floor(log U / log(1 - q_i)), U = ((w >> 8) + 1) 2^-24
 // on (0, 1]; a candidate j is kept when V < fl(p_ij / q_i), V = (w' >> 8)
@@ -474,7 +480,9 @@ __global__ void __launch_bounds__(256) k_skip(SweepArgs A) {
   const unsigned lt = (1u << lane) - 1u;
   const float cmax = A.sc->cmax32;
   const float kappa = A.sc->kappa32, scale = A.sc->scale32;
-  const bool lv32 = MODE == SK_FILL && A.logval != nullptr && !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64;
+  const int wfr = pd.cost_kind == SPS_COST_WFR;
+  const float inv2eta = A.sc->inv2eta32, g2 = A.sc->g2_32;
+  const bool lv32 = MODE == SK_FILL && A.logval != nullptr && !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64 && !wfr;
   float k_hi = 0.0f, k_lo = 0.0f;
   if (lv32) {
     const double k64 = 1.0 / (A.sc->dn64 * pd.eps);
@@ -535,7 +543,7 @@ __global__ void __launch_bounds__(256) k_skip(SweepArgs A) {
           float p;
           if (UOT) {
             Dv[e] = raw32(pd.cv, i, jj);
-            p = __fmul_rn(scale, __fmul_rn(__fmul_rn(r, A.colf[jj]), spec_exp(-__fmul_rn(Dv[e], kappa))));
+            p = __fmul_rn(scale, __fmul_rn(__fmul_rn(r, A.colf[jj]), uot_factor(wfr, Dv[e], kappa, inv2eta, g2)));
           } else {
             p = __fmul_rn(r, A.colf[jj]);
           }
@@ -570,7 +578,7 @@ __global__ void __launch_bounds__(256) k_skip(SweepArgs A) {
               reinterpret_cast<V*>(A.val)[wpos] =
                   from_d<V>(ValMath<V>::value(pd, *A.sc, i, jj, UOT ? Dv[e] : raw32(pd.cv, i, jj), ps));
               if (A.logval) {
-                const double C64 = raw64(pd.cv, i, jj) / A.sc->dn64;
+                const double C64 = value_cost64(pd, *A.sc, i, jj);
                 A.logval[wpos] = (float)(-C64 / pd.eps - (double)logf(ps));
               }
             }
@@ -625,7 +633,7 @@ void launch_count(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st)
   A.col_cnt = at<int>(ws, L.col_cnt);
   const SweepGeo g = sweep_geometry(pd.n, pd.m);
   const dim3 grid(g.row_blocks, g.nchunk);
-  if (pd.is_ot) launch_sweep<SW_COUNT, false, float>(A, grid, st);
+  if (pd.sep) launch_sweep<SW_COUNT, false, float>(A, grid, st);
   else launch_sweep<SW_COUNT, true, float>(A, grid, st);
   k_sum_chunks<<<std::max(1, std::min(1216, (pd.n + 255) / 256)), 256, 0, st>>>(pd.n, g.nchunk, A.cnt2,
                                                                                  at<int>(ws, L.row_cnt), A.ctrl);
@@ -644,7 +652,7 @@ static void fill_v(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st
   A.tmp_src = at<int>(ws, L.tmp_src);
   const SweepGeo g = sweep_geometry(pd.n, pd.m);
   const dim3 grid(g.row_blocks, g.nchunk);
-  if (pd.is_ot) launch_sweep<SW_FILL, false, V>(A, grid, st);
+  if (pd.sep) launch_sweep<SW_FILL, false, V>(A, grid, st);
   else launch_sweep<SW_FILL, true, V>(A, grid, st);
 }
 
@@ -663,10 +671,10 @@ static void fused_v(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t s
   const SweepGeo g = sweep_geometry(pd.n, pd.m);
   const long long len = (long long)pd.n * g.nchunk;
   int* caps = at<int>(ws, L.pad_ofs) + len + 1;   // scratch after the offsets
-  if (pd.is_ot)
+  if (pd.sep)
     k_chunk_csum<<<std::min(g.nchunk, 1024), 256, 0, st>>>(pd.m, g.chunk, g.nchunk, A.colf, at<float>(ws, L.csum));
   const int gc = (int)std::max<long long>(1, std::min<long long>(4096, (len + 255) / 256));
-  k_pad_caps<<<gc, 256, 0, st>>>(pd.n, pd.m, g.chunk, g.nchunk, pd.is_ot ? 0 : 1, A.rowf, at<float>(ws, L.csum),
+  k_pad_caps<<<gc, 256, 0, st>>>(pd.n, pd.m, g.chunk, g.nchunk, pd.sep ? 0 : 1, A.rowf, at<float>(ws, L.csum),
                                  L.zsum ? at<float>(ws, L.zsum) : nullptr, A.sc, caps);
   k_pad_scan<<<1, 1024, 0, st>>>(caps, at<int>(ws, L.pad_ofs), len, (long long)L.pad_cap, A.ctrl);
   A.col_cnt = at<int>(ws, L.col_cnt);
@@ -675,7 +683,7 @@ static void fused_v(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t s
   A.pad_val = ws + L.pad_val;
   A.pad_lv = L.pad_lv ? at<float>(ws, L.pad_lv) : nullptr;
   const dim3 grid(g.row_blocks, g.nchunk);
-  if (pd.is_ot) launch_sweep<SW_FUSED, false, V>(A, grid, st);
+  if (pd.sep) launch_sweep<SW_FUSED, false, V>(A, grid, st);
   else launch_sweep<SW_FUSED, true, V>(A, grid, st);
 }
 
@@ -727,7 +735,7 @@ static void skip_fill_v(const ProbDev& pd, const Layout& L, char* ws, int grid, 
   A.logval = L.logval ? at<float>(ws, L.logval) : nullptr;
   A.tmp_row = at<int>(ws, L.tmp_row);
   A.tmp_src = at<int>(ws, L.tmp_src);
-  if (pd.is_ot) k_skip<SK_FILL, false, V><<<grid, 256, 0, st>>>(A);
+  if (pd.sep) k_skip<SK_FILL, false, V><<<grid, 256, 0, st>>>(A);
   else k_skip<SK_FILL, true, V><<<grid, 256, 0, st>>>(A);
 }
 
@@ -738,7 +746,7 @@ sps_status launch_skip_sample(const ProbDev& pd, const Layout& L, char* ws, sps_
   const int grid = std::max(1, std::min(152 * 8, (pd.n + 7) / 8));   // one warp per row
   cudaMemsetAsync(A.col_cnt, 0, sizeof(int) * (size_t)pd.m, st);
   k_colf_max<<<std::max(1, std::min(1024, (pd.m + 255) / 256)), 256, 0, st>>>(A.colf, pd.m, A.sc);
-  if (pd.is_ot) k_skip<SK_COUNT, false, float><<<grid, 256, 0, st>>>(A);
+  if (pd.sep) k_skip<SK_COUNT, false, float><<<grid, 256, 0, st>>>(A);
   else k_skip<SK_COUNT, true, float><<<grid, 256, 0, st>>>(A);
   launch_scan_counts(A.cnt_row, at<int>(ws, L.row_ptr), pd.n, A.col_cnt, at<int>(ws, L.col_ptr),
                      at<int>(ws, L.col_cur), pd.m, (long long)L.cap, A.ctrl, st);

@@ -30,6 +30,8 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "ERR_INVALID_ARG", 3: "ERR_WORKS
 F64, F32, BF16, F16 = 0, 1, 2, 3
 DTYPE_CODES = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
 COST_RAW, COST_MAXNORM, COST_SCALE = 0, 1, 2
+COST_KINDS = {"sqeuclid": 0, "wfr": 1}
+PROBS = {"paper": 0, "equal": 1}
 STOP_RESIDUAL, STOP_DELTA_UV = 0, 1
 OP_SPARSIFY, OP_SPAR_SINK, OP_DENSE = 0, 1, 2
 
@@ -43,7 +45,7 @@ class SpsError(RuntimeError):
 class Problem(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("d", C.c_int32), ("x", C.c_void_p), ("y", C.c_void_p),
                 ("C", C.c_void_p), ("cost_norm", C.c_int32), ("cost_scale", C.c_double), ("a", C.c_void_p),
-                ("b", C.c_void_p), ("dtype", C.c_int32)]
+                ("b", C.c_void_p), ("dtype", C.c_int32), ("cost_kind", C.c_int32), ("eta", C.c_double)]
 
 
 class Params(C.Structure):
@@ -52,7 +54,7 @@ class Params(C.Structure):
                 ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("kdtype", C.c_int32),
                 ("log_domain", C.c_int32), ("absorb_tau", C.c_double), ("init_alpha", C.c_void_p),
                 ("init_beta", C.c_void_p), ("gather_mode", C.c_int32), ("sketch_mode", C.c_int32),
-                ("sampler", C.c_int32)]
+                ("sampler", C.c_int32), ("probs", C.c_int32)]
 
 GATHER_AUTO, GATHER_DIRECT, GATHER_STAGED = 0, 1, 2
 
@@ -133,8 +135,11 @@ class Marshalled:
     keep: tuple
 
 
-def make_problem(a, b, x=None, y=None, C_=None, dtype="f32", cost_norm=COST_MAXNORM, cost_scale=1.0, device=None):
-    """Device copies of the inputs in `dtype` and the sps_problem struct."""
+def make_problem(a, b, x=None, y=None, C_=None, dtype="f32", cost_norm=COST_MAXNORM, cost_scale=1.0, device=None,
+                 cost_kind="sqeuclid", eta=0.0):
+    """Device copies of the inputs in `dtype` and the sps_problem struct.
+    cost_kind "wfr" is the Wasserstein-Fisher-Rao cost with length scale eta
+    (points, raw cost: cost_norm = COST_RAW)."""
     device = torch.device("cuda") if device is None else torch.device(device)
     tdt = torch.float64 if dtype == "f64" else torch.float32
     a, b = _dev(a, tdt, device), _dev(b, tdt, device)
@@ -142,7 +147,8 @@ def make_problem(a, b, x=None, y=None, C_=None, dtype="f32", cost_norm=COST_MAXN
     n, m = a.numel(), b.numel()
     d = 0 if x is None else (x.shape[1] if x.dim() == 2 else 1)
     p = Problem(n, m, d, _ptr(x), _ptr(y), _ptr(C_), cost_norm, float(cost_scale), _ptr(a), _ptr(b),
-                F64 if dtype == "f64" else F32)
+                F64 if dtype == "f64" else F32, COST_KINDS[cost_kind] if isinstance(cost_kind, str) else int(cost_kind),
+                float(eta))
     return Marshalled(p, (a, b, x, y, C_))
 
 
@@ -151,11 +157,12 @@ SAMPLERS = {"element": 0, "skip": 1}
 
 def make_params(eps, lam=math.inf, s=1.0, tol=1e-6, max_iter=1000, check_every=0, stop_rule=STOP_RESIDUAL,
                 seed=0x5EED, problem_id=0, kdtype="f32", log_domain=0, absorb_tau=0.0, init_alpha=None,
-                init_beta=None, gather_mode=GATHER_AUTO, sketch_mode=0, sampler="element"):
+                init_beta=None, gather_mode=GATHER_AUTO, sketch_mode=0, sampler="element", probs="paper"):
     return Params(float(eps), float(lam), float(s), float(tol), int(max_iter), int(check_every), int(stop_rule),
                   int(seed) & ((1 << 64) - 1), int(problem_id), DTYPE_CODES[kdtype] if isinstance(kdtype, str) else kdtype,
                   int(log_domain), float(absorb_tau), _ptr(init_alpha), _ptr(init_beta), int(gather_mode),
-                  int(sketch_mode), SAMPLERS[sampler] if isinstance(sampler, str) else int(sampler))
+                  int(sketch_mode), SAMPLERS[sampler] if isinstance(sampler, str) else int(sampler),
+                  PROBS[probs] if isinstance(probs, str) else int(probs))
 
 
 def sps_workspace_bytes(prob: Problem, prm: Params, op: int) -> int:
@@ -205,33 +212,36 @@ def _solve(fn_name, prob: Problem, prm: Params, device, op, workspace=None, rais
 def spar_sink_ot(a, b, x=None, y=None, C_=None, *, eps, s, tol=1e-6, max_iter=1000, dtype="f32", kdtype=None,
                  seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL,
                  check_every=0, init_alpha=None, init_beta=None, log_domain=0, absorb_tau=0.0, gather_mode=0, sketch_mode=0, workspace=None,
-                 device=None, raise_on_error=True, sampler="element"):
+                 device=None, raise_on_error=True, sampler="element", cost_kind="sqeuclid", eta=0.0, probs="paper"):
     """Alg. 3: importance-sparsified Sinkhorn for balanced OT.  sampler="skip"
     draws the sketch by geometric gaps with thinning (work proportional to the
-    sampled count; the same law as the per-element decisions)."""
-    M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
+    sampled count; the same law as the per-element decisions).  probs="equal"
+    samples every element with p_ij = 1/(n m) (the Rand-Sink control)."""
+    M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device, cost_kind, eta)
     dev = M.keep[0].device
     kd = kdtype or dtype
     it = torch.float64 if kd == "f64" else torch.float32
     ia, ib = _dev(init_alpha, it, dev), _dev(init_beta, it, dev)
     prm = make_params(eps, math.inf, s, tol, max_iter, check_every, stop_rule, seed, problem_id, kd, log_domain,
-                      absorb_tau, ia, ib, gather_mode, sketch_mode, sampler)
+                      absorb_tau, ia, ib, gather_mode, sketch_mode, sampler, probs)
     return _solve("spar_sink_ot", M.prob, prm, dev, OP_SPAR_SINK, workspace, raise_on_error)
 
 
 def spar_sink_uot(a, b, x=None, y=None, C_=None, *, eps, lam, s, tol=1e-6, max_iter=1000, dtype="f32", kdtype=None,
                   seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, stop_rule=STOP_RESIDUAL,
                   check_every=0, init_alpha=None, init_beta=None, log_domain=0, absorb_tau=0.0, gather_mode=0, sketch_mode=0, workspace=None,
-                  device=None, raise_on_error=True, sampler="element"):
+                  device=None, raise_on_error=True, sampler="element", cost_kind="sqeuclid", eta=0.0, probs="paper"):
     """Alg. 4: importance-sparsified Sinkhorn for UOT with KL penalty lam.
-    sampler="skip" draws the sketch by geometric gaps with thinning."""
-    M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
+    sampler="skip" draws the sketch by geometric gaps with thinning;
+    cost_kind="wfr" uses the Wasserstein-Fisher-Rao cost (length scale eta,
+    cost_norm=COST_RAW); probs="equal" samples with p_ij = 1/(n m)."""
+    M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device, cost_kind, eta)
     dev = M.keep[0].device
     kd = kdtype or dtype
     it = torch.float64 if kd == "f64" else torch.float32
     ia, ib = _dev(init_alpha, it, dev), _dev(init_beta, it, dev)
     prm = make_params(eps, lam, s, tol, max_iter, check_every, stop_rule, seed, problem_id, kd, log_domain,
-                      absorb_tau, ia, ib, gather_mode, sketch_mode, sampler)
+                      absorb_tau, ia, ib, gather_mode, sketch_mode, sampler, probs)
     return _solve("spar_sink_uot", M.prob, prm, dev, OP_SPAR_SINK, workspace, raise_on_error)
 
 
@@ -253,12 +263,13 @@ _NP_DT = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: tor
 
 def sparsify_kernel(a, b, x=None, y=None, C_=None, *, eps, s, lam=math.inf, dtype="f32", kdtype=None, seed=0x5EED,
                     problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, sketch_mode=0, workspace=None,
-                    device=None, sampler="element"):
+                    device=None, sampler="element", cost_kind="sqeuclid", eta=0.0, probs="paper"):
     """Eq. (pois) sketch K~ as CSR + CSC tensor views (copied out of the workspace)."""
-    M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device)
+    M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device, cost_kind, eta)
     dev = M.keep[0].device
     kd = kdtype or dtype
-    prm = make_params(eps, lam, s, 0.0, 1, 0, 0, seed, problem_id, kd, sketch_mode=sketch_mode, sampler=sampler)
+    prm = make_params(eps, lam, s, 0.0, 1, 0, 0, seed, problem_id, kd, sketch_mode=sketch_mode, sampler=sampler,
+                      probs=probs)
     nbytes = sps_workspace_bytes(M.prob, prm, OP_SPARSIFY)
     if nbytes == 0:
         raise SpsError(SPS_ERR_INVALID_ARG, last_error())

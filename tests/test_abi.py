@@ -255,3 +255,41 @@ def test_every_declaration_is_documented():
             assert "*/" in above, f"{fn}: {m.group(1)} has no comment above its declaration"
             seen.add(m.group(1))
     assert seen == _declared_functions()
+
+
+def _wfr_prob(S, eta=0.5, cost_norm=0, with_C=False, kind=1):
+    fake = C.c_void_p(256)
+    return S.Problem(100, 120, 3, fake, fake, fake if with_C else None, cost_norm, 1.0, fake, fake, 1, kind, eta)
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(kind=7), "cost_kind"), (dict(eta=0.0), "eta"), (dict(eta=float("inf")), "eta"),
+    (dict(eta=float("nan")), "eta"), (dict(cost_norm=1), "cost_norm"), (dict(with_C=True), "points"),
+])
+def test_wfr_arguments_validated(S, kw, frag):
+    Q = S.make_params(0.1, 1.0, 1000.0)
+    assert S.sps_workspace_bytes(_wfr_prob(S, **kw), Q, 1) == 0
+    assert frag in S.last_error()
+
+
+def test_wfr_accepted_for_the_sketch_and_refused_by_dense(S):
+    Q = S.make_params(0.1, 1.0, 1000.0)
+    assert S.sps_workspace_bytes(_wfr_prob(S), Q, 0) > 0
+    assert S.sps_workspace_bytes(_wfr_prob(S), Q, 1) > 0
+    assert S.sps_workspace_bytes(_wfr_prob(S), Q, 2) == 0
+    assert "dense" in S.last_error()
+
+
+def test_probs_validated(S):
+    P = _prob(S)
+    assert S.sps_workspace_bytes(P, S.make_params(0.1, 1.0, 1000.0, probs=2), 1) == 0
+    assert "probs" in S.last_error()
+    for probs in ("paper", "equal"):
+        assert S.sps_workspace_bytes(P, S.make_params(0.1, 1.0, 1000.0, probs=probs), 1) > 0
+
+
+def test_batch_refuses_equal_probabilities(S):
+    Q = S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f32", probs="equal")
+    B, keep = _batch(S)
+    assert _batch_bytes(S, B, Q) == 0
+    assert "probs" in S.last_error()
