@@ -319,6 +319,50 @@ sps_status spar_sink_batched(const sps_batch* batch, const sps_params* prm, sps_
                              size_t ws_bytes, void* alpha_out, void* beta_out, sps_result* res,
                              sps_stream stream);
 
+/* ---------------- Wasserstein barycenters (Spar-IBP) ----------------
+ * The fixed-support barycenter q of M measures b_1 .. b_M on one support x
+ * (n points): the minimiser of sum_k w_k OT_eps(q, b_k), by the iterative
+ * Bregman projections (IBP) of the paper's appendix run on sketches.  Spar-IBP
+ * (the appendix's algorithm): every Gibbs kernel K_k = exp(-C / eps) of the
+ * shared cost C (squared Euclidean on x, normalised by cost_norm) is replaced
+ * by its sketch of Eq. (pois) with p_{k,ij} = sqrt(b_{k,j}) / (n sum_j
+ * sqrt(b_{k,j})) -- Eq. (pij-ot) with the uniform source a = 1/n -- drawn
+ * with Philox problem id prm->problem_id + k.  From q^0 = 1/n and u_k = 1,
+ * every iteration forms v_k = b_k / (K~_k^T u_k), then q = prod_k (K~_k
+ * v_k)^{w_k}, then u_k = q / (K~_k v_k) (the order of the cited IBP: as
+ * printed, the listing forms u_k from the previous q, which leaves a common
+ * scale of the u_k oscillating), and stops when ||q^t - q^{t-1}||_1 <= tol.
+ * An empty row of a sketch gives q_i = 0 and u_{k,i} = 0; an empty column gives
+ * v_{k,j} = 0.  A budget s at least 1 / min p_ij keeps every element and the
+ * iterations are those of IBP on the dense kernels. */
+typedef struct {
+  int32_t n, d;         /* support size and dimension */
+  int32_t n_measures;   /* M, 1 .. 64 */
+  const void* x;        /* device, n*d row-major, dtype: the shared support */
+  const void* b;        /* device, M*n, dtype: measure k in b[k n .. (k+1) n), b >= 0 */
+  const double* w;      /* host, M weights: finite, >= 0, summing to 1 within 1e-9 */
+  int32_t cost_norm;    /* SPS_COST_*: of the squared Euclidean cost on x */
+  double cost_scale;    /* divisor for SPS_COST_SCALE */
+  sps_dtype dtype;      /* SPS_F32 or SPS_F64: type of x and b */
+} sps_barycenter;
+
+/* Workspace bytes of spar_ibp (0 and an error message on invalid arguments).
+ * prm: eps, s (the budget of every sketch), tol, max_iter, seed, problem_id,
+ * kdtype (F64 iterates in FP64, F32 / BF16 / F16 values iterate in FP32) and
+ * sampler are used; lambda must be +INFINITY, log_domain 0, probs
+ * SPS_PROBS_PAPER, stop_rule SPS_STOP_RESIDUAL (here: the ||q^t - q^{t-1}||_1
+ * rule of the appendix). */
+size_t sps_ibp_workspace_bytes(const sps_barycenter* bar, const sps_params* prm);
+
+/* Spar-IBP (the appendix's Spar-IBP algorithm, after Benamou et al. 2015):
+ * writes the barycenter q (n, iterate type: double for kdtype F64, else
+ * float) to q_out (device).  res (host, optional): iters, residual =
+ * ||q^t - q^{t-1}||_1 of the returned q, nnz = total elements of the M
+ * sketches, ms_sketch / ms_iter, status (SPS_OK or SPS_NOT_CONVERGED; other
+ * fields 0).  Synchronises the stream.  Errors as for spar_sink_ot. */
+sps_status spar_ibp(const sps_barycenter* bar, const sps_params* prm, void* ws, size_t ws_bytes, void* q_out,
+                    sps_result* res, sps_stream stream);
+
 /* ---------------- learned warm start ----------------
  * The paper starts the scaling iterations from u = v = 1 (Alg. 1, Alg. 2).
  * These entry points predict starting potentials instead, with one small

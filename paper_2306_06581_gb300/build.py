@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsparsink.so")
 SOURCES = ["sps_sketch.cu", "sps_iter.cu", "sps_dense.cu", "sps_api.cu", "sps_noalloc.cu", "sps_sweep.cu", "sps_logdom.cu",
-           "sps_dense_lse.cu", "sps_batch.cu", "sps_mlp.cu", "sps_costmax.cu", "sps_selftest.cu"]
+           "sps_dense_lse.cu", "sps_batch.cu", "sps_mlp.cu", "sps_costmax.cu", "sps_selftest.cu", "sps_ibp.cu"]
 HEADERS = ["sps_device.cuh", "sps_internal.h", "sps_iterdev.cuh", "sps_dense.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

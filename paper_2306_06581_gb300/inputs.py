@@ -213,3 +213,21 @@ def mlp_weights(d, seed, scale=1.0):
 def ot_gmm16(n, seed, eps=0.01):
     """The 16-component mixture family in R^3 (balanced OT, s = 16 n ln n)."""
     return ot_gmm(n, 3, 16, seed, eps, 16.0, 1e-5, "f32", name=f"ot_n{n}_d3_gmm16_seed{seed}")
+
+
+def ibp_measures(n):
+    """The synthetic barycenter recipe of the paper's appendix on a 1-D grid of
+    n points (i + 0.5) / n: a Gaussian N(0.2, 1/50), an equal mixture of
+    N(0.5, 1/60) and N(0.8, 1/80), and a t density with 5 degrees of freedom
+    at 0.6 with scale sqrt(1/100); each plus 1e-2 of its maximum, normalised.
+    Returns (grid points n x 1, [b_1, b_2, b_3])."""
+    from scipy import stats
+    g = (np.arange(n) + 0.5) / n
+    b1 = stats.norm.pdf(g, 0.2, math.sqrt(1 / 50))
+    b2 = 0.5 * stats.norm.pdf(g, 0.5, math.sqrt(1 / 60)) + 0.5 * stats.norm.pdf(g, 0.8, math.sqrt(1 / 80))
+    b3 = stats.t.pdf((g - 0.6) / math.sqrt(1 / 100), 5)
+    out = []
+    for b in (b1, b2, b3):
+        b = b + 1e-2 * b.max()
+        out.append(b / b.sum())
+    return g.reshape(-1, 1), out

@@ -326,6 +326,57 @@ def version() -> str:
 
 
 # ---------------------------------------------------------------------------
+# Wasserstein barycenters (Spar-IBP)
+# ---------------------------------------------------------------------------
+
+class Barycenter(C.Structure):
+    _fields_ = [("n", C.c_int32), ("d", C.c_int32), ("n_measures", C.c_int32), ("x", C.c_void_p),
+                ("b", C.c_void_p), ("w", C.c_void_p), ("cost_norm", C.c_int32), ("cost_scale", C.c_double),
+                ("dtype", C.c_int32)]
+
+
+def spar_ibp(x, bs, w, *, eps, s, tol=1e-9, max_iter=10000, dtype="f64", kdtype=None, seed=0x5EED, problem_id=0,
+             cost_norm=COST_MAXNORM, cost_scale=1.0, sampler="element", check_every=0, workspace=None, device=None,
+             raise_on_error=True):
+    """Spar-IBP barycenter of the measures bs (M x n) on the shared support x
+    (n x d) with weights w (summing to 1): IBP on the sketches of Eq. (pois)
+    with Eq. (pij-ot) for a = 1/n, measure k drawn with problem id
+    problem_id + k.  Returns q (iterate type) and the solve's counters."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    dt = torch.float64 if dtype == "f64" else torch.float32
+    xd = _dev(x, dt, dev)
+    if xd.dim() == 1:
+        xd = xd.reshape(-1, 1).contiguous()
+    bd = _dev(bs, dt, dev).reshape(-1, xd.shape[0]).contiguous()
+    M, n = bd.shape
+    wh = np.ascontiguousarray(np.asarray(w, np.float64).reshape(M))
+    kd = kdtype or dtype
+    B = Barycenter(n, xd.shape[1], M, _ptr(xd), _ptr(bd), wh.ctypes.data, int(cost_norm), float(cost_scale),
+                   F64 if dtype == "f64" else F32)
+    prm = make_params(eps, math.inf, s, tol, max_iter, check_every, STOP_RESIDUAL, seed, problem_id, kd,
+                      sampler=sampler)
+    L = lib()
+    L.sps_ibp_workspace_bytes.argtypes = [C.c_void_p, C.c_void_p]
+    L.sps_ibp_workspace_bytes.restype = C.c_size_t
+    L.spar_ibp.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.spar_ibp.restype = C.c_int
+    nbytes = L.sps_ibp_workspace_bytes(C.byref(B), C.byref(prm))
+    if nbytes == 0:
+        raise SpsError(SPS_ERR_INVALID_ARG, last_error())
+    ws = _workspace(nbytes, dev, workspace)
+    q = torch.empty(n, dtype=torch.float64 if kd == "f64" else torch.float32, device=dev)
+    res = Result()
+    st = L.spar_ibp(C.byref(B), C.byref(prm), _ptr(ws), nbytes, _ptr(q), C.byref(res), _stream())
+    if raise_on_error:
+        _check(st)
+    out = res.as_dict()
+    out["status_code"] = st
+    out["q"] = q
+    out["workspace"] = ws
+    return out
+
+
+# ---------------------------------------------------------------------------
 # batches of problems over shared point sets
 # ---------------------------------------------------------------------------
 

@@ -293,3 +293,35 @@ def test_batch_refuses_equal_probabilities(S):
     B, keep = _batch(S)
     assert _batch_bytes(S, B, Q) == 0
     assert "probs" in S.last_error()
+
+
+def _bary(S, n=50, M=3, w=None, d=1, dtype=1):
+    import numpy as np
+    wh = np.ascontiguousarray(np.asarray(w if w is not None else [1.0 / max(M, 1)] * max(M, 1), np.float64))
+    fake = C.c_void_p(256)
+    return S.Barycenter(n, d, M, fake, fake, wh.ctypes.data, 1, 1.0, dtype), wh
+
+
+def _ibp_bytes(S, B, Q):
+    f = S.lib().sps_ibp_workspace_bytes
+    f.argtypes = [C.c_void_p, C.c_void_p]
+    f.restype = C.c_size_t
+    return int(f(C.byref(B), C.byref(Q)))
+
+
+def test_ibp_arguments_validated(S):
+    Q = S.make_params(0.05, math.inf, 500.0, 1e-9, 100, kdtype="f64")
+    B, keep = _bary(S)
+    assert _ibp_bytes(S, B, Q) > 0
+    for kw, frag in ((dict(M=0), "n_measures"), (dict(M=65), "n_measures"), (dict(w=[0.5, 0.6, -0.1]), "w[2]"),
+                     (dict(w=[0.2, 0.2, 0.2]), "sum to 1"), (dict(n=0), "support"), (dict(dtype=2), "dtype")):
+        B, keep = _bary(S, **kw)
+        assert _ibp_bytes(S, B, Q) == 0, kw
+        assert frag in S.last_error(), (kw, S.last_error())
+    B, keep = _bary(S)
+    for q, frag in ((S.make_params(0.05, 1.0, 500.0, kdtype="f64"), "lambda"),
+                    (S.make_params(0.05, math.inf, 500.0, kdtype="f32", log_domain=1), "log_domain"),
+                    (S.make_params(0.05, math.inf, 500.0, probs="equal"), "probs"),
+                    (S.make_params(-1.0, math.inf, 500.0), "eps")):
+        assert _ibp_bytes(S, B, q) == 0
+        assert frag in S.last_error(), (frag, S.last_error())
