@@ -168,7 +168,19 @@ typedef struct {
   float ms_sketch, ms_iter, ms_obj; /* device time of the three phases */
   int32_t launches;    /* kernels this call launched (including iterations enqueued after the stop flag) */
   int32_t iters_enqueued; /* iterations enqueued (>= iters; the surplus returned at once) */
+  int32_t gather;      /* how the iterations read the sketch: SPS_PASS_* below */
 } sps_result;
+
+/* sps_result.gather.  DIRECT: every product gathers the scaling vector from
+   global memory (CSR / CSC order).  STAGED (log_domain, long vectors): the
+   vector passes through shared memory chunk by chunk and the sketch is read
+   from a copy grouped by chunk (runs of 32 rows sorted by length, 16-bit
+   chunk-local indices).  STAGED_FALLBACK: staging was planned but the grouped
+   copy did not fit its planned space (a sketch with very uneven runs), so the
+   products gathered directly; the results are the same up to rounding. */
+#define SPS_PASS_DIRECT 0
+#define SPS_PASS_STAGED 1
+#define SPS_PASS_STAGED_FALLBACK 2
 
 /* Views of a sketch inside the workspace (filled by sparsify_kernel). */
 typedef struct {

@@ -44,13 +44,17 @@ static int64_t sketch_capacity(const sps_problem* P, const sps_params* Q) {
 // too long to stay in L1 (2^16 entries and more), every block streams the
 // gathered vector through shared memory in chunks of W entries, one block per
 // SM.  W is the largest multiple of 1024 (at most 48K entries) that leaves room
-// for the block's own row sums, balanced over the chunks.
+// for the block's own row sums and its warps' stream rings, balanced over the
+// chunks.  The sketch is read
+// from a grouped copy per pass (runs of 32 rows sorted by length, 16-bit
+// chunk-local indices); its size depends on the run lengths, so it is planned
+// generously and, when a sketch does not fit, the passes gather directly.
 constexpr int kStageMin = 1 << 16;
 constexpr int kStageWMax = 48 * 1024;
 constexpr size_t kStageSmem = 227 * 1024 - 1024;   // dynamic shared memory of one block
 
 template <typename Take>
-static void plan_staging(int n, int m, int mode, Layout* L, Take& take) {
+static void plan_staging(int n, int m, int mode, int kd, Layout* L, Take& take) {
   if (mode == SPS_GATHER_DIRECT) return;
   if (mode == SPS_GATHER_AUTO && (n < kStageMin || m < kStageMin)) return;
   if (L->cap <= 0) return;
@@ -62,9 +66,10 @@ static void plan_staging(int n, int m, int mode, Layout* L, Take& take) {
   }
   const int big = std::max(n, m);
   const size_t acc = (size_t)((big + nsm - 1) / nsm);   // row sums of one block
-  if (acc * 4 + 16 + 8192 * 4 > kStageSmem) return;
-  if (acc >= 65536) return;   // the chunk-major copy packs block-local rows into 16 bits
-  const int wcap = std::min<int>(kStageWMax, (int)(((kStageSmem - acc * 4 - 16) / 4) / 1024 * 1024));
+  if (ell_smem_bytes(8192, (int)acc) > kStageSmem) return;
+  if (acc >= 65535) return;   // the grouped copy names block-local rows in 16 bits (0xFFFF: none)
+  const size_t fixed = ell_smem_bytes(0, (int)acc) + 128;   // row sums, rings, alignment
+  const int wcap = std::min<int>(kStageWMax, (int)(((kStageSmem - fixed) / 4) / 1024 * 1024));
   int J = (big + wcap - 1) / wcap;
   if (mode == SPS_GATHER_STAGED) J = std::max(J, std::min(4, (big + 1023) / 1024));   // forced: several chunks
   const int W = (int)(((big + J - 1) / J + 1023) / 1024 * 1024);
@@ -72,17 +77,33 @@ static void plan_staging(int n, int m, int mode, Layout* L, Take& take) {
   L->stage_jr = (m + W - 1) / W;
   L->stage_jc = (n + W - 1) / W;
   L->stage_nsm = nsm;
+  const int vb = (kd == SPS_BF16 || kd == SPS_F16) ? 2 : 4;   // the stabilised passes store K' in 16 or 32 bits
+  L->stage_vb = vb;
   L->seg_r = take((size_t)(L->stage_jr + 1) * n * 4);
   L->seg_c = take((size_t)(L->stage_jc + 1) * m * 4);
-  L->cm_ofs_r = take((size_t)L->stage_jr * (n + 1) * 4);
-  L->cm_ofs_c = take((size_t)L->stage_jc * (m + 1) * 4);
-  L->cm_base_r = take((size_t)(L->stage_jr + 1) * 4);
-  L->cm_base_c = take((size_t)(L->stage_jc + 1) * 4);
-  // + 8 entries: the streaming pass reads whole aligned groups of 8 past the last element
-  L->cm_idx_r = take(((size_t)L->cap + 8) * 4);
-  L->cm_idx_c = take(((size_t)L->cap + 8) * 4);
-  L->cm_perm_r = take((size_t)L->cap * 4);
-  L->cm_perm_c = take((size_t)L->cap * 4);
+  const size_t parts[2] = {(size_t)nsm * kEllWarps * L->stage_jr, (size_t)nsm * kEllWarps * L->stage_jc};
+  const int rows[2] = {n, m};
+  // A part's groups are sorted, so each group's height is at most the shortest
+  // run of the group before it: a part holds at most its elements plus 32 x
+  // its longest run h0 of (2 + vb)-byte steps, and a header per 32 runs plus
+  // one.  The plan takes h0 <= 3 x the mean run + 16 (sketches of independent
+  // inclusions stay far below; a sketch that does not fit falls back to
+  // direct gathers).
+  int64_t need = 0;
+  for (int s = 0; s < 2; ++s) {
+    const int J = s ? L->stage_jc : L->stage_jr;
+    const int64_t h0 = 3 * ((L->cap + (int64_t)rows[s] * J - 1) / ((int64_t)rows[s] * J)) + 16;
+    need = std::max<int64_t>(need, (int64_t)(2 + vb + 3) * L->cap + (int64_t)parts[s] * (kEllHdr + 32 * (2 + vb) * h0));
+  }
+  L->el_pack_cap = (need + 15) & ~(int64_t)15;
+  for (int s = 0; s < 2; ++s) {
+    L->el_slice[s] = take((size_t)nsm * (kEllWarps + 1) * 4);
+    L->el_pbytes[s] = take(parts[s] * 8);
+    L->el_poff[s] = take((parts[s] + 1) * 8);
+    L->el_tmp[s] = take((size_t)rows[s] * 12);
+    L->el_perm[s] = take((size_t)L->cap * 4);
+    L->el_pack[s] = take((size_t)L->el_pack_cap);
+  }
 }
 
 bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
@@ -180,7 +201,7 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
       L->ecol = take((size_t)m * 4);
       L->pot_a = take((size_t)n * 4);
       L->pot_b = take((size_t)m * 4);
-      if (op == SPS_OP_SPAR_SINK) plan_staging(n, m, Q->gather_mode, L, take);
+      if (op == SPS_OP_SPAR_SINK) plan_staging(n, m, Q->gather_mode, Q->kdtype, L, take);
     }
   }
   L->nblk_rows = nb;
@@ -457,6 +478,8 @@ static sps_status spar_sink_impl(const sps_problem* P, const sps_params* Q, void
   SPS_TRY(cuda_fail(cudaStreamSynchronize(st), "stream synchronize"));
   sps_result r;
   fill_result(&r, dr, h, Q, nnz);
+  r.gather = (ic.log_domain && L.stage_w > 0) ? (h.ell_overflow ? SPS_PASS_STAGED_FALLBACK : SPS_PASS_STAGED)
+                                              : SPS_PASS_DIRECT;
   r.ms_sketch = ev.ms(0, 1);
   r.ms_iter = ev.ms(1, 2);
   r.ms_obj = ev.ms(2, 3);

@@ -43,6 +43,7 @@ struct Ctrl {
   int sketch_fault;       // fill disagreed with count (write skipped instead of out of range)
   int pad_overflow;       // single-pass sketch: a padded (row, chunk) slot was too small
   int oob_code;           // a bounds check skipped an access (code of the place; 0: none)
+  int ell_overflow;       // staged layout: the grouped copy would not fit its planned space (direct gathers instead)
   long long oob_index;    //   and the index it refused
 };
 
@@ -85,22 +86,57 @@ struct Layout {
   size_t logval, logvalT;           // log-domain: log K~ in CSR / CSC order (binary32)
   size_t bhat, erow, ecol, pot_a, pot_b;
   size_t seg_r, seg_c;              // staged gathers: chunk pointers of the CSR rows / CSC columns
-  size_t cm_ofs_r, cm_ofs_c;        // staged gathers: chunk-major offsets [J][n+1] (chunk-local) and
-  size_t cm_base_r, cm_base_c;      //   chunk bases [J+1]
-  size_t cm_idx_r, cm_idx_c;        //   indices in chunk-major order (K' values are stored in that order)
-  size_t cm_perm_r, cm_perm_c;      //   row-major position -> chunk-major position
+  // staged gathers, per side (0: row pass over the CSR, 1: column pass over the CSC): the grouped copy
+  size_t el_slice[2];               //   warp slices of every block: block-local row bounds [nblk][kEllWarps + 1]
+  size_t el_pbytes[2];              //   bytes of every part (block, slice, chunk)
+  size_t el_poff[2];                //   their exclusive prefix sums [parts + 1]
+  size_t el_tmp[2];                 //   layout scratch: (row, length, start) of every run of one slice
+  size_t el_pack[2];                //   the grouped copy
+  size_t el_perm[2];                //   CSR (CSC) position -> value slot of the grouped copy
+  int64_t el_pack_cap;              //   bytes planned for one grouped copy
   size_t pad_ofs, pad_col, pad_val, pad_lv, zsum, csum;   // single-pass sketch (0: two passes)
   size_t unit_r, unit_c;            // persistent iterations: unit starts over rows [n + 2] / columns [m + 2]
   size_t cmx;                       // pruned cost maximum: scratch (0: the full sweep only)
   int64_t pad_cap;
   int stage_w, stage_jr, stage_jc;  // staged gathers: chunk width, chunks over columns / rows (0: off)
-  int stage_nsm;                    // SM count the staging was planned for
+  int stage_nsm;                    // SM count the staging was planned for (one block per SM)
+  int stage_vb;                     // bytes of a stored value of the grouped copy
   size_t part;                      // block partials
   size_t total;
   int64_t cap;                      // sketch capacity (elements)
   int nblk_rows, nblk_cols;         // grid sizes of the half-iteration kernels
   int vbytes, ibytes;               // value / iterate element sizes
 };
+
+// Staged stabilised passes (sps_logdom.cu).  Block b (one per SM) owns a row
+// range; warp w of the block owns a slice of those rows (slices hold about
+// equal element counts).  A part is (block, slice, chunk of W columns): the
+// runs of the slice's rows inside the chunk.  Each part is stored as groups
+// of 32 runs sorted by run length (longest first), lane l of the warp walking
+// run l:
+//   bytes [0, 64)        32 block-local rows (u16; 0xFFFF: no run),
+//   bytes [64, 68)       the group's height h (int), the length of its first run,
+//   bytes [68, 72)       the height of the next group of the slice's stream (0: none),
+//   bytes [72, 80)       zero,
+//   then h steps of 32 x (2 + vb) bytes: 32 chunk-local indices (u16), then
+//   32 values (V); step k holds element k of every run of the group, a run
+//   shorter than h padded with index 0 and value 0.
+// Parts follow each other in (block, slice, chunk) order, so that a warp's
+// pass over its slice is one contiguous byte range; the warp streams it
+// through a ring of kEllRing bytes of shared memory in windows of kEllWin.
+constexpr int kEllWarps = 16;                      // warps (slices) of the staged kernel's block
+constexpr int kStgThreads = 32 * kEllWarps;        // its threads
+constexpr int kEllHdr = 80;                        // bytes of a group header
+constexpr int kEllBins = 256;                      // run-length bins of the sort (the last one holds >= 255)
+constexpr int kEllRing = 4096;                     // ring of one warp (a power of two)
+constexpr int kEllWin = 512;                       // window: one 16-byte copy per lane
+__host__ __device__ constexpr long long ell_step_bytes(int vb) { return 32LL * (2 + vb); }
+__host__ __device__ constexpr long long ell_group_bytes(int h, int vb) { return kEllHdr + (long long)h * ell_step_bytes(vb); }
+// Dynamic shared memory of the staged kernel: the chunk of the gathered
+// vector (W entries), the block's row sums (128-byte aligned), the rings.
+__host__ __device__ constexpr size_t ell_acc_offset(int W) { return (size_t)W * 4; }
+__host__ __device__ constexpr size_t ell_ring_offset(int W, int rows) { return ((size_t)W * 4 + (size_t)rows * 4 + 127) & ~(size_t)127; }
+__host__ __device__ constexpr size_t ell_smem_bytes(int W, int rows) { return ell_ring_offset(W, rows) + (size_t)kEllWarps * kEllRing; }
 
 constexpr int kPartSlots = 8;      // partial arrays of nblk doubles each
 constexpr int kMaxBlocks = 4096;

@@ -58,11 +58,21 @@ struct LogArgs {
   // position of row i with column >= c W (c = 0 .. Jr), seg_c likewise for CSC.
   int stage, W, Jr, Jc, rows_pb, cols_pb;
   const int *seg_r, *seg_c;
-  // chunk-major copies for the staged passes: the elements of chunk c are
-  // cm_base[c] + [cm_ofs[c (n+1) + i], cm_ofs[c (n+1) + i + 1]) for row i; K'
-  // (val / valT) is stored in this order and perm maps row-major positions to it
-  const int *cm_ofs_r, *cm_ofs_c, *cm_base_r, *cm_base_c, *cm_idx_r, *cm_idx_c, *cm_perm_r, *cm_perm_c;
-  long long nnz_lim;   // elements the chunk-major arrays hold (bounds checks)
+  // grouped copies for the staged passes (side 0: rows over the CSR, 1:
+  // columns over the CSC; layout in sps_internal.h): the warp slices, the
+  // parts' byte offsets, the copies themselves and, per CSR / CSC position,
+  // the value slot its K' goes to.  K' is stored there instead of val / valT
+  // unless ctrl->ell_overflow is set (a sketch too large for the planned copy),
+  // in which case the passes gather directly.
+  int sblk;                        // blocks of the staged kernel (one per SM)
+  int* el_slice[2];
+  long long* el_pbytes[2];
+  long long* el_poff[2];
+  int* el_tmp[2];
+  unsigned char* el_pack[2];
+  int* el_perm[2];
+  long long pack_lim;              // bytes of one grouped copy
+  long long nnz_lim;               // elements of the CSR / CSC arrays (bounds checks)
 };
 
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
@@ -126,17 +136,33 @@ __device__ __forceinline__ void absorb_segment(int lo, int hi, const int* idx, c
   if (lane == 0) *e_out = e;
 }
 
+// Where K' of one side goes: the grouped copy through perm (staged passes) or
+// val / valT in CSR / CSC order.
+template <typename V>
+struct AbsorbOut {
+  V* out;
+  const int* perm;
+  long long limit;
+};
+template <typename V>
+__device__ __forceinline__ AbsorbOut<V> absorb_out(const LogArgs& A, int side) {
+  if (A.stage && !*(volatile int*)&A.ctrl->ell_overflow)
+    return {reinterpret_cast<V*>(A.el_pack[side]), A.el_perm[side], A.pack_lim / (long long)sizeof(V)};
+  return {reinterpret_cast<V*>(side ? A.valT : A.val), nullptr, A.nnz_lim};
+}
+
 template <typename V>
 __global__ void __launch_bounds__(kT) k_absorb_all(LogArgs A, int t) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
+  const AbsorbOut<V> R = absorb_out<V>(A, 0), C = absorb_out<V>(A, 1);
   for (int i = gw; i < A.n; i += nw)
-    absorb_segment<V>(A.row_ptr[i], A.row_ptr[i + 1], A.col_idx, A.logval, A.alpha[i], A.beta, A.inv_eps,
-                      (V*)A.val, A.erow + i, lane, A.cm_perm_r, A.nnz_lim, A.ctrl);
+    absorb_segment<V>(A.row_ptr[i], A.row_ptr[i + 1], A.col_idx, A.logval, A.alpha[i], A.beta, A.inv_eps, R.out,
+                      A.erow + i, lane, R.perm, R.limit, A.ctrl);
   for (int j = gw; j < A.m; j += nw)
-    absorb_segment<V>(A.col_ptr[j], A.col_ptr[j + 1], A.row_idx, A.logvalT, A.beta[j], A.alpha, A.inv_eps,
-                      (V*)A.valT, A.ecol + j, lane, A.cm_perm_c, A.nnz_lim, A.ctrl);
+    absorb_segment<V>(A.col_ptr[j], A.col_ptr[j + 1], A.row_idx, A.logvalT, A.beta[j], A.alpha, A.inv_eps, C.out,
+                      A.ecol + j, lane, C.perm, C.limit, A.ctrl);
   // scalings of the pair t: 1 where the potential is finite, 0 where the row / column is unreachable
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
   float* u = A.ubuf + (size_t)(t & 1) * A.n;
@@ -164,6 +190,7 @@ __global__ void k_log_init(int n, int m, float* alpha, float* beta, const T* al0
     ctrl->t = 0; ctrl->done = 0; ctrl->iters = 0;
     ctrl->blocks_a = ctrl->blocks_b = ctrl->blocks_c = 0u;
     ctrl->bar_count = 0u;
+    ctrl->ell_overflow = 0;
     if (ctrl->status != SPS_OK) ctrl->done = 1;
   }
 }
@@ -267,32 +294,6 @@ __device__ __forceinline__ void log_col_phase(const LogArgs& A, int t, float (&o
   o[0] = s1[0];
 }
 
-// Eight consecutive values from an 8-aligned position (one or two 128-bit loads).
-template <typename V> __device__ __forceinline__ void load8(const V* p, float (&o)[8]);
-template <> __device__ __forceinline__ void load8<float>(const float* p, float (&o)[8]) {
-  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
-  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
-}
-template <> __device__ __forceinline__ void load8<__nv_bfloat16>(const __nv_bfloat16* p, float (&o)[8]) {
-  const uint4 q = *reinterpret_cast<const uint4*>(p);
-  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    o[2 * k] = __uint_as_float(w[k] << 16);
-    o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
-  }
-}
-template <> __device__ __forceinline__ void load8<__half>(const __half* p, float (&o)[8]) {
-  const uint4 q = *reinterpret_cast<const uint4*>(p);
-  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
-    o[2 * k] = f.x;
-    o[2 * k + 1] = f.y;
-  }
-}
-
 // 16-byte asynchronous copy global -> shared through L2 (cp.async.cg), and the
 // wait for all of this thread's copies.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -303,55 +304,117 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-__device__ __forceinline__ void load8i(const int* p, int (&o)[8]) {
-  const int4 a = __ldg(reinterpret_cast<const int4*>(p)), b = __ldg(reinterpret_cast<const int4*>(p + 4));
-  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
-}
+// ----------------------------------------------------------------------------
+// Staged passes over the grouped copy (its layout is described with kEllWarps).
+// ----------------------------------------------------------------------------
 
-// One aligned group of 8 elements starting at w: the products of those inside
-// [E0, E1) added to their rows' sums.  An element of the chunk-major copy
-// carries its block-local row in the high 16 bits and its chunk-local index
-// in the low 16 bits, so consecutive elements of one row are summed in a
-// register and each row change costs one shared atomic.
-__device__ __forceinline__ void group8(int w, int E0, int E1, const int (&id)[8], const float (&vv)[8], int jn,
-                                       const float* xs, float* acc) {
-  const int u0 = max(0, E0 - w), u1 = min(8, E1 - w);
-  if (u0 >= u1) return;
-  int k = -1;
-  float s = 0.0f;
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    if (u >= u0 && u < u1) {
-      const int r = (int)((unsigned)id[u] >> 16);
-      const int q = id[u] & 0xffff;
-      if (r != k) {
-        if (k >= 0) atomicAdd(&acc[k], s);
-        s = 0.0f;
-        k = r;
-      }
-      if (q < jn) s = fmaf(vv[u], xs[q], s);
-    }
+constexpr int kEllWins = kEllRing / kEllWin;   // windows a ring holds
+
+// Wait until at most n of this thread's cp.async groups are pending (n is
+// clamped to 0 .. kEllWins - 1; the instruction takes an immediate).
+__device__ __forceinline__ void cp_async_wait_n(int n) {
+  switch (n <= 0 ? 0 : n >= kEllWins - 1 ? kEllWins - 1 : n) {
+    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
+    case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
   }
-  atomicAdd(&acc[k], s);
+}
+static_assert(kEllWins == 8, "cp_async_wait_n covers eight windows");
+static_assert(kEllWin == 32 * 16, "a window is one 16-byte copy per lane");
+
+template <typename V> __device__ __forceinline__ float ring_val(const unsigned char* p);
+template <> __device__ __forceinline__ float ring_val<float>(const unsigned char* p) {
+  return *reinterpret_cast<const float*>(p);
+}
+template <> __device__ __forceinline__ float ring_val<__nv_bfloat16>(const unsigned char* p) {
+  return __uint_as_float((unsigned)*reinterpret_cast<const unsigned short*>(p) << 16);
+}
+template <> __device__ __forceinline__ float ring_val<__half>(const unsigned char* p) {
+  return __half2float(*reinterpret_cast<const __half*>(p));
 }
 
-// The sparse products of one block's rows [r0, r0 + nr) with x staged in
-// shared memory chunk by chunk (J chunks of W entries of x, x of length nx),
-// over the chunk-major copy: the block's elements of chunk c are one
-// contiguous range, streamed as aligned groups of 8 per thread, two groups in
-// registers that take turns (one is used while the other loads, with no copy
-// between them).  Each element names its block-local row (group8), and row
-// partial products go to acc with shared atomics, so the order of the
-// additions within a row is not fixed.  The chunk of x arrives by cp.async.
+// One warp's stream of the grouped copy: the bytes [s0, s1) of the pack, at
+// positions relative to a0 (s0 rounded down to a window), pass through the
+// warp's ring; relative byte r sits at ring[r mod kEllRing] while resident.
+// Window k is the relative bytes [k kEllWin, (k + 1) kEllWin), clipped to the
+// stream; lane l copies its 16 bytes of each window (cp.async through L2) and
+// commits one group per window, so window k has landed for the lane once at
+// most (issued - 1 - k) of its groups are pending.  Window k is issued once
+// every byte of window k - kEllWins has been read by the whole warp.
+struct EllRing {
+  const unsigned char* src;   // pack + a0
+  unsigned char* ring;
+  unsigned r0, r1;            // the stream, relative
+  unsigned issued, nwin;
+};
+
+// Make the relative bytes below `end` readable by the warp: issue the windows
+// that the read position `cons` allows (every byte below it has been read by
+// every lane), wait for the window holding byte end - 1, then a warp barrier.
+// end - cons <= kEllRing - kEllWin, so that window has been issued.
+__device__ __forceinline__ void ell_need(EllRing& R, unsigned cons, unsigned end) {
+  __syncwarp();
+  const unsigned lim = min(R.nwin, cons / kEllWin + kEllWins);
+  const unsigned l16 = 16u * (threadIdx.x & 31);
+  while (R.issued < lim) {
+    const unsigned r = R.issued * kEllWin + l16;
+    if (r >= R.r0 && r < R.r1) cp_async16(R.ring + (r & (kEllRing - 1)), R.src + r);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    ++R.issued;
+  }
+  cp_async_wait_n((int)R.issued - 1 - (int)((end - 1) / kEllWin));
+  __syncwarp();
+}
+
+// One staged pass of this block: acc[r] += sum over the block's row r of
+// K'_rj x_j (rows local to the block, nr of them), x of length nx passing
+// through shared memory (xs) in J chunks of W entries.  Warp w streams its
+// slice's groups (one contiguous byte range over all chunks) through its ring
+// and walks them chunk by chunk; lane l of a group continues its row's sum
+// with run l, one multiply-add per step in column order, so every row's sum is
+// one sequential chain over its columns and no two lanes of the block ever
+// hold the same row at once (a row belongs to one slice and appears once in a
+// chunk's groups): plain loads and stores of acc, no atomics.  A group's
+// header names the next group's height, so one wait covers a whole group (up
+// to KB steps).  The stream runs ahead across chunk boundaries; the chunk of x
+// arrives by cp.async between two block barriers.
 template <typename V>
-__device__ __forceinline__ void staged_pass_cm(const int* __restrict__ idx, const V* val, const float* x, int nx,
-                                               const int* __restrict__ ofs, const int* __restrict__ base, int ld,
-                                               int r0, int nr, int W, int J, float* xs, float* acc,
-                                               long long limit, Ctrl* ctrl) {
-  const int T = blockDim.x, t = threadIdx.x;
+__device__ __forceinline__ void ell_pass(const unsigned char* __restrict__ pack, const long long* __restrict__ poff,
+                                         const float* x, int nx, int nr, int W, int J, float* xs, float* acc,
+                                         unsigned char* rings, long long pack_lim, Ctrl* ctrl) {
+  constexpr int vb = (int)sizeof(V);
+  constexpr unsigned st = (unsigned)ell_step_bytes(vb);
+  constexpr unsigned M = kEllRing - 1;
+  constexpr int KB = (int)((kEllRing - kEllWin - kEllHdr) / st);   // steps one wait covers
+  const int T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const long long* po = poff + ((size_t)blockIdx.x * kEllWarps + warp) * J;
+  long long s0 = __ldg(po), s1 = __ldg(po + J);
+  if (s0 < 0 || s1 < s0 || s1 > pack_lim || (s0 & 15) || (s1 & 15) || s1 - s0 > (1LL << 30)) {
+    if (lane == 0) oob(ctrl, 2, s1);   // inconsistent slice bounds: skip the slice
+    s1 = s0 = 0;
+  }
+  const long long a0 = s0 & ~(long long)(kEllWin - 1);
+  EllRing R;
+  R.src = pack + a0;
+  R.ring = rings + (size_t)warp * kEllRing;
+  R.r0 = (unsigned)(s0 - a0);
+  R.r1 = (unsigned)(s1 - a0);
+  R.nwin = R.r1 > R.r0 ? (R.r1 - 1) / kEllWin + 1 : 0;
+  R.issued = 0;
+  ell_need(R, R.r0, R.r0 + 16);   // the first windows (the wait is for the first one only)
+  const unsigned l2 = 2u * lane, lv = 64u + (unsigned)vb * lane;
+  unsigned p = R.r0;   // read position (uniform over the warp)
+  int Hc = -1;         // height of the group at p, when known from the previous header
   for (int c = 0; c < J; ++c) {
     const int j0 = c * W;
     const int jn = min(W, nx - j0);
+    const long long e1 = __ldg(po + c + 1);
+    const unsigned pe = (unsigned)(min(max(e1, a0 + (long long)p), s1) - a0);   // end of this part
     __syncthreads();   // the previous chunk is no longer read (and acc is initialised)
     if ((((uintptr_t)(x + j0)) & 15) == 0) {
       const int n4 = jn >> 2;
@@ -360,102 +423,62 @@ __device__ __forceinline__ void staged_pass_cm(const int* __restrict__ idx, cons
     } else {
       for (int k = t; k < jn; k += T) xs[k] = __ldcg(x + j0 + k);
     }
-    const int bc = base[c];
-    // a block past the last row (r0 >= rows) owns nothing and reads no bounds
-    int E0 = 0, E1 = 0;
-    if (nr > 0) {
-      E0 = bc + ofs[(size_t)c * ld + r0];
-      E1 = bc + ofs[(size_t)c * ld + r0 + nr];
-    }
-    cp_async_wait_all();
+    cp_async_wait_all();   // also lands the stream windows issued so far
     __syncthreads();
-    if (E0 < 0 || E1 < E0 || (long long)E1 > limit) {   // inconsistent bounds: skip the chunk
-      if (t == 0) oob(ctrl, 2, E1);
-      E1 = E0 = 0;
-    }
-    const int S = 8 * T;
-    int w = (E0 & ~7) + 8 * t;
-    int ia[8], ib[8];
-    float va[8], vb[8];
-    if (w < E1) { load8i(idx + w, ia); load8<V>(val + w, va); }
-    while (w < E1) {
-      if (w + S < E1) { load8i(idx + w + S, ib); load8<V>(val + w + S, vb); }
-      group8(w, E0, E1, ia, va, jn, xs, acc);
-      w += S;
-      if (w >= E1) break;
-      if (w + S < E1) { load8i(idx + w + S, ia); load8<V>(val + w + S, va); }
-      group8(w, E0, E1, ib, vb, jn, xs, acc);
-      w += S;
-    }
-  }
-  __syncthreads();
-}
-
-// Chunk-major copies (built once after the sketch).  ofs[c (rows+1) + i] is
-// the chunk-local start of segment i in chunk c; base[c] the chunk's start.
-__global__ void __launch_bounds__(1024) k_cm_scan(int rows, const int* seg, int J, int* ofs) {
-  __shared__ long long sh[1024];
-  const int c = blockIdx.x;
-  if (c >= J) return;
-  const int T = blockDim.x, t = threadIdx.x;
-  const int per = (rows + T - 1) / T;
-  const int lo = min(rows, t * per), hi = min(rows, lo + per);
-  const int* s0 = seg + (size_t)c * rows;
-  const int* s1 = seg + (size_t)(c + 1) * rows;
-  long long s = 0;
-  for (int i = lo; i < hi; ++i) s += s1[i] - s0[i];
-  sh[t] = s;
-  __syncthreads();
-  for (int o = 1; o < T; o <<= 1) {
-    const long long v = t >= o ? sh[t - o] : 0;
-    __syncthreads();
-    sh[t] += v;
-    __syncthreads();
-  }
-  long long run = sh[t] - s;
-  int* out = ofs + (size_t)c * (rows + 1);
-  for (int i = lo; i < hi; ++i) {
-    out[i] = (int)run;
-    run += s1[i] - s0[i];
-  }
-  if (t == T - 1) out[rows] = (int)sh[T - 1];
-}
-
-__global__ void k_cm_base(int rows, int J, const int* ofs, int* base) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  int b = 0;
-  for (int c = 0; c < J; ++c) {
-    base[c] = b;
-    b += ofs[(size_t)c * (rows + 1) + rows];
-  }
-  base[J] = b;
-}
-
-// The copy's element: (i mod rpb) << 16 | (index - c W), the row local to its
-// block (rpb rows a block) and the index local to its chunk.
-__global__ void k_cm_copy(int rows, const int* seg, int J, const int* ofs, const int* base, const int* idx,
-                          int* cm_idx, int* perm, long long limit, Ctrl* ctrl, int rpb, int W) {
-  const int lane = threadIdx.x & 31;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += (gridDim.x * blockDim.x) >> 5) {
-    for (int c = 0; c < J; ++c) {
-      const int src = seg[(size_t)c * rows + i];
-      const int len = seg[(size_t)(c + 1) * rows + i] - src;
-      const int dst = base[c] + ofs[(size_t)c * (rows + 1) + i];
-      for (int e = lane; e < len; e += 32) {
-        if (src + e < 0 || (long long)(src + e) >= limit || dst + e < 0 || (long long)(dst + e) >= limit) {
-          oob(ctrl, 3, (long long)dst + e);
-          continue;
-        }
-        cm_idx[dst + e] = ((i % rpb) << 16) | (idx[src + e] - c * W);
-        perm[src + e] = dst + e;
+    while (p < pe) {
+      if (Hc < 0) {
+        ell_need(R, p, min(p + kEllHdr, pe));
+        Hc = *reinterpret_cast<const int*>(R.ring + ((p + 64) & M));
       }
+      if (Hc < 1 || (long long)p + ell_group_bytes(Hc, vb) > pe) {   // inconsistent group: skip the rest of the part
+        if (lane == 0) oob(ctrl, 4, a0 + p);
+        p = pe;
+        Hc = -1;
+        break;
+      }
+      const int H = Hc;
+      int n = min(H, KB);
+      ell_need(R, p, p + kEllHdr + n * st);
+      const unsigned row = *reinterpret_cast<const unsigned short*>(R.ring + ((p + l2) & M));
+      const int Hn = *reinterpret_cast<const int*>(R.ring + ((p + 68) & M));
+      if (*reinterpret_cast<const int*>(R.ring + ((p + 64) & M)) != H) {
+        if (lane == 0) oob(ctrl, 4, a0 + p);
+        p = pe;
+        Hc = -1;
+        break;
+      }
+      const bool mine = row < (unsigned)nr;
+      if (!mine && row != 0xFFFFu) oob(ctrl, 5, row);
+      float s = mine ? acc[row] : 0.0f;
+      unsigned q = p + kEllHdr;
+      for (int k = 0;;) {
+#pragma unroll 4
+        for (int u = 0; u < n; ++u) {
+          const unsigned o = q + u * st;
+          const unsigned iq = *reinterpret_cast<const unsigned short*>(R.ring + ((o + l2) & M));
+          const float w = ring_val<V>(R.ring + ((o + lv) & M));
+          // a padding step adds 0 x xs[0] (x is finite); an index past the chunk
+          // (only in an inconsistent copy) reads inside xs
+          s = fmaf(w, xs[min(iq, (unsigned)(W - 1))], s);
+        }
+        q += n * st;
+        k += n;
+        if (k >= H) break;
+        n = min(KB, H - k);
+        ell_need(R, q, q + n * st);
+      }
+      if (mine) acc[row] = s;
+      p = q;
+      Hc = Hn > 0 ? Hn : -1;
     }
+    p = max(p, pe);
   }
+  cp_async_wait_all();   // nothing of the stream stays in flight
+  __syncthreads();
 }
 
-// Staged row pass: v passes through shared memory chunk by chunk; the partial
-// products of this block's rows accumulate in shared memory.
-template <int LPR, typename V, bool UOT>
+// Staged row pass: u~ of this block's rows from the grouped copy of the CSR.
+template <typename V, bool UOT>
 __device__ __forceinline__ void log_row_phase_staged(const LogArgs& A, int t, float (&o)[3], float* sh, float* dsm) {
   const float* v = A.vbuf + (size_t)(t & 1) * A.m;
   const float* uold = A.ubuf + (size_t)(t & 1) * A.n;
@@ -464,8 +487,8 @@ __device__ __forceinline__ void log_row_phase_staged(const LogArgs& A, int t, fl
   const int nr = max(0, min(A.n, r0 + A.rows_pb) - r0);
   float* acc = dsm + A.W;
   for (int k = threadIdx.x; k < nr; k += blockDim.x) acc[k] = 0.0f;
-  staged_pass_cm<V>(A.cm_idx_r, (const V*)A.val, v, A.m, A.cm_ofs_r, A.cm_base_r, A.n + 1, r0, nr, A.W, A.Jr, dsm, acc,
-                    A.nnz_lim, A.ctrl);
+  unsigned char* rings = reinterpret_cast<unsigned char*>(dsm) + ell_ring_offset(A.W, max(A.rows_pb, A.cols_pb));
+  ell_pass<V>(A.el_pack[0], A.el_poff[0], v, A.m, nr, A.W, A.Jr, dsm, acc, rings, A.pack_lim, A.ctrl);
   float res = 0.0f, unr = 0.0f, mlog = 0.0f;
   for (int k = threadIdx.x; k < nr; k += blockDim.x) {
     const int i = r0 + k;
@@ -476,7 +499,8 @@ __device__ __forceinline__ void log_row_phase_staged(const LogArgs& A, int t, fl
   o[0] = s2[0]; o[1] = s2[1];
 }
 
-template <int LPR, typename V, bool UOT>
+// Staged column pass: v~ of this block's columns from the grouped copy of the CSC.
+template <typename V, bool UOT>
 __device__ __forceinline__ void log_col_phase_staged(const LogArgs& A, int t, float (&o)[2], float* sh, float* dsm) {
   const float* u = A.ubuf + (size_t)((t + 1) & 1) * A.n;
   float* vnew = A.vbuf + (size_t)((t + 1) & 1) * A.m;
@@ -484,8 +508,8 @@ __device__ __forceinline__ void log_col_phase_staged(const LogArgs& A, int t, fl
   const int nc = max(0, min(A.m, c0 + A.cols_pb) - c0);
   float* acc = dsm + A.W;
   for (int k = threadIdx.x; k < nc; k += blockDim.x) acc[k] = 0.0f;
-  staged_pass_cm<V>(A.cm_idx_c, (const V*)A.valT, u, A.n, A.cm_ofs_c, A.cm_base_c, A.m + 1, c0, nc, A.W, A.Jc, dsm,
-                    acc, A.nnz_lim, A.ctrl);
+  unsigned char* rings = reinterpret_cast<unsigned char*>(dsm) + ell_ring_offset(A.W, max(A.rows_pb, A.cols_pb));
+  ell_pass<V>(A.el_pack[1], A.el_poff[1], u, A.n, nc, A.W, A.Jc, dsm, acc, rings, A.pack_lim, A.ctrl);
   float unb = 0.0f, mlog = 0.0f;
   for (int k = threadIdx.x; k < nc; k += blockDim.x) {
     const int j = c0 + k;
@@ -520,6 +544,275 @@ __global__ void k_chunk_ptrs(int rows, const int* __restrict__ ptr, const int* _
   }
 }
 
+// ----------------------------------------------------------------------------
+// Building the grouped copies (once a solve, after the sketch).
+// ----------------------------------------------------------------------------
+
+// Warp slices: slice w of block b is the block-local rows [S[w], S[w + 1]),
+// cut where the elements before it reach w / kEllWarps of the block's (block b
+// owns rows [b R, (b + 1) R) of the rows).
+__global__ void k_el_slices(int rows, int R, int nblk, const int* __restrict__ ptr, int* __restrict__ S) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= nblk * (kEllWarps + 1)) return;
+  const int b = tid / (kEllWarps + 1), w = tid % (kEllWarps + 1);
+  const int r0 = (int)min((long long)rows, (long long)b * R), r1 = (int)min((long long)rows, (long long)r0 + R);
+  const long long e0 = ptr[r0], E = (long long)ptr[r1] - e0;
+  const long long target = e0 + E * w / kEllWarps;
+  int lo = r0, hi = r1;   // the first row i of [r0, r1] with ptr[i] >= target
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (ptr[mid] < target) lo = mid + 1; else hi = mid;
+  }
+  S[tid] = w == kEllWarps ? r1 - r0 : lo - r0;
+}
+
+// Run lengths of one part, the rows [g0, g1) in chunk c (one warp):
+// len = seg[(c + 1) rows + r] - seg[c rows + r], counted in hist by bin
+// min(len, kEllBins - 1) (rows without a run are left out).  Returns the
+// longest run of the last bin (0 if it is empty) on every lane; a negative
+// length (inconsistent chunk pointers) sets *bad.
+__device__ __forceinline__ int ell_hist(const int* __restrict__ seg, int rows, int c, int g0, int g1, int* hist,
+                                        int* bad) {
+  const int lane = threadIdx.x & 31;
+  for (int k = lane; k < kEllBins; k += 32) hist[k] = 0;
+  __syncwarp();
+  const int* s0 = seg + (size_t)c * rows;
+  const int* s1 = s0 + rows;
+  unsigned lump = 0u;
+  for (int r = g0 + lane; r < g1; r += 32) {
+    const int len = s1[r] - s0[r];
+    if (len < 0) *bad = 1;
+    if (len > 0) {
+      atomicAdd(&hist[min(len, kEllBins - 1)], 1);
+      if (len >= kEllBins - 1) lump = max(lump, (unsigned)len);
+    }
+  }
+  __syncwarp();
+  return (int)__reduce_max_sync(0xffffffffu, lump);
+}
+
+// The sorted order of a part (longest runs first): start[k] = runs in bins
+// above k (if start is given), *bytes = the part's bytes (every group takes
+// the height of its first run; the last bin's groups take the longest run).
+// Lane l handles bins 8 l .. 8 l + 7.  Returns the part's runs on every lane.
+__device__ __forceinline__ int ell_order(const int* hist, int* start, int lump, int vb, long long* bytes) {
+  const int lane = threadIdx.x & 31;
+  int cnt[8], tot = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    cnt[u] = hist[8 * lane + u];
+    tot += cnt[u];
+  }
+  int suf = tot;   // runs in the bins of this lane and the lanes above
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_down_sync(0xffffffffu, suf, o);
+    if (lane + o < 32) suf += y;
+  }
+  int pos = suf - tot;
+  long long by = 0;
+#pragma unroll
+  for (int u = 7; u >= 0; --u) {
+    const int k = 8 * lane + u;
+    if (start) start[k] = pos;
+    const int C = cnt[u];
+    if (C > 0) {
+      const int h = k < kEllBins - 1 ? k : lump;
+      const int groups = (pos + C + 31) / 32 - (pos + 31) / 32;   // groups whose first run is in bin k
+      by += (long long)groups * ell_group_bytes(h, vb);
+    }
+    pos += C;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) by += __shfl_xor_sync(0xffffffffu, by, o);
+  *bytes = by;
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, suf, 0);
+}
+
+// Bytes of every part: one warp a slice, chunk by chunk.
+__global__ void __launch_bounds__(256) k_el_size(int rows, int R, int nblk, int J, const int* __restrict__ seg,
+                                                 const int* __restrict__ S, int vb, long long* __restrict__ pbytes,
+                                                 Ctrl* ctrl) {
+  __shared__ int hist_sh[8][kEllBins];
+  __shared__ int bad_sh[8];
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sl = blockIdx.x * 8 + wl;   // b kEllWarps + w
+  if (sl >= nblk * kEllWarps) return;
+  const int b = sl / kEllWarps, w = sl % kEllWarps;
+  const int r0 = (int)min((long long)rows, (long long)b * R);
+  const int* Sb = S + (size_t)b * (kEllWarps + 1);
+  const int g0 = r0 + Sb[w], g1 = r0 + Sb[w + 1];
+  if (lane == 0) bad_sh[wl] = 0;
+  __syncwarp();
+  for (int c = 0; c < J; ++c) {
+    const int lump = ell_hist(seg, rows, c, g0, g1, hist_sh[wl], &bad_sh[wl]);
+    long long by = 0;
+    ell_order(hist_sh[wl], nullptr, lump, vb, &by);
+    if (lane == 0) pbytes[(size_t)sl * J + c] = by;
+  }
+  __syncwarp();
+  if (lane == 0 && bad_sh[wl]) {
+    oob(ctrl, 6, sl);
+    ctrl->ell_overflow = 1;
+  }
+}
+
+// Exclusive prefix sums of the parts' bytes (one block); a total above the
+// planned copy, or with more value slots than an int counts, sets
+// ell_overflow (the passes then gather directly).
+__global__ void __launch_bounds__(1024) k_el_scan(long long P, const long long* __restrict__ pbytes,
+                                                  long long* __restrict__ poff, long long cap_bytes, int vb,
+                                                  Ctrl* ctrl) {
+  __shared__ long long sh[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const long long per = (P + T - 1) / T;
+  const long long lo = min(P, (long long)t * per), hi = min(P, lo + per);
+  long long s = 0;
+  for (long long i = lo; i < hi; ++i) s += pbytes[i];
+  sh[t] = s;
+  __syncthreads();
+  for (int o = 1; o < T; o <<= 1) {
+    const long long y = t >= o ? sh[t - o] : 0;
+    __syncthreads();
+    sh[t] += y;
+    __syncthreads();
+  }
+  long long run = sh[t] - s;
+  for (long long i = lo; i < hi; ++i) {
+    poff[i] = run;
+    run += pbytes[i];
+  }
+  if (t == T - 1) {
+    const long long tot = sh[T - 1];
+    poff[P] = tot;
+    if (tot > cap_bytes || tot / vb > 0x7fffffffLL) ctrl->ell_overflow = 1;
+  }
+}
+
+// The grouped copy of every part (one warp a slice, chunk by chunk): the runs
+// in sorted order (a bin's runs in row order) go to the slice's scratch as
+// (block-local row, length, first CSR position), then each group of 32 is
+// written: header, indices (padding 0), padding values 0, and perm of every
+// element (its value slot; absorption writes K' there).  A part whose bytes
+// disagree with k_el_size sets ell_overflow.
+template <typename V>
+__global__ void __launch_bounds__(256) k_el_fill(int rows, int R, int nblk, int J, int W, const int* __restrict__ seg,
+                                                 const int* __restrict__ idx, const int* __restrict__ S,
+                                                 const long long* __restrict__ poff, int* __restrict__ tmp,
+                                                 unsigned char* __restrict__ pack, int* __restrict__ perm,
+                                                 long long nnz_lim, long long pack_lim, Ctrl* ctrl) {
+  constexpr int vb = (int)sizeof(V);
+  __shared__ int hist_sh[8][kEllBins];
+  __shared__ int start_sh[8][kEllBins];
+  __shared__ int bad_sh[8];
+  if (*(volatile int*)&ctrl->ell_overflow) return;
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sl = blockIdx.x * 8 + wl;
+  if (sl >= nblk * kEllWarps) return;
+  const int b = sl / kEllWarps, w = sl % kEllWarps;
+  const int r0 = (int)min((long long)rows, (long long)b * R);
+  const int* Sb = S + (size_t)b * (kEllWarps + 1);
+  const int g0 = r0 + Sb[w], g1 = r0 + Sb[w + 1];
+  int* cur = start_sh[wl];
+  if (lane == 0) bad_sh[wl] = 0;
+  __syncwarp();
+  long long prev = -1;   // header of the slice's previous group (its next-height field is set here)
+  for (int c = 0; c < J; ++c) {
+    const int lump = ell_hist(seg, rows, c, g0, g1, hist_sh[wl], &bad_sh[wl]);
+    long long by = 0;
+    const int runs = ell_order(hist_sh[wl], cur, lump, vb, &by);
+    const long long p0 = poff[(size_t)sl * J + c], p1 = poff[(size_t)sl * J + c + 1];
+    if (p1 - p0 != by || p0 < 0 || p1 > pack_lim || runs > g1 - g0) {
+      if (lane == 0) {
+        oob(ctrl, 7, p0);
+        ctrl->ell_overflow = 1;
+      }
+      return;
+    }
+    // sorted positions: within a bin, runs keep their row order
+    for (int base = g0; base < g1; base += 32) {
+      const int r = base + lane;
+      int len = 0, src = 0;
+      if (r < g1) {
+        src = seg[(size_t)c * rows + r];
+        len = seg[(size_t)(c + 1) * rows + r] - src;
+      }
+      const int bin = len > 0 ? min(len, kEllBins - 1) : -1;
+      const unsigned same = __match_any_sync(0xffffffffu, bin);
+      const int rank = __popc(same & ((1u << lane) - 1u));
+      const int pos = bin > 0 ? cur[bin] + rank : 0;
+      __syncwarp();
+      if (bin > 0 && rank == 0) cur[bin] += __popc(same);
+      __syncwarp();
+      if (bin > 0) {
+        int* e = tmp + 3 * ((size_t)g0 + pos);
+        e[0] = r - r0;
+        e[1] = len;
+        e[2] = src;
+      }
+    }
+    __syncwarp();
+    long long off = p0;
+    const int G = (runs + 31) / 32;
+    for (int g = 0; g < G; ++g) {
+      const int pos = 32 * g + lane;
+      int row = 0xFFFF, len = 0, src = 0;
+      if (pos < runs) {
+        const int* e = tmp + 3 * ((size_t)g0 + pos);
+        row = e[0];
+        len = e[1];
+        src = e[2];
+      }
+      const int l0 = __shfl_sync(0xffffffffu, len, 0);
+      const int h = l0 < kEllBins - 1 ? l0 : lump;
+      if (off + ell_group_bytes(h, vb) > p1) {
+        if (lane == 0) {
+          oob(ctrl, 8, off);
+          ctrl->ell_overflow = 1;
+        }
+        return;
+      }
+      unsigned char* gp = pack + off;
+      reinterpret_cast<unsigned short*>(gp)[lane] = (unsigned short)row;
+      if (lane < 4) reinterpret_cast<int*>(gp + 64)[lane] = lane == 0 ? h : 0;
+      if (lane == 0 && prev >= 0) reinterpret_cast<int*>(pack + prev + 68)[0] = h;
+      prev = off;
+      constexpr long long st = ell_step_bytes(vb);
+      for (int k = 0; k < h; ++k) {
+        unsigned char* sp = gp + kEllHdr + k * st;   // step k: 32 indices, then 32 values
+        unsigned short q = 0;
+        if (k < len) {
+          const long long e = (long long)src + k;
+          if (e >= 0 && e < nnz_lim) {
+            q = (unsigned short)(idx[e] - c * W);
+            perm[e] = (int)((off + kEllHdr + k * st + 64) / vb + lane);
+          } else {
+            oob(ctrl, 9, e);
+            ctrl->ell_overflow = 1;
+          }
+        } else {
+          reinterpret_cast<V*>(sp + 64)[lane] = from_d<V>(0.0);
+        }
+        reinterpret_cast<unsigned short*>(sp)[lane] = q;
+      }
+      off += ell_group_bytes(h, vb);
+    }
+    if (off != p1) {
+      if (lane == 0) {
+        oob(ctrl, 8, off);
+        ctrl->ell_overflow = 1;
+      }
+      return;
+    }
+  }
+  __syncwarp();
+  if (lane == 0 && bad_sh[wl]) {
+    oob(ctrl, 6, sl);
+    ctrl->ell_overflow = 1;
+  }
+}
+
 // Fold the scalings of the pair t into the potentials (this block's rows and
 // columns) and reset them to 1.
 __device__ __forceinline__ void fold_scalings(const LogArgs& A, int t) {
@@ -551,12 +844,13 @@ __device__ __forceinline__ void rewrite_block(const LogArgs& A) {
   const int nw = blockDim.x >> 5;
   const int gw = blockIdx.x * nw + (threadIdx.x >> 5);
   const int tw = gridDim.x * nw;
+  const AbsorbOut<V> R = absorb_out<V>(A, 0), C = absorb_out<V>(A, 1);
   for (int i = gw; i < A.n; i += tw)
-    absorb_segment<V>(A.row_ptr[i], A.row_ptr[i + 1], A.col_idx, A.logval, A.alpha[i], A.beta, A.inv_eps,
-                      (V*)A.val, A.erow + i, lane, A.cm_perm_r, A.nnz_lim, A.ctrl);
+    absorb_segment<V>(A.row_ptr[i], A.row_ptr[i + 1], A.col_idx, A.logval, A.alpha[i], A.beta, A.inv_eps, R.out,
+                      A.erow + i, lane, R.perm, R.limit, A.ctrl);
   for (int j = gw; j < A.m; j += tw)
-    absorb_segment<V>(A.col_ptr[j], A.col_ptr[j + 1], A.row_idx, A.logvalT, A.beta[j], A.alpha, A.inv_eps,
-                      (V*)A.valT, A.ecol + j, lane, A.cm_perm_c, A.nnz_lim, A.ctrl);
+    absorb_segment<V>(A.col_ptr[j], A.col_ptr[j + 1], A.row_idx, A.logvalT, A.beta[j], A.alpha, A.inv_eps, C.out,
+                      A.ecol + j, lane, C.perm, C.limit, A.ctrl);
 }
 
 // Persistent stabilised iterations.  Partial slots: 0 residual, 1 unreachable
@@ -564,17 +858,23 @@ __device__ __forceinline__ void rewrite_block(const LogArgs& A) {
 // row phase of the next iteration writes it before any barrier while slower
 // blocks may still read this iteration's values), 6 max |log v~|.
 template <int LR, int LC, typename V, bool UOT, bool STG>
-__global__ void __launch_bounds__(kIterThreads) k_iterate_log(LogArgs A, int iters, int row_only) {
+__global__ void __launch_bounds__(STG ? kStgThreads : kIterThreads, 1) k_iterate_log(LogArgs A, int iters, int row_only) {
   __shared__ float sh[3 * 32 + 64];
   __shared__ int absorb_now;
   extern __shared__ __align__(16) float dsm[];   // staged chunk of the gathered vector, then row sums
   Ctrl* ctrl = A.ctrl;
   if (ctrl->done) return;
+  // staged launches read the grouped copies unless the sketch did not fit them
+  const bool grp = STG && !*(volatile int*)&ctrl->ell_overflow;
   int t = ctrl->t;
   for (int k = 0; k < iters; ++k) {
     float r3[3];
-    if constexpr (STG) log_row_phase_staged<LR, V, UOT>(A, t, r3, sh, dsm);
-    else log_row_phase<LR, V, UOT>(A, t, r3, sh);
+    if constexpr (STG) {
+      if (grp) log_row_phase_staged<V, UOT>(A, t, r3, sh, dsm);
+      else log_row_phase<LR, V, UOT>(A, t, r3, sh);
+    } else {
+      log_row_phase<LR, V, UOT>(A, t, r3, sh);
+    }
     if (threadIdx.x == 0) {
       A.part[0 * (size_t)A.nblk + blockIdx.x] = r3[0];
       A.part[1 * (size_t)A.nblk + blockIdx.x] = r3[1];
@@ -609,8 +909,12 @@ __global__ void __launch_bounds__(kIterThreads) k_iterate_log(LogArgs A, int ite
     }
     if (row_only) return;
     float c2[2];
-    if constexpr (STG) log_col_phase_staged<LC, V, UOT>(A, t, c2, sh, dsm);
-    else log_col_phase<LC, V, UOT>(A, t, c2, sh);
+    if constexpr (STG) {
+      if (grp) log_col_phase_staged<V, UOT>(A, t, c2, sh, dsm);
+      else log_col_phase<LC, V, UOT>(A, t, c2, sh);
+    } else {
+      log_col_phase<LC, V, UOT>(A, t, c2, sh);
+    }
     if (threadIdx.x == 0) {
       A.part[3 * (size_t)A.nblk + blockIdx.x] = c2[0];
       A.part[6 * (size_t)A.nblk + blockIdx.x] = c2[1];
@@ -660,24 +964,26 @@ bool coop_log(LogArgs A, int iters, int row_only, cudaStream_t st) {
   size_t smem = 0;
   if (STG) {
     // one block per SM owns a fixed row range and column range
-    smem = sizeof(float) * ((size_t)A.W + (size_t)std::max(A.rows_pb, A.cols_pb) + 1);
+    smem = ell_smem_bytes(A.W, std::max(A.rows_pb, A.cols_pb));
     if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kIterThreads, smem) != cudaSuccess || per_sm < 1) {
+  const int threads = STG ? kStgThreads : kIterThreads;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return false;
   }
   if (STG) {
-    if ((int64_t)A.rows_pb * nsm < A.n || (int64_t)A.cols_pb * nsm < A.m || A.nblk < nsm) return false;
+    // the grouped copies were laid out for one block per SM of this device
+    if ((int64_t)A.rows_pb * nsm < A.n || (int64_t)A.cols_pb * nsm < A.m || A.sblk != nsm) return false;
     A.nblk = nsm;
   } else {
     A.nblk = std::min(A.nblk, nsm * per_sm);
   }
   void* args[] = {(void*)&A, (void*)&iters, (void*)&row_only};
-  if (cudaLaunchCooperativeKernel((const void*)fn, dim3(A.nblk), dim3(kIterThreads), args, smem, st) != cudaSuccess) {
+  if (cudaLaunchCooperativeKernel((const void*)fn, dim3(A.nblk), dim3(threads), args, smem, st) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -729,14 +1035,16 @@ LogArgs make_log_args(const ProbDev& pd, const Layout& L, char* ws, const IterCf
   A.cols_pb = L.stage_nsm > 0 ? (pd.m + L.stage_nsm - 1) / L.stage_nsm : 0;
   A.seg_r = A.stage ? at<int>(ws, L.seg_r) : nullptr;
   A.seg_c = A.stage ? at<int>(ws, L.seg_c) : nullptr;
-  A.cm_ofs_r = A.stage ? at<int>(ws, L.cm_ofs_r) : nullptr;
-  A.cm_ofs_c = A.stage ? at<int>(ws, L.cm_ofs_c) : nullptr;
-  A.cm_base_r = A.stage ? at<int>(ws, L.cm_base_r) : nullptr;
-  A.cm_base_c = A.stage ? at<int>(ws, L.cm_base_c) : nullptr;
-  A.cm_idx_r = A.stage ? at<int>(ws, L.cm_idx_r) : nullptr;
-  A.cm_idx_c = A.stage ? at<int>(ws, L.cm_idx_c) : nullptr;
-  A.cm_perm_r = A.stage ? at<int>(ws, L.cm_perm_r) : nullptr;
-  A.cm_perm_c = A.stage ? at<int>(ws, L.cm_perm_c) : nullptr;
+  A.sblk = L.stage_nsm;
+  for (int s = 0; s < 2; ++s) {
+    A.el_slice[s] = A.stage ? at<int>(ws, L.el_slice[s]) : nullptr;
+    A.el_pbytes[s] = A.stage ? at<long long>(ws, L.el_pbytes[s]) : nullptr;
+    A.el_poff[s] = A.stage ? at<long long>(ws, L.el_poff[s]) : nullptr;
+    A.el_tmp[s] = A.stage ? at<int>(ws, L.el_tmp[s]) : nullptr;
+    A.el_pack[s] = A.stage ? at<unsigned char>(ws, L.el_pack[s]) : nullptr;
+    A.el_perm[s] = A.stage ? at<int>(ws, L.el_perm[s]) : nullptr;
+  }
+  A.pack_lim = A.stage ? L.el_pack_cap : 0;
   A.nnz_lim = L.cap;
   return A;
 }
@@ -865,19 +1173,24 @@ void first_iteration_v(const LogArgs& A, const IterCfg& ic, const void* al0, con
   k_lse_half<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.col_ptr, A.row_idx, A.logvalT, A.alpha, A.b,
                                                          A.beta, A.eps, A.phi);
   if (A.stage) {
-    // segment pointers and chunk-major copies (the absorption below writes K' through perm)
+    // chunk pointers, then the grouped copies (the absorption below writes K' through perm)
     k_chunk_ptrs<<<grid1((int64_t)A.n * 32, kT), kT, 0, st>>>(A.n, A.row_ptr, A.col_idx, A.W, A.Jr, (int*)A.seg_r);
     k_chunk_ptrs<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.col_ptr, A.row_idx, A.W, A.Jc, (int*)A.seg_c);
-    k_cm_scan<<<A.Jr, 1024, 0, st>>>(A.n, A.seg_r, A.Jr, (int*)A.cm_ofs_r);
-    k_cm_scan<<<A.Jc, 1024, 0, st>>>(A.m, A.seg_c, A.Jc, (int*)A.cm_ofs_c);
-    k_cm_base<<<1, 32, 0, st>>>(A.n, A.Jr, A.cm_ofs_r, (int*)A.cm_base_r);
-    k_cm_base<<<1, 32, 0, st>>>(A.m, A.Jc, A.cm_ofs_c, (int*)A.cm_base_c);
-    k_cm_copy<<<grid1((int64_t)A.n * 32, kT), kT, 0, st>>>(A.n, A.seg_r, A.Jr, A.cm_ofs_r, A.cm_base_r, A.col_idx,
-                                                          (int*)A.cm_idx_r, (int*)A.cm_perm_r, A.nnz_lim, A.ctrl,
-                                                          A.rows_pb, A.W);
-    k_cm_copy<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.seg_c, A.Jc, A.cm_ofs_c, A.cm_base_c, A.row_idx,
-                                                          (int*)A.cm_idx_c, (int*)A.cm_perm_c, A.nnz_lim, A.ctrl,
-                                                          A.cols_pb, A.W);
+    for (int side = 0; side < 2; ++side) {
+      const int rows = side ? A.m : A.n, R = side ? A.cols_pb : A.rows_pb, J = side ? A.Jc : A.Jr;
+      const int* ptr = side ? A.col_ptr : A.row_ptr;
+      const int* idx = side ? A.row_idx : A.col_idx;
+      const int* seg = side ? A.seg_c : A.seg_r;
+      const long long P = (long long)A.sblk * kEllWarps * J;
+      const int slices = A.sblk * kEllWarps;
+      k_el_slices<<<(A.sblk * (kEllWarps + 1) + 255) / 256, 256, 0, st>>>(rows, R, A.sblk, ptr, A.el_slice[side]);
+      k_el_size<<<(slices + 7) / 8, 256, 0, st>>>(rows, R, A.sblk, J, seg, A.el_slice[side], (int)sizeof(V),
+                                                  A.el_pbytes[side], A.ctrl);
+      k_el_scan<<<1, 1024, 0, st>>>(P, A.el_pbytes[side], A.el_poff[side], A.pack_lim, (int)sizeof(V), A.ctrl);
+      k_el_fill<V><<<(slices + 7) / 8, 256, 0, st>>>(rows, R, A.sblk, J, A.W, seg, idx, A.el_slice[side],
+                                                     A.el_poff[side], A.el_tmp[side], A.el_pack[side],
+                                                     A.el_perm[side], A.nnz_lim, A.pack_lim, A.ctrl);
+    }
   }
   k_absorb_all<V><<<grid1((int64_t)std::max(A.n, A.m) * 32, kT), kT, 0, st>>>(A, 1);
   (void)ic;
@@ -893,7 +1206,7 @@ sps_status launch_log_first_iteration(const ProbDev& pd, const Layout& L, char* 
     case SPS_F16: first_iteration_v<__half>(A, ic, init_alpha, init_beta, st); break;
     default: first_iteration_v<float>(A, ic, init_alpha, init_beta, st); break;
   }
-  add_launches(A.stage ? 12 : 4);
+  add_launches(A.stage ? 14 : 4);
   return cuda_fail(cudaGetLastError(), "log-domain first iteration");
 }
 

@@ -57,6 +57,7 @@ class Params(C.Structure):
                 ("sampler", C.c_int32), ("probs", C.c_int32)]
 
 GATHER_AUTO, GATHER_DIRECT, GATHER_STAGED = 0, 1, 2
+PASS_DIRECT, PASS_STAGED, PASS_STAGED_FALLBACK = 0, 1, 2
 
 
 class Result(C.Structure):
@@ -65,7 +66,8 @@ class Result(C.Structure):
                 ("logp", C.c_double), ("mass", C.c_double), ("kl_a", C.c_double), ("kl_b", C.c_double),
                 ("unreach_a", C.c_double), ("unreach_b", C.c_double), ("nnz", C.c_int64),
                 ("n_absorb", C.c_int32), ("ms_sketch", C.c_float), ("ms_iter", C.c_float),
-                ("ms_obj", C.c_float), ("launches", C.c_int32), ("iters_enqueued", C.c_int32)]
+                ("ms_obj", C.c_float), ("launches", C.c_int32), ("iters_enqueued", C.c_int32),
+                ("gather", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

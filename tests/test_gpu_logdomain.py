@@ -15,6 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2306_06581_gb300 import inputs  # noqa: E402
+from parity_util import compare_potentials, fixed_k, fp32_potential_bound, max_nnz  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -105,6 +106,7 @@ def test_staged_gathers_match_direct(S, ot_case, kd):
     d = S.spar_sink_ot(a, b, x, y, gather_mode=S.GATHER_DIRECT, **kw)
     g = S.spar_sink_ot(a, b, x, y, gather_mode=S.GATHER_STAGED, **kw)
     assert g["status"] == 0 and g["nnz"] == d["nnz"]
+    assert d["gather"] == S.PASS_DIRECT and g["gather"] == S.PASS_STAGED
     assert abs(g["iters"] - d["iters"]) <= 1
     assert abs(g["obj"] - d["obj"]) <= 2e-6 * abs(d["obj"])
     if kd == "f32":
@@ -119,5 +121,47 @@ def test_staged_gathers_uot(S, orc):
     g = S.spar_sink_uot(a, b, x, y, eps=0.01, lam=1.0, s=w.s, tol=1e-5, max_iter=20000, dtype="f32", seed=w.seed,
                         log_domain=1, gather_mode=S.GATHER_STAGED)
     assert g["status"] == 0 and o["info"]["status"] == 0
+    assert g["gather"] == S.PASS_STAGED
     assert abs(g["iters"] - o["info"]["iters"]) <= max(3, 0.05 * o["info"]["iters"])
     assert abs(g["obj"] - o["obj"]) <= 1e-5 * abs(o["obj"])
+
+
+@pytest.mark.parametrize("kind", ["ot", "uot"])
+def test_staged_potentials_after_fixed_iterations(S, orc, kind):
+    """Staged passes over the grouped copy: potentials element by element after
+    the oracle's iteration count (FP32 bound of parity_util)."""
+    if kind == "ot":
+        w = inputs.ot_gmm(2500, d=3, k=8, seed=33, eps=0.01, s_factor=16.0)
+        lam = math.inf
+    else:
+        w = inputs.uot_n20000(n=2500)
+        lam = 1.0
+    x, y, a, b = _r32(w)
+    P = orc.OracleProblem(a, b, 0.01, w.s, lam, x=x, y=y, seed=w.seed)
+    sk = P.sparsify()
+    o = orc.spar_sink(P, tol=1e-5, max_iter=20000, log_domain=True, sketch=sk)
+    K = o["info"]["iters"]
+    kw = dict(eps=0.01, s=w.s, dtype="f32", seed=w.seed, log_domain=1, gather_mode=S.GATHER_STAGED)
+    if kind == "ot":
+        run = lambda **e: S.spar_sink_ot(a, b, x, y, **kw, **e)
+    else:
+        run = lambda **e: S.spar_sink_uot(a, b, x, y, lam=lam, **kw, **e)
+    gk, ok = fixed_k(run, orc, P, sk, K, log_domain=True)
+    assert gk["gather"] == S.PASS_STAGED
+    da, db = compare_potentials(gk["alpha"].cpu(), gk["beta"].cpu(), ok["alpha"], ok["beta"],
+                                fp32_potential_bound(0.01, max_nnz(sk)))
+    print(f"staged {kind}: potentials after {K} iterations |d alpha| {da:.2e}, |d beta| {db:.2e}")
+
+
+def test_staged_passes_are_reproducible(S, ot_case):
+    """Every row's sum in a staged pass is one sequential chain over its columns,
+    whatever the order of the groups: two solves agree bit for bit."""
+    w, (x, y, a, b), _ = ot_case
+    kw = dict(eps=w.eps, s=w.s, tol=1e-5, max_iter=20000, dtype="f32", seed=w.seed, log_domain=1,
+              gather_mode=S.GATHER_STAGED)
+    g1 = S.spar_sink_ot(a, b, x, y, **kw)
+    g2 = S.spar_sink_ot(a, b, x, y, **kw)
+    assert g1["gather"] == g2["gather"] == S.PASS_STAGED
+    assert g1["iters"] == g2["iters"] and g1["obj"] == g2["obj"]
+    assert torch.equal(g1["alpha"].view(torch.int32), g2["alpha"].view(torch.int32))
+    assert torch.equal(g1["beta"].view(torch.int32), g2["beta"].view(torch.int32))
