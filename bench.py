@@ -297,6 +297,15 @@ def _max_over_ranks(x, dist, device):
     return float(t.item())
 
 
+def _kernel_ms_per_iteration(res, log_domain):
+    """Device time of one iteration of the iteration kernel: the solve's
+    iteration phase less its setup (the initial pair; in the log domain the
+    exact first iteration, the absorption and the grouped copies), over the
+    iterations the kernel ran (the first log-domain iteration is the setup's)."""
+    its = res["iters_enqueued"] - (1 if log_domain else 0)
+    return (res["ms_iter"] - res["ms_setup"]) / max(its, 1)
+
+
 def _spmv_bytes(res, n, m, kdtype="f32", log_domain=0):
     """Algorithmic HBM bytes of one iteration (row pass + column pass): every
     stored element once (int32 index + value), the pointer arrays, the per-row
@@ -310,6 +319,29 @@ def _spmv_bytes(res, n, m, kdtype="f32", log_domain=0):
     row = nnz * (4 + vb) + 4 * (n + 1) + ib * n * kr + ib * m
     col = nnz * (4 + vb) + 4 * (m + 1) + ib * m * kc + ib * n
     return row, col
+
+
+def _stream_bytes(res, n, m, kdtype="f32", log_domain=0):
+    """Bytes one iteration streams when the staged passes read the grouped
+    copies (sps_result.stream_bytes: both copies, with their headers and
+    padding, 16-bit indices) plus the same per-row and per-column vectors as
+    _spmv_bytes; None when the solve gathered directly."""
+    if not res.get("stream_bytes"):
+        return None
+    row, col = _spmv_bytes(res, n, m, kdtype, log_domain)
+    vectors = row + col - 2 * res["nnz"] * (4 + _VB[kdtype]) - 4 * (n + 1) - 4 * (m + 1)
+    return int(res["stream_bytes"] + vectors)
+
+
+def _stream_fields(res, w, kd, logd, per_iter_ms, peak):
+    """The staged passes' own bytes next to the algorithmic ones: what one
+    iteration streams (grouped copies, 16-bit indices) and the fraction of the
+    peak that rate is; empty when the solve gathered directly."""
+    sb = _stream_bytes(res, w.n, w.m, kd, logd)
+    if sb is None:
+        return {}
+    rate = sb / (per_iter_ms * 1e-3) / 1e9
+    return {"stream_bytes_per_iteration": sb, "stream_gbs": round(rate, 1), "stream_frac": round(rate / peak, 4)}
 
 
 def _traffic(name):
@@ -432,7 +464,7 @@ def run_ours(args):
     fixed_iters = 200
     rf = solve(tol=0.0, max_iter=fixed_iters, check_every=fixed_iters, workspace=ws)
     row_b, col_b = _spmv_bytes(rf, w.n, w.m, kd, logd)
-    per_iter_ms = rf["ms_iter"] / max(rf["iters_enqueued"], 1)
+    per_iter_ms = _kernel_ms_per_iteration(rf, logd)
     peak, peak_kind = _peaks()
     achieved = (row_b + col_b) / (per_iter_ms * 1e-3) / 1e9
     traffic, traffic_src = _traffic(w.name)
@@ -526,7 +558,8 @@ def run_ours(args):
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                      "traffic": traffic, "traffic_source": traffic_src,
                      "algorithmic_bytes_per_iteration": row_b + col_b,
-                     "ms_per_iteration": round(per_iter_ms, 5), "iterations_timed": rf["iters_enqueued"]},
+                     "ms_per_iteration": round(per_iter_ms, 5), "iterations_timed": rf["iters_enqueued"],
+                     **_stream_fields(rf, w, kd, logd, per_iter_ms, peak)},
         "e2e": {"value": round(statistics.median(e2e), 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
@@ -585,7 +618,7 @@ def _other_workload_leg(S, name, dev, flush_buf, sampler, steps=10):
         times.append(e0.elapsed_time(e1))
     rf = run(tol=0.0, max_iter=200, check_every=200, workspace=ws)
     row_b, col_b = _spmv_bytes(rf, w.n, w.m, kd, logd)
-    per = rf["ms_iter"] / max(rf["iters_enqueued"], 1)
+    per = _kernel_ms_per_iteration(rf, logd)
     peak, peak_kind = _peaks()
     ach = (row_b + col_b) / (per * 1e-3) / 1e9
     traffic, src = _traffic(w.name)
@@ -596,7 +629,8 @@ def _other_workload_leg(S, name, dev, flush_buf, sampler, steps=10):
             "roofline": {"bound": _bound(traffic, row_b + col_b), "achieved": round(ach, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(ach / peak, 4), "peak_kind": peak_kind,
                          "traffic": traffic, "traffic_source": src,
-                         "algorithmic_bytes_per_iteration": row_b + col_b, "ms_per_iteration": round(per, 5)}}
+                         "algorithmic_bytes_per_iteration": row_b + col_b, "ms_per_iteration": round(per, 5),
+                         **_stream_fields(rf, w, kd, logd, per, peak)}}
 
 
 def _warm_start_leg(args, w, S, x, y, a, b, kd, logd, cold):

@@ -169,6 +169,11 @@ typedef struct {
   int32_t launches;    /* kernels this call launched (including iterations enqueued after the stop flag) */
   int32_t iters_enqueued; /* iterations enqueued (>= iters; the surplus returned at once) */
   int32_t gather;      /* how the iterations read the sketch: SPS_PASS_* below */
+  float ms_setup;      /* device time of the part of ms_iter before the iteration kernels: the
+                          initial pair, and in the log domain the exact first iteration, the
+                          absorption and the staged passes' grouped copies */
+  int64_t stream_bytes; /* gather == STAGED: bytes of the two grouped copies, which one iteration
+                           reads once each (0 otherwise) */
 } sps_result;
 
 /* sps_result.gather.  DIRECT: every product gathers the scaling vector from

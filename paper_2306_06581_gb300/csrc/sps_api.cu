@@ -103,6 +103,7 @@ static void plan_staging(int n, int m, int mode, int kd, Layout* L, Take& take) 
     L->el_tmp[s] = take((size_t)rows[s] * 12);
     L->el_perm[s] = take((size_t)L->cap * 4);
     L->el_pack[s] = take((size_t)L->el_pack_cap);
+    L->el_logk[s] = take((size_t)(L->el_pack_cap / vb) * 4);
   }
 }
 
@@ -300,7 +301,7 @@ static sps_status read_ctrl(const Layout& L, char* ws, Ctrl* h, cudaStream_t st)
 
 
 struct Events {
-  cudaEvent_t e[4];
+  cudaEvent_t e[5];   // start, sketch done, iterations done, objective done; 4: iteration setup done
   bool ok = false;
   Events() { ok = true; for (auto& x : e) if (cudaEventCreate(&x) != cudaSuccess) ok = false; }
   ~Events() { for (auto& x : e) cudaEventDestroy(x); }
@@ -356,7 +357,7 @@ typedef sps_status (*RowFn)(const ProbDev&, const Layout&, char*, const IterCfg&
 static thread_local int g_iters_enqueued = 0;
 
 static sps_status run_iterations(const ProbDev& pd, const Layout& L, char* ws, const IterCfg& ic, const sps_params* Q,
-                                 IterFn full, RowFn row_only, cudaStream_t st, Ctrl* h) {
+                                 IterFn full, RowFn row_only, cudaStream_t st, Ctrl* h, Events* ev) {
   int launched = 0;
   if (ic.log_domain && ic.dense) {
     SPS_TRY(launch_dense_lse_init(pd, L, ws, Q->init_alpha, Q->init_beta, st));
@@ -368,6 +369,7 @@ static sps_status run_iterations(const ProbDev& pd, const Layout& L, char* ws, c
   } else {
     SPS_TRY(launch_iter_init(pd, L, ws, ic, Q->init_alpha, Q->init_beta, st));
   }
+  ev->rec(4, st);   // the setup before the iteration kernels (a first exact iteration in the log domain)
   if (launched >= ic.max_iter) {
     SPS_TRY(read_ctrl(L, ws, h, st));
   }
@@ -464,11 +466,11 @@ static sps_status spar_sink_impl(const sps_problem* P, const sps_params* Q, void
     ic.lpr_cols = ic.lpr_rows;
   }
   if (ic.log_domain) {
-    SPS_TRY(run_iterations(pd, L, ws, ic, Q, launch_log_iterations, launch_log_row_only, st, &h));
+    SPS_TRY(run_iterations(pd, L, ws, ic, Q, launch_log_iterations, launch_log_row_only, st, &h, &ev));
     ev.rec(2, st);
     SPS_TRY(launch_log_objective(pd, L, ws, ic, alpha_out, beta_out, st));
   } else {
-    SPS_TRY(run_iterations(pd, L, ws, ic, Q, launch_sparse_iterations, launch_sparse_row_only, st, &h));
+    SPS_TRY(run_iterations(pd, L, ws, ic, Q, launch_sparse_iterations, launch_sparse_row_only, st, &h, &ev));
     ev.rec(2, st);
     SPS_TRY(launch_sparse_objective(pd, L, ws, ic, alpha_out, beta_out, st));
   }
@@ -480,8 +482,10 @@ static sps_status spar_sink_impl(const sps_problem* P, const sps_params* Q, void
   fill_result(&r, dr, h, Q, nnz);
   r.gather = (ic.log_domain && L.stage_w > 0) ? (h.ell_overflow ? SPS_PASS_STAGED_FALLBACK : SPS_PASS_STAGED)
                                               : SPS_PASS_DIRECT;
+  if (r.gather == SPS_PASS_STAGED) r.stream_bytes = h.ell_bytes[0] + h.ell_bytes[1];
   r.ms_sketch = ev.ms(0, 1);
   r.ms_iter = ev.ms(1, 2);
+  r.ms_setup = ev.ms(1, 4);
   r.ms_obj = ev.ms(2, 3);
   if (res) *res = r;
   if (r.status == SPS_ERR_NUMERIC) set_error("non-finite value in the iterates");
@@ -584,11 +588,11 @@ sps_status sinkhorn_dense(const sps_problem* prob, const sps_params* prm, void* 
   ic.dense = 1;
   ic.log_domain = prm->log_domain ? 1 : 0;
   if (ic.log_domain) {
-    SPS_TRY(run_iterations(pd, L, ws, ic, prm, launch_dense_lse_iterations, launch_dense_lse_row_only, st, &h));
+    SPS_TRY(run_iterations(pd, L, ws, ic, prm, launch_dense_lse_iterations, launch_dense_lse_row_only, st, &h, &ev));
     ev.rec(2, st);
     SPS_TRY(launch_dense_lse_objective(pd, L, ws, ic, alpha_out, beta_out, st));
   } else {
-    SPS_TRY(run_iterations(pd, L, ws, ic, prm, launch_dense_iterations, launch_dense_row_only, st, &h));
+    SPS_TRY(run_iterations(pd, L, ws, ic, prm, launch_dense_iterations, launch_dense_row_only, st, &h, &ev));
     ev.rec(2, st);
     SPS_TRY(launch_dense_objective(pd, L, ws, ic, alpha_out, beta_out, st));
   }
@@ -600,6 +604,7 @@ sps_status sinkhorn_dense(const sps_problem* prob, const sps_params* prm, void* 
   fill_result(&r, dr, h, prm, (int64_t)prob->n * prob->m);
   r.ms_sketch = ev.ms(0, 1);
   r.ms_iter = ev.ms(1, 2);
+  r.ms_setup = ev.ms(1, 4);
   r.ms_obj = ev.ms(2, 3);
   if (res) *res = r;
   if (r.status == SPS_ERR_NUMERIC) set_error("non-finite value in the iterates");

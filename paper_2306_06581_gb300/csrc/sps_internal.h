@@ -44,6 +44,7 @@ struct Ctrl {
   int pad_overflow;       // single-pass sketch: a padded (row, chunk) slot was too small
   int oob_code;           // a bounds check skipped an access (code of the place; 0: none)
   int ell_overflow;       // staged layout: the grouped copy would not fit its planned space (direct gathers instead)
+  long long ell_bytes[2]; // staged layout: bytes of the grouped copies (row pass, column pass)
   long long oob_index;    //   and the index it refused
 };
 
@@ -93,6 +94,7 @@ struct Layout {
   size_t el_tmp[2];                 //   layout scratch: (row, length, start) of every run of one slice
   size_t el_pack[2];                //   the grouped copy
   size_t el_perm[2];                //   CSR (CSC) position -> value slot of the grouped copy
+  size_t el_logk[2];                //   log K~ by value slot (-inf in padding), for absorptions in copy order
   int64_t el_pack_cap;              //   bytes planned for one grouped copy
   size_t pad_ofs, pad_col, pad_val, pad_lv, zsum, csum;   // single-pass sketch (0: two passes)
   size_t unit_r, unit_c;            // persistent iterations: unit starts over rows [n + 2] / columns [m + 2]
@@ -129,7 +131,7 @@ constexpr int kStgThreads = 32 * kEllWarps;        // its threads
 constexpr int kEllHdr = 80;                        // bytes of a group header
 constexpr int kEllBins = 256;                      // run-length bins of the sort (the last one holds >= 255)
 constexpr int kEllRing = 4096;                     // ring of one warp (a power of two)
-constexpr int kEllWin = 512;                       // window: one 16-byte copy per lane
+constexpr int kEllWin = 1024;                      // window: two 16-byte copies per lane
 __host__ __device__ constexpr long long ell_step_bytes(int vb) { return 32LL * (2 + vb); }
 __host__ __device__ constexpr long long ell_group_bytes(int h, int vb) { return kEllHdr + (long long)h * ell_step_bytes(vb); }
 // Dynamic shared memory of the staged kernel: the chunk of the gathered

@@ -71,6 +71,7 @@ struct LogArgs {
   int* el_tmp[2];
   unsigned char* el_pack[2];
   int* el_perm[2];
+  float* el_logk[2];               // log K~ by value slot of the grouped copy (-inf in padding)
   long long pack_lim;              // bytes of one grouped copy
   long long nnz_lim;               // elements of the CSR / CSC arrays (bounds checks)
 };
@@ -110,6 +111,21 @@ __global__ void __launch_bounds__(kT) k_lse_half(int rows, const int* ptr, const
   }
 }
 
+// The stored kernel value, step by step with explicit rounding (no
+// contraction into fused multiply-adds), so that both absorption paths (by
+// CSR / CSC segment and in grouped-copy order) store the same bits:
+// z = logK~ + (pot_i + other_j)/eps, e = floor(log2 of the row's largest
+// exp(z)), K' = 2^(z log2(e) - e).
+__device__ __forceinline__ float absorbed_z(float lk, float pi, float o, float inv_eps) {
+  return __fadd_rn(lk, __fmul_rn(__fadd_rn(pi, o), inv_eps));
+}
+__device__ __forceinline__ float absorbed_exponent(float zmax) {
+  return zmax == neg_inf() ? 0.0f : floorf(__fmul_rn(zmax, kLog2e));
+}
+__device__ __forceinline__ float absorbed_value(float z, float e) {
+  return exp2f(__fsub_rn(__fmul_rn(z, kLog2e), e));
+}
+
 // Write one row (CSR) or column (CSC) of K' = exp(logK~ + (pot_i + other_j)/eps)
 // scaled by 2^-e, e = floor(log2 of the largest value).
 template <typename V>
@@ -121,17 +137,17 @@ __device__ __forceinline__ void absorb_segment(int lo, int hi, const int* idx, c
   if (pot_i != neg_inf())
     for (int k = lo + lane; k < hi; k += 32) {
       const float o = other[idx[k]];
-      if (o != neg_inf()) mx = fmaxf(mx, logv[k] + (pot_i + o) * inv_eps);
+      if (o != neg_inf()) mx = fmaxf(mx, absorbed_z(logv[k], pot_i, o, inv_eps));
     }
   mx = warp_max(mx);
-  const float e = (mx == neg_inf()) ? 0.0f : floorf(mx * kLog2e);
+  const float e = absorbed_exponent(mx);
   for (int k = lo + lane; k < hi; k += 32) {
     const float o = other[idx[k]];
     float z = neg_inf();
-    if (pot_i != neg_inf() && o != neg_inf()) z = logv[k] + (pot_i + o) * inv_eps;
+    if (pot_i != neg_inf() && o != neg_inf()) z = absorbed_z(logv[k], pot_i, o, inv_eps);
     const int dst = perm ? perm[k] : k;
     if (perm && (dst < 0 || (long long)dst >= limit)) { oob(ctrl, 1, dst); continue; }
-    out[dst] = from_d<V>((double)exp2f(z * kLog2e - e));
+    out[dst] = from_d<V>((double)absorbed_value(z, e));
   }
   if (lane == 0) *e_out = e;
 }
@@ -157,10 +173,11 @@ __global__ void __launch_bounds__(kT) k_absorb_all(LogArgs A, int t) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const AbsorbOut<V> R = absorb_out<V>(A, 0), C = absorb_out<V>(A, 1);
-  for (int i = gw; i < A.n; i += nw)
+  const bool grouped = R.perm != nullptr;   // the grouped copies were written by k_absorb_pack
+  for (int i = gw; i < A.n && !grouped; i += nw)
     absorb_segment<V>(A.row_ptr[i], A.row_ptr[i + 1], A.col_idx, A.logval, A.alpha[i], A.beta, A.inv_eps, R.out,
                       A.erow + i, lane, R.perm, R.limit, A.ctrl);
-  for (int j = gw; j < A.m; j += nw)
+  for (int j = gw; j < A.m && !grouped; j += nw)
     absorb_segment<V>(A.col_ptr[j], A.col_ptr[j + 1], A.row_idx, A.logvalT, A.beta[j], A.alpha, A.inv_eps, C.out,
                       A.ecol + j, lane, C.perm, C.limit, A.ctrl);
   // scalings of the pair t: 1 where the potential is finite, 0 where the row / column is unreachable
@@ -191,6 +208,7 @@ __global__ void k_log_init(int n, int m, float* alpha, float* beta, const T* al0
     ctrl->blocks_a = ctrl->blocks_b = ctrl->blocks_c = 0u;
     ctrl->bar_count = 0u;
     ctrl->ell_overflow = 0;
+    ctrl->ell_bytes[0] = ctrl->ell_bytes[1] = 0;
     if (ctrl->status != SPS_OK) ctrl->done = 1;
   }
 }
@@ -324,8 +342,8 @@ __device__ __forceinline__ void cp_async_wait_n(int n) {
     default: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
   }
 }
-static_assert(kEllWins == 8, "cp_async_wait_n covers eight windows");
-static_assert(kEllWin == 32 * 16, "a window is one 16-byte copy per lane");
+static_assert(kEllWins >= 2 && kEllWins <= 8, "cp_async_wait_n covers up to eight windows");
+static_assert(kEllWin % (32 * 16) == 0, "a window is a whole number of 16-byte copies per lane");
 
 template <typename V> __device__ __forceinline__ float ring_val(const unsigned char* p);
 template <> __device__ __forceinline__ float ring_val<float>(const unsigned char* p) {
@@ -342,8 +360,8 @@ template <> __device__ __forceinline__ float ring_val<__half>(const unsigned cha
 // positions relative to a0 (s0 rounded down to a window), pass through the
 // warp's ring; relative byte r sits at ring[r mod kEllRing] while resident.
 // Window k is the relative bytes [k kEllWin, (k + 1) kEllWin), clipped to the
-// stream; lane l copies its 16 bytes of each window (cp.async through L2) and
-// commits one group per window, so window k has landed for the lane once at
+// stream; lane l copies its 16-byte pieces l, l + 32, ... of each window
+// (cp.async through L2) and commits one group per window, so window k has landed for the lane once at
 // most (issued - 1 - k) of its groups are pending.  Window k is issued once
 // every byte of window k - kEllWins has been read by the whole warp.
 struct EllRing {
@@ -362,8 +380,11 @@ __device__ __forceinline__ void ell_need(EllRing& R, unsigned cons, unsigned end
   const unsigned lim = min(R.nwin, cons / kEllWin + kEllWins);
   const unsigned l16 = 16u * (threadIdx.x & 31);
   while (R.issued < lim) {
-    const unsigned r = R.issued * kEllWin + l16;
-    if (r >= R.r0 && r < R.r1) cp_async16(R.ring + (r & (kEllRing - 1)), R.src + r);
+#pragma unroll
+    for (int j = 0; j < kEllWin / 512; ++j) {
+      const unsigned r = R.issued * kEllWin + 512u * j + l16;
+      if (r >= R.r0 && r < R.r1) cp_async16(R.ring + (r & (kEllRing - 1)), R.src + r);
+    }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     ++R.issued;
   }
@@ -663,7 +684,7 @@ __global__ void __launch_bounds__(256) k_el_size(int rows, int R, int nblk, int 
 // ell_overflow (the passes then gather directly).
 __global__ void __launch_bounds__(1024) k_el_scan(long long P, const long long* __restrict__ pbytes,
                                                   long long* __restrict__ poff, long long cap_bytes, int vb,
-                                                  Ctrl* ctrl) {
+                                                  Ctrl* ctrl, int side) {
   __shared__ long long sh[1024];
   const int t = threadIdx.x, T = blockDim.x;
   const long long per = (P + T - 1) / T;
@@ -686,6 +707,7 @@ __global__ void __launch_bounds__(1024) k_el_scan(long long P, const long long* 
   if (t == T - 1) {
     const long long tot = sh[T - 1];
     poff[P] = tot;
+    ctrl->ell_bytes[side] = tot;
     if (tot > cap_bytes || tot / vb > 0x7fffffffLL) ctrl->ell_overflow = 1;
   }
 }
@@ -701,6 +723,7 @@ __global__ void __launch_bounds__(256) k_el_fill(int rows, int R, int nblk, int 
                                                  const int* __restrict__ idx, const int* __restrict__ S,
                                                  const long long* __restrict__ poff, int* __restrict__ tmp,
                                                  unsigned char* __restrict__ pack, int* __restrict__ perm,
+                                                 const float* __restrict__ logv, float* __restrict__ logk,
                                                  long long nnz_lim, long long pack_lim, Ctrl* ctrl) {
   constexpr int vb = (int)sizeof(V);
   __shared__ int hist_sh[8][kEllBins];
@@ -781,12 +804,15 @@ __global__ void __launch_bounds__(256) k_el_fill(int rows, int R, int nblk, int 
       constexpr long long st = ell_step_bytes(vb);
       for (int k = 0; k < h; ++k) {
         unsigned char* sp = gp + kEllHdr + k * st;   // step k: 32 indices, then 32 values
+        const long long slot = (off + kEllHdr + k * st + 64) / vb + lane;
         unsigned short q = 0;
+        float lk = neg_inf();
         if (k < len) {
           const long long e = (long long)src + k;
           if (e >= 0 && e < nnz_lim) {
             q = (unsigned short)(idx[e] - c * W);
-            perm[e] = (int)((off + kEllHdr + k * st + 64) / vb + lane);
+            perm[e] = (int)slot;
+            lk = logv[e];
           } else {
             oob(ctrl, 9, e);
             ctrl->ell_overflow = 1;
@@ -794,6 +820,7 @@ __global__ void __launch_bounds__(256) k_el_fill(int rows, int R, int nblk, int 
         } else {
           reinterpret_cast<V*>(sp + 64)[lane] = from_d<V>(0.0);
         }
+        logk[slot] = lk;
         reinterpret_cast<unsigned short*>(sp)[lane] = q;
       }
       off += ell_group_bytes(h, vb);
@@ -811,6 +838,121 @@ __global__ void __launch_bounds__(256) k_el_fill(int rows, int R, int nblk, int 
     oob(ctrl, 6, sl);
     ctrl->ell_overflow = 1;
   }
+}
+
+// Absorption in copy order, one side (0: rows over the CSR copy, 1: columns
+// over the CSC copy) of this block's rows:
+// K' = exp(logK~ + (pot_i + other_j)/eps) 2^-e_i, e_i = floor(log2 of row i's
+// largest value), the formula of absorb_segment element for element, so the
+// stored values are the same.  Pass 1 takes each row's maximum (lane l of a
+// group holds row l, and a slice's rows belong to one warp, so mx needs no
+// atomics), pass 2 writes the values over the groups' value steps, every
+// write a whole 32-lane row of a step.  The other side's potentials pass
+// through shared memory (xs) chunk by chunk, as the gathered vector does in
+// ell_pass.  mx: shared scratch of the block's rows.
+template <typename V>
+__device__ void ell_absorb(const LogArgs& A, int side, float* xs, float* mx) {
+  constexpr int vb = (int)sizeof(V);
+  constexpr long long st = ell_step_bytes(vb);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int R = side ? A.cols_pb : A.rows_pb;
+  const int rows = side ? A.m : A.n;
+  const int r0 = blockIdx.x * R;
+  const int nr = max(0, min(rows, r0 + R) - r0);
+  const int J = side ? A.Jc : A.Jr;
+  const int nx = side ? A.n : A.m;
+  const float* pot = side ? A.beta : A.alpha;
+  const float* oth = side ? A.alpha : A.beta;
+  float* e_out = side ? A.ecol : A.erow;
+  const unsigned char* pack = A.el_pack[side];
+  V* val = reinterpret_cast<V*>(A.el_pack[side]);
+  const float* logk = A.el_logk[side];
+  const long long* po = A.el_poff[side] + ((size_t)blockIdx.x * kEllWarps + warp) * J;
+  for (int k = threadIdx.x; k < nr; k += blockDim.x) mx[k] = neg_inf();
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    long long off = __ldg(po);
+    long long s1 = __ldg(po + J);
+    if (off < 0 || s1 < off || s1 > A.pack_lim) {   // inconsistent slice bounds: skip the slice
+      if (lane == 0) oob(A.ctrl, 2, s1);
+      off = s1 = 0;
+    }
+    for (int c = 0; c < J; ++c) {
+      const long long pe = min(max(__ldg(po + c + 1), off), s1);
+      const int j0 = c * A.W, jn = min(A.W, nx - j0);
+      __syncthreads();   // the previous chunk is no longer read
+      for (int k = threadIdx.x; k < jn; k += blockDim.x) xs[k] = __ldcg(oth + j0 + k);
+      __syncthreads();
+      while (off < pe) {
+        const int H = __ldg(reinterpret_cast<const int*>(pack + off + 64));
+        const unsigned row = __ldg(reinterpret_cast<const unsigned short*>(pack + off) + lane);
+        if (H < 1 || off + ell_group_bytes(H, vb) > pe) {
+          if (lane == 0) oob(A.ctrl, 4, off);
+          off = pe;
+          break;
+        }
+        const bool mine = row < (unsigned)nr;
+        const float pi = mine ? __ldcg(pot + r0 + row) : neg_inf();
+        const float ei = (pass == 1 && mine) ? mx[row] : 0.0f;
+        float m = neg_inf();
+        // eight steps at a time: their indices and log K~, then the staged
+        // potentials, then the values (loads first: the stores go to the
+        // same buffer as the indices)
+        for (int k0 = 0; k0 < H; k0 += 8) {
+          const int nk = min(8, H - k0);
+          unsigned q[8];
+          float lk[8], o[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            q[u] = 0u;
+            lk[u] = neg_inf();
+            if (u < nk) {
+              const long long so = off + kEllHdr + (long long)(k0 + u) * st;
+              q[u] = __ldg(reinterpret_cast<const unsigned short*>(pack + so) + lane);
+              lk[u] = __ldg(logk + (so + 64) / vb + lane);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) o[u] = u < nk ? xs[min(q[u], (unsigned)(jn - 1))] : neg_inf();
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (u < nk) {
+              float z = neg_inf();
+              if (pi != neg_inf() && o[u] != neg_inf()) z = absorbed_z(lk[u], pi, o[u], A.inv_eps);
+              if (pass == 0) {
+                m = fmaxf(m, z);
+              } else {
+                const long long so = off + kEllHdr + (long long)(k0 + u) * st;
+                val[(so + 64) / vb + lane] = from_d<V>((double)absorbed_value(z, ei));
+              }
+            }
+          }
+        }
+        if (pass == 0 && mine) mx[row] = fmaxf(mx[row], m);
+        off += ell_group_bytes(H, vb);
+      }
+      off = max(off, pe);
+    }
+    __syncthreads();
+    if (pass == 0) {
+      for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+        const float e = absorbed_exponent(mx[k]);
+        mx[k] = e;
+        e_out[r0 + k] = e;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// The first absorption of a staged solve, in copy order (block b of the
+// staged kernel's grid owns the same rows and columns here).
+template <typename V>
+__global__ void __launch_bounds__(kStgThreads, 1) k_absorb_pack(LogArgs A) {
+  extern __shared__ __align__(16) float absorb_sh[];   // W entries of the other side's potentials, then rows
+  if (*(volatile int*)&A.ctrl->ell_overflow) return;
+  ell_absorb<V>(A, 0, absorb_sh, absorb_sh + A.W);
+  ell_absorb<V>(A, 1, absorb_sh, absorb_sh + A.W);
 }
 
 // Fold the scalings of the pair t into the potentials (this block's rows and
@@ -946,7 +1088,16 @@ __global__ void __launch_bounds__(STG ? kStgThreads : kIterThreads, 1) k_iterate
     if (absorb_now) {
       fold_scalings(A, t + 1);
       if (!grid_barrier(ctrl)) return;
-      rewrite_block<V>(A);
+      if constexpr (STG) {
+        if (grp) {
+          ell_absorb<V>(A, 0, dsm, dsm + A.W);
+          ell_absorb<V>(A, 1, dsm, dsm + A.W);
+        } else {
+          rewrite_block<V>(A);
+        }
+      } else {
+        rewrite_block<V>(A);
+      }
       if (!grid_barrier(ctrl)) return;
       if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->n_absorb += 1;
     }
@@ -1043,6 +1194,7 @@ LogArgs make_log_args(const ProbDev& pd, const Layout& L, char* ws, const IterCf
     A.el_tmp[s] = A.stage ? at<int>(ws, L.el_tmp[s]) : nullptr;
     A.el_pack[s] = A.stage ? at<unsigned char>(ws, L.el_pack[s]) : nullptr;
     A.el_perm[s] = A.stage ? at<int>(ws, L.el_perm[s]) : nullptr;
+    A.el_logk[s] = A.stage ? at<float>(ws, L.el_logk[s]) : nullptr;
   }
   A.pack_lim = A.stage ? L.el_pack_cap : 0;
   A.nnz_lim = L.cap;
@@ -1186,11 +1338,19 @@ void first_iteration_v(const LogArgs& A, const IterCfg& ic, const void* al0, con
       k_el_slices<<<(A.sblk * (kEllWarps + 1) + 255) / 256, 256, 0, st>>>(rows, R, A.sblk, ptr, A.el_slice[side]);
       k_el_size<<<(slices + 7) / 8, 256, 0, st>>>(rows, R, A.sblk, J, seg, A.el_slice[side], (int)sizeof(V),
                                                   A.el_pbytes[side], A.ctrl);
-      k_el_scan<<<1, 1024, 0, st>>>(P, A.el_pbytes[side], A.el_poff[side], A.pack_lim, (int)sizeof(V), A.ctrl);
+      k_el_scan<<<1, 1024, 0, st>>>(P, A.el_pbytes[side], A.el_poff[side], A.pack_lim, (int)sizeof(V), A.ctrl,
+                                    side);
       k_el_fill<V><<<(slices + 7) / 8, 256, 0, st>>>(rows, R, A.sblk, J, A.W, seg, idx, A.el_slice[side],
                                                      A.el_poff[side], A.el_tmp[side], A.el_pack[side],
-                                                     A.el_perm[side], A.nnz_lim, A.pack_lim, A.ctrl);
+                                                     A.el_perm[side], side ? A.logvalT : A.logval,
+                                                     A.el_logk[side], A.nnz_lim, A.pack_lim, A.ctrl);
     }
+  }
+  if (A.stage) {
+    // a refused attribute makes the launch fail, and the caller reports it
+    const size_t sm = sizeof(float) * ((size_t)A.W + std::max(A.rows_pb, A.cols_pb));
+    cudaFuncSetAttribute((const void*)k_absorb_pack<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_absorb_pack<V><<<A.sblk, kStgThreads, sm, st>>>(A);
   }
   k_absorb_all<V><<<grid1((int64_t)std::max(A.n, A.m) * 32, kT), kT, 0, st>>>(A, 1);
   (void)ic;
@@ -1206,7 +1366,7 @@ sps_status launch_log_first_iteration(const ProbDev& pd, const Layout& L, char* 
     case SPS_F16: first_iteration_v<__half>(A, ic, init_alpha, init_beta, st); break;
     default: first_iteration_v<float>(A, ic, init_alpha, init_beta, st); break;
   }
-  add_launches(A.stage ? 14 : 4);
+  add_launches(A.stage ? 15 : 4);
   return cuda_fail(cudaGetLastError(), "log-domain first iteration");
 }
 

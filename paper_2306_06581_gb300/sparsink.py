@@ -67,7 +67,7 @@ class Result(C.Structure):
                 ("unreach_a", C.c_double), ("unreach_b", C.c_double), ("nnz", C.c_int64),
                 ("n_absorb", C.c_int32), ("ms_sketch", C.c_float), ("ms_iter", C.c_float),
                 ("ms_obj", C.c_float), ("launches", C.c_int32), ("iters_enqueued", C.c_int32),
-                ("gather", C.c_int32)]
+                ("gather", C.c_int32), ("ms_setup", C.c_float), ("stream_bytes", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -113,3 +113,19 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"]["workload"] == inputs.ot_n1000().name
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_kernel_time_excludes_the_iteration_setup():
+    # 1 setup iteration (log domain) + 199 kernel iterations; 30 ms of the phase is setup
+    r = {"ms_iter": 30.0 + 199 * 0.9, "ms_setup": 30.0, "iters_enqueued": 200}
+    assert abs(bench._kernel_ms_per_iteration(r, 1) - 0.9) < 1e-12
+    r = {"ms_iter": 0.01 + 200 * 0.2, "ms_setup": 0.01, "iters_enqueued": 200}
+    assert abs(bench._kernel_ms_per_iteration(r, 0) - 0.2) < 1e-12
+
+
+def test_stream_bytes_replace_the_element_bytes_only():
+    res = {"nnz": 1000, "stream_bytes": 7000}
+    row, col = bench._spmv_bytes(res, 100, 120, "f32", 1)
+    vec = row + col - 2 * 1000 * 8 - 4 * 101 - 4 * 121
+    assert bench._stream_bytes(res, 100, 120, "f32", 1) == 7000 + vec
+    assert bench._stream_bytes({"nnz": 1000, "stream_bytes": 0}, 100, 120, "f32", 1) is None
