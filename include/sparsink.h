@@ -257,9 +257,9 @@ sps_status spar_sink_uot(const sps_problem* prob, const sps_params* prm, void* w
  * CUDA events that time its phases.  The first call made on a device in a
  * CUDA context (with that device current) looks up the array's device address
  * with cudaGetSymbolAddress; later calls in the same context reuse it, and a
- * new context (after cudaDeviceReset, say) gets its own lookup.  Make that
- * first call before any stream capture begins.  Like spar_sink_ot, the call
- * waits for its stream and reads the result back before it returns.
+ * new context (after cudaDeviceReset, say) gets its own lookup.  Like
+ * spar_sink_ot, the call waits for its stream and reads the result back
+ * before it returns.
  * Problems whose sps_workspace_bytes(..., SPS_OP_SPAR_SINK) exceeds the array
  * are rejected with SPS_ERR_WORKSPACE before any launch.  All calls share the
  * array, which keeps the last call's contents (each call clears what must
