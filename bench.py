@@ -85,7 +85,7 @@ def run_batch(args):
     sets, pairs, s = _frames_batch()
     kd = args.kdtype or "f32"
     kw = dict(eps=0.01, lam=1.0, tol=TOL, max_iter=20000, seed=0x5EED, problem_id=rank * len(pairs),
-              cost_norm=S.COST_SCALE, cost_scale=inputs.FRAME_COST_SCALE, kdtype=kd)
+              cost_norm=S.COST_SCALE, cost_scale=inputs.FRAME_COST_SCALE, kdtype=kd, sampler=args.sampler)
     dsets = [(torch.tensor(x, dtype=torch.float32, device=dev), torch.tensor(w, dtype=torch.float32, device=dev))
              for x, w in sets]
     stream = torch.cuda.Stream(dev)
@@ -114,6 +114,21 @@ def run_batch(args):
         clk = clocks.stop()
         # un-captured run for the phase split (sketch vs iterations + objective)
         split = S.spar_sink_batched(dsets, pairs, s, workspace=ws, **kw)
+        # the other sampler on the same batch (its own workspace), for the sketch comparison
+        other = "element" if args.sampler == "skip" else "skip"
+        okw = dict(kw, sampler=other)
+        o1 = S.spar_sink_batched(dsets, pairs, s, **okw)
+        torch.cuda.synchronize()
+        oe0, oe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        oe0.record(stream)
+        o2 = S.spar_sink_batched(dsets, pairs, s, workspace=o1["workspace"], **okw)
+        oe1.record(stream)
+        oe1.synchronize()
+        other_line = {"sampler": other, "ms": round(oe0.elapsed_time(oe1), 3),
+                      "phases_ms": {"sketch": round(o2["results"][0]["ms_sketch"], 3),
+                                    "iterations_and_objective": round(o2["results"][0]["ms_iter"], 3)},
+                      "nnz_total": int(sum(r["nnz"] for r in o2["results"]))}
+        del o1, o2
     ms = sum(times) / len(times)
     if world > 1:
         ms = _max_over_ranks(ms, dist, dev)
@@ -164,8 +179,9 @@ def run_batch(args):
                    "eps": 0.01, "lambda": 1.0, "tol": TOL, "s": "8 s0(sqrt(n_i n_j)) per pair",
                    "cost": "squared pixel distance / (2 95^2)", "value_dtype": kd, "log_domain": 1,
                    "l2": "flushed between steps (512 MB write)", "graph": "captured once, replayed per step",
-                   "parallelism": "replicas (one batch per GPU)"},
+                   "parallelism": "replicas (one batch per GPU)", "sampler": args.sampler},
         "pairs_per_s": round(len(pairs) / (ms * 1e-3), 1),
+        "other_sampler": other_line,
         "phases_ms": {"sketch": round(split["results"][0]["ms_sketch"], 3), "iterations_and_objective": round(it_ms, 3)},
         "iters": {"mean": float(iters.mean()), "max": int(iters.max()), "min": int(iters.min())},
         "not_converged": int(sum(r["status"] != 0 for r in res)), "nnz_total": int(nnz.sum()),
@@ -184,14 +200,14 @@ def run_batch(args):
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _batch_cpu_baseline(sets, pairs, s)
+        line["cpu_baseline"] = _batch_cpu_baseline(sets, pairs, s, sampler=args.sampler)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def _batch_cpu_baseline(sets, pairs, s, k=2):
+def _batch_cpu_baseline(sets, pairs, s, k=2, sampler="element"):
     import numpy as np
 
     import oracle
@@ -205,12 +221,12 @@ def _batch_cpu_baseline(sets, pairs, s, k=2):
         f = lambda z: np.asarray(z, np.float32).astype(np.float64)
         P = oracle.OracleProblem(f(a), f(b), 0.01, s[p], 1.0, x=f(x), y=f(y), seed=0x5EED, pid=p,
                                  cost_norm=2, cost_scale=inputs.FRAME_COST_SCALE)
-        oracle.spar_sink(P, tol=TOL, max_iter=20000, log_domain=True)
+        oracle.spar_sink(P, tol=TOL, max_iter=20000, log_domain=True, sketch=P.sparsify(sampler=sampler))
     el = (time.perf_counter() - t0) * 1e3
     return {"value": round(el / len(samp) * len(pairs), 1), "unit": UNIT,
             "cores": int(os.environ.get("OMP_NUM_THREADS", _threads())), "kind": "oracle",
-            "sample": f"FP64 oracle Spar-Sink (log domain) of {len(samp)} of the {len(pairs)} pairs, "
-                      f"{el / 1e3:.1f} s, scaled to all pairs"}
+            "sample": f"FP64 oracle Spar-Sink (log domain, {sampler} sampler) of {len(samp)} of the {len(pairs)} "
+                      f"pairs, {el / 1e3:.1f} s, scaled to all pairs"}
 
 
 def _workload(name, n=None):
@@ -794,7 +810,7 @@ def run_reference(args):
         times = []
         t_start = time.perf_counter()
         for k in range(args.steps):
-            b = _batch_cpu_baseline(sets, pairs, s)
+            b = _batch_cpu_baseline(sets, pairs, s, sampler=args.sampler)
             times.append(b["value"])
             if time.perf_counter() - t_start > 200.0:
                 break

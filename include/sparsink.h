@@ -125,8 +125,10 @@ typedef struct {
                           kept independently with probability p*_ij) from a different random
                           stream, with work proportional to the sampled count (the UOT
                           normaliser Z is still an exact sum over all pairs).  sketch_mode
-                          does not apply to it; spar_sink_batched accepts SPS_SAMPLER_ELEMENT
-                          only. */
+                          does not apply to it.  spar_sink_batched takes both; with either,
+                          pair p's sketch is the one a single solve with problem id
+                          problem_id + p draws (its row bound takes the largest factor of the
+                          pair's target set). */
   int32_t probs;       /* Sampling probabilities of Eq. (pois).  SPS_PROBS_PAPER (0):
                           Eq. (pij-ot) for OT, Eq. (pij-uot) for UOT.  SPS_PROBS_EQUAL (1):
                           p_ij = 1/(n m) for every element, p*_ij = min(1, s/(n m)) -- the

@@ -66,6 +66,7 @@ struct BatchDev {
   double cost_scale, eps, lam, tol;
   float gamma32, phi, inv_phi, inv_eps, eps32, inv_lam, tau;
   int max_iter;
+  int skip;                       // sketch by the skip sampler (else one decision per element)
   uint64_t seed;
   long long R, M, P;              // total rows, columns, set points
   const PairDesc* pairs;
@@ -354,6 +355,162 @@ __global__ void __launch_bounds__(kBT) k_b_sweep(BatchDev B) {
     if (MODE == SW_MAX) {
       dmax = warp_max(dmax);
       if (lane == 0 && dmax > 0.0f) atomicMax(&B.ps[zp].dmax_bits, __float_as_uint(dmax));
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Skip sampler for the batch (sampler = SPS_SAMPLER_SKIP): per row the stream
+// of the single-problem skip sampler (k_skip in sps_sweep.cu) with the pair's
+// problem id, so every pair's sketch is the one a single solve with that id
+// draws.  Row i of pair p bounds every p_ij by q_i: OT q_i = min(1,
+// fl(r_i cmax)), UOT q_i = min(1, fl(scale fl(A_i cmax))), cmax the largest
+// decision factor of the target set.  Candidates are a Bernoulli(q_i) process
+// of geometric gaps G = floor(log U / log(1 - q_i)), U = ((w >> 8) + 1) 2^-24;
+// candidate j is kept when V < fl(p_ij / q_i), V = (w' >> 8) 2^-24; candidate t
+// of row i reads Philox at counter (t >> 1, i, pid, 0x5B1E).  A warp takes 64
+// candidates at a time (lane l: candidates 2l and 2l + 1 of the round, one
+// Philox call) and places them by a prefix sum of the steps 1 + G.
+// ----------------------------------------------------------------------------
+enum { BK_COUNT = 0, BK_FILL = 1 };
+
+template <int MODE, bool UOT, int DM>
+__global__ void __launch_bounds__(kBT) k_b_skip(BatchDev B) {
+  if (B.ctrl->status != SPS_OK) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (;;) {
+    long long r0 = 0;
+    if (lane == 0) r0 = (long long)atomicAdd(&B.queue[MODE == BK_COUNT ? Q_COUNT : Q_FILL], 1u) * kGrabRows;
+    r0 = __shfl_sync(0xffffffffu, r0, 0);
+    if (r0 >= B.R) break;
+    const long long r1 = min(B.R, r0 + kGrabRows);
+    int p = pair_of_row(B, r0);
+    for (long long r = r0; r < r1; ++r) {
+      while (r >= B.ro_tab[p + 1]) ++p;
+      const PairDesc P = B.pairs[p];
+      const int i = (int)(r - P.ro);
+      const int m = P.m;
+      if (B.out[p].status != SPS_OK) {   // the pair's scalars failed: no elements
+        if (MODE == BK_COUNT && lane == 0) B.row_cnt[r] = 0;
+        continue;
+      }
+      const long long xk = P.xo + i;
+      const PairScal* S = B.ps + p;
+      float ri = B.fac[xk];
+      if (!UOT) ri = __fmul_rn(__fmul_rn(S->s32, ri), S->scale32);
+      const float cmax = __uint_as_float(B.ss[P.dst].fmax_bits);
+      const float kappa = S->kappa32, scale = S->scale32;
+      const float q = UOT ? __fmul_rn(scale, __fmul_rn(ri, cmax)) : __fmul_rn(ri, cmax);
+      float xi[DM];
+#pragma unroll
+      for (int k = 0; k < DM; ++k) xi[k] = k < B.d ? B.x32[xk * B.d + k] : 0.0f;
+      float k_hi = 0.0f, k_lo = 0.0f;
+      if (MODE == BK_FILL) {
+        const double k64 = 1.0 / (S->dn64 * B.eps);
+        k_hi = __double2float_rn(k64);
+        k_lo = __double2float_rn(k64 - (double)k_hi);
+      }
+      int cnt = 0;
+      int pos = MODE == BK_FILL ? B.row_ptr[r] : 0;
+      const int pend = MODE == BK_FILL ? B.row_ptr[r + 1] : 0;
+      if (q > 0.0f) {
+        const bool full = q >= 1.0f;
+        const float L = full ? 0.0f : spec_log1m(q);
+        long long jprev = -1;
+        for (uint32_t call0 = 0;; call0 += 32) {
+          const uint4 w4 = skip_words4(B.seed, P.pid, (uint32_t)i, call0 + (uint32_t)lane);
+          // gaps of the lane's two candidates; an invalid gap ends the row there
+          bool ok0 = true, ok1 = true;
+          long long st0 = 1, st1 = 1;
+          if (!full) {
+            const float g0 = __fdiv_rn(spec_log(__fmul_rn(__uint2float_rn((w4.x >> 8) + 1u), 5.9604644775390625e-08f)), L);
+            const float g1 = __fdiv_rn(spec_log(__fmul_rn(__uint2float_rn((w4.z >> 8) + 1u), 5.9604644775390625e-08f)), L);
+            ok0 = g0 < (float)m;
+            ok1 = g1 < (float)m;
+            st0 = ok0 ? 1 + (long long)floorf(g0) : 0;
+            st1 = ok1 ? 1 + (long long)floorf(g1) : 0;
+          }
+          const unsigned bad = __ballot_sync(0xffffffffu, !ok0 || !ok1);
+          int tstop = 64;
+          if (bad) {
+            const int fl = __ffs(bad) - 1;
+            const bool b0 = __shfl_sync(0xffffffffu, !ok0, fl);
+            tstop = 2 * fl + (b0 ? 0 : 1);
+          }
+          const long long tot = st0 + st1;
+          long long inc = tot;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+          }
+          const long long j0 = jprev + (inc - tot) + st0;
+          const long long j1 = j0 + st1;
+          const bool in0 = 2 * lane < tstop && j0 < m;
+          const bool in1 = 2 * lane + 1 < tstop && j1 < m;
+          bool keep_[2] = {false, false};
+          float pv[2] = {0.0f, 0.0f};
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const bool in = e == 0 ? in0 : in1;
+            if (!in) continue;
+            const long long yk = P.yo + (e == 0 ? j0 : j1);
+            float pr;
+            if (UOT) {
+              const float D = spec_dist<DM>(xi, B.x32 + yk * B.d, B.d);
+              pr = __fmul_rn(scale, __fmul_rn(__fmul_rn(ri, B.fac[yk]), spec_exp(-__fmul_rn(D, kappa))));
+            } else {
+              pr = __fmul_rn(ri, B.fac[yk]);
+            }
+            const float a_ = full ? pr : __fdiv_rn(pr, q);
+            const uint32_t h = e == 0 ? w4.y : w4.w;
+            keep_[e] = __fmul_rn(__uint2float_rn(h >> 8), 5.9604644775390625e-08f) < a_;
+            pv[e] = pr;
+          }
+          const unsigned m0 = __ballot_sync(0xffffffffu, keep_[0]), m1 = __ballot_sync(0xffffffffu, keep_[1]);
+          if (MODE == BK_COUNT) {
+            cnt += __popc(m0) + __popc(m1);
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+              if (keep_[e]) atomicAdd(&B.col_cnt[P.co + (e == 0 ? j0 : j1)], 1);
+          } else {
+            int wpos = pos + __popc(m0 & lt) + __popc(m1 & lt);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              if (!keep_[e]) continue;
+              const int jj = (int)(e == 0 ? j0 : j1);
+              if (wpos >= pend) {   // count and fill disagree: never write out of range
+                B.ctrl->sketch_fault = 1;
+                continue;
+              }
+              const float ps = pv[e] < 1.0f ? pv[e] : 1.0f;
+              B.col_idx[wpos] = jj;
+              if (B.x64) {
+                const double C = dist64(B, xk, P.yo + jj) / S->dn64;
+                B.logval[wpos] = (float)(-C / B.eps - (double)logf(ps));
+              } else {
+                B.logval[wpos] =
+                    __fsub_rn(-cost_over_eps_df(xi, B.x32 + (P.yo + jj) * B.d, B.d, k_hi, k_lo), logf(ps));
+              }
+              const int slot = atomicAdd(&B.col_cur[P.co + jj], 1);
+              if (slot < B.col_ptr[P.co + jj + 1]) {
+                B.tmp_row[slot] = i;
+                B.tmp_src[slot] = wpos;
+              } else {
+                B.ctrl->sketch_fault = 1;
+              }
+              ++wpos;
+            }
+            pos += __popc(m0) + __popc(m1);
+          }
+          // the row ends at an invalid gap or once a position reaches m
+          const long long jlast = __shfl_sync(0xffffffffu, j1, 31);
+          if (tstop < 64 || jlast >= m) break;
+          jprev = jlast;
+        }
+      }
+      if (MODE == BK_COUNT && lane == 0) B.row_cnt[r] = cnt;   // cnt is the same on every lane (ballot counts)
     }
   }
 }
@@ -794,7 +951,7 @@ bool plan(const sps_batch* Bt, const sps_params* Q, Plan* L, std::vector<PairDes
 sps_status validate_batch(const sps_batch* Bt, const sps_params* Q) {
   if (!Bt || !Q) { set_error("null batch or params"); return SPS_ERR_INVALID_ARG; }
   if (Bt->n_sets < 1 || Bt->n_pairs < 1) { set_error("empty batch"); return SPS_ERR_INVALID_ARG; }
-  if (Q->sampler != SPS_SAMPLER_ELEMENT) { set_error("the batched solver draws one decision per element (sampler 0)"); return SPS_ERR_INVALID_ARG; }
+  if (Q->sampler != SPS_SAMPLER_ELEMENT && Q->sampler != SPS_SAMPLER_SKIP) { set_error("unknown sampler %d", Q->sampler); return SPS_ERR_INVALID_ARG; }
   if (Q->probs != SPS_PROBS_PAPER) { set_error("the batched solver samples with Eq. (pij-ot) / Eq. (pij-uot) only (probs 0)"); return SPS_ERR_INVALID_ARG; }
   if (Bt->d < 1 || Bt->d > 16) { set_error("batch points need 1 <= d <= 16 (d=%d)", Bt->d); return SPS_ERR_INVALID_ARG; }
   if (!Bt->set_off || !Bt->pts || !Bt->mass || !Bt->src || !Bt->dst || !Bt->s) { set_error("null batch array"); return SPS_ERR_INVALID_ARG; }
@@ -846,6 +1003,7 @@ BatchDev make_dev(const sps_batch* Bt, const sps_params* Q, const Plan& L, char*
   if (B.uot) B.gamma32 = (float)(Q->lambda / (2.0 * Q->lambda + Q->eps));   // the same rounding as the device
   B.max_iter = Q->max_iter;
   B.seed = Q->seed;
+  B.skip = Q->sampler == SPS_SAMPLER_SKIP ? 1 : 0;
   B.R = L.R; B.M = L.M; B.P = L.P;
   B.pairs = at<PairDesc>(ws, L.pairs);
   B.ro_tab = at<long long>(ws, L.ro_tab);
@@ -890,6 +1048,20 @@ void sweep(const BatchDev& B, cudaStream_t st) {
   }
 }
 
+template <int MODE, bool UOT>
+void skip(const BatchDev& B, cudaStream_t st) {
+  const int g = sweep_grid();
+  switch (B.d) {
+    case 1: k_b_skip<MODE, UOT, 1><<<g, kBT, 0, st>>>(B); break;
+    case 2: k_b_skip<MODE, UOT, 2><<<g, kBT, 0, st>>>(B); break;
+    case 3: k_b_skip<MODE, UOT, 3><<<g, kBT, 0, st>>>(B); break;
+    default:
+      if (B.d <= 4) k_b_skip<MODE, UOT, 4><<<g, kBT, 0, st>>>(B);
+      else if (B.d <= 8) k_b_skip<MODE, UOT, 8><<<g, kBT, 0, st>>>(B);
+      else k_b_skip<MODE, UOT, 16><<<g, kBT, 0, st>>>(B);
+  }
+}
+
 template <bool UOT>
 void sweeps_t(const BatchDev& B, const Plan& L, cudaStream_t st) {
   if (B.cost_norm == SPS_COST_MAXNORM) sweep<SW_MAX, UOT>(B, st);
@@ -898,9 +1070,11 @@ void sweeps_t(const BatchDev& B, const Plan& L, cudaStream_t st) {
     sweep<SW_Z, UOT>(B, st);
     k_b_scalars<<<(B.n_pairs + 127) / 128, 128, 0, st>>>(B, 1);
   }
-  sweep<SW_COUNT, UOT>(B, st);
+  if (B.skip) skip<BK_COUNT, UOT>(B, st);
+  else sweep<SW_COUNT, UOT>(B, st);
   launch_scan_counts(B.row_cnt, B.row_ptr, (int)B.R, B.col_cnt, B.col_ptr, B.col_cur, (int)B.M, L.cap, B.ctrl, st);
-  sweep<SW_FILL, UOT>(B, st);
+  if (B.skip) skip<BK_FILL, UOT>(B, st);
+  else sweep<SW_FILL, UOT>(B, st);
   launch_csc_sort_f32((int)B.M, B.col_ptr, B.tmp_row, B.tmp_src, B.logval, B.row_idx, B.csr_pos, B.logvalT, B.ctrl,
                       st);
 }
@@ -1064,10 +1238,10 @@ sps_status spar_sink_batched(const sps_batch* Bt, const sps_params* Q, sps_batch
   GraphEntry* cached = nullptr;
   if (O->use_graph) {
     char buf[256];
-    snprintf(buf, sizeof(buf), "%p|%p|%p|%p|%p|%d|%lld|%lld|%lld|%lld|%d|%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%d|%llu|%u|%d|%g|%d|%d",
+    snprintf(buf, sizeof(buf), "%p|%p|%p|%p|%p|%d|%lld|%lld|%lld|%lld|%d|%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%d|%llu|%u|%d|%g|%d|%d|%d",
              wsv, alpha_out, beta_out, Bt->pts, Bt->mass, np, L.R, L.M, L.P, L.cap, L.nmax, L.mmax, Q->kdtype,
              Bt->cost_norm, Bt->cost_scale, Q->eps, Q->lambda, Q->tol, Q->max_iter, (unsigned long long)Q->seed,
-             Q->problem_id, Bt->d, Q->absorb_tau, O->lanes_per_row, O->block_threads);
+             Q->problem_id, Bt->d, Q->absorb_tau, O->lanes_per_row, O->block_threads, Q->sampler);
     gkey = buf;
     std::lock_guard<std::mutex> lk(g_graph_mu);
     auto it = g_graphs.find(gkey);

@@ -405,10 +405,12 @@ class BatchOpts(C.Structure):
 def spar_sink_batched(sets, pairs, s, *, eps, lam=math.inf, tol=1e-5, max_iter=1000, dtype="f32", kdtype=None,
                       seed=0x5EED, problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, absorb_tau=0.0,
                       lanes_per_row=0, block_threads=0, use_graph=0, init_alpha=None, init_beta=None,
-                      workspace=None, device=None, raise_on_error=True):
+                      workspace=None, device=None, raise_on_error=True, sampler="element"):
     """Every pair (src, dst) of `pairs` solved as Alg. 3 (lam = inf) or Alg. 4
     on the sets `sets` = [(points k x d, masses k), ...] with budget s[p] and
-    Philox problem id problem_id + p.  Returns the per-pair results, the
+    Philox problem id problem_id + p; sampler "element" (one decision per
+    element) or "skip" (geometric gaps with thinning), each pair's sketch the
+    one a single solve with its problem id draws.  Returns the per-pair results, the
     potentials split per pair, and the launch shape the library used."""
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     dt = torch.float64 if dtype == "f64" else torch.float32
@@ -424,7 +426,8 @@ def spar_sink_batched(sets, pairs, s, *, eps, lam=math.inf, tol=1e-5, max_iter=1
                dst.ctypes.data, sv.ctypes.data, int(cost_norm), float(cost_scale), DTYPE_CODES[dtype])
     kd = kdtype or ("f32" if dtype == "f64" else dtype)
     ia, ib = _dev(init_alpha, torch.float32, dev), _dev(init_beta, torch.float32, dev)
-    prm = make_params(eps, lam, 1.0, tol, max_iter, 0, STOP_RESIDUAL, seed, problem_id, kd, 1, absorb_tau, ia, ib)
+    prm = make_params(eps, lam, 1.0, tol, max_iter, 0, STOP_RESIDUAL, seed, problem_id, kd, 1, absorb_tau, ia, ib,
+                      sampler=sampler)
     L = lib()
     L.sps_batch_workspace_bytes.argtypes = [C.c_void_p, C.c_void_p]
     L.sps_batch_workspace_bytes.restype = C.c_size_t

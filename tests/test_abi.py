@@ -170,9 +170,11 @@ def test_batch_arguments_validated(S):
     # 2 n + m at the limit is accepted
     Bl, kl = _batch(S, sets=(16384, 16384), pairs=((0, 1),))
     assert _batch_bytes(S, Bl, Q) > 0
+    # both samplers
+    assert _batch_bytes(S, B, S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f32", sampler="skip")) > 0
     # parameters the batched solver does not take
     for Qb, frag in [(S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f64"), "F32, BF16 or F16"),
-                     (S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f32", sampler="skip"), "sampler"),
+                     (S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f32", sampler=2), "sampler"),
                      (S.make_params(0.01, 1.0, 1.0, 1e-5, 100, kdtype="f32", stop_rule=1), "residual"),
                      (S.make_params(0.01, 1.0, 1.0, 1e-5, 0, kdtype="f32"), "max_iter"),
                      (S.make_params(0.0, 1.0, 1.0, 1e-5, 100, kdtype="f32"), "eps"),

@@ -120,3 +120,89 @@ def test_batch_bf16_values(S, uot_batch):
     for p in range(len(pairs)):
         rel = abs(h["results"][p]["obj"] - r["results"][p]["obj"]) / abs(r["results"][p]["obj"])
         assert rel < 2.0 ** -7, (p, rel)
+
+
+@pytest.fixture(scope="module")
+def uot_batch_skip(S):
+    sets = _sets(5, [420, 650, 300, 520, 800])
+    pairs = _pairs(5)
+    s = [12.0 * math.sqrt(len(sets[i][1]) * len(sets[j][1])) * math.log(len(sets[i][1])) for i, j in pairs]
+    kw = dict(eps=0.01, lam=1.0, tol=1e-5, max_iter=5000, seed=77, problem_id=3,
+              cost_norm=S.COST_SCALE, cost_scale=SCALE)
+    r = S.spar_sink_batched(sets, pairs, s, sampler="skip", **kw)
+    return sets, pairs, s, kw, r
+
+
+def test_batch_skip_counts_follow_the_oracle_stream(S, orc, uot_batch_skip):
+    """Skip sampler in the batch: every pair draws the stream of a single problem
+    with id problem_id + p, so its sketch count equals the oracle's skip count."""
+    sets, pairs, s, kw, r = uot_batch_skip
+    assert r["status_code"] == 0
+    for p, (i, j) in enumerate(pairs):
+        (x, a), (y, b) = sets[i], sets[j]
+        P = orc.OracleProblem(a, b, kw["eps"], s[p], 1.0, x=x, y=y, seed=kw["seed"], pid=kw["problem_id"] + p,
+                              cost_norm=S.COST_SCALE, cost_scale=SCALE)
+        _, nnz = P.skip_count()
+        assert r["results"][p]["nnz"] == nnz, p
+
+
+def test_batch_skip_pairs_equal_single_skip_solves(S, uot_batch_skip):
+    sets, pairs, s, kw, r = uot_batch_skip
+    for p, (i, j) in enumerate(pairs):
+        (x, a), (y, b) = sets[i], sets[j]
+        g = S.spar_sink_uot(a, b, x, y, eps=kw["eps"], lam=1.0, s=s[p], tol=kw["tol"], max_iter=5000, dtype="f32",
+                            seed=kw["seed"], problem_id=kw["problem_id"] + p, cost_norm=S.COST_SCALE,
+                            cost_scale=SCALE, log_domain=1, sampler="skip")
+        rb = r["results"][p]
+        assert rb["status"] == 0 and rb["nnz"] == g["nnz"], p
+        assert abs(rb["iters"] - g["iters"]) <= max(2, 0.03 * g["iters"]), (p, rb["iters"], g["iters"])
+        assert abs(rb["obj"] - g["obj"]) <= 2e-6 * abs(g["obj"]), p
+        assert torch.allclose(r["alpha"][p], g["alpha"], rtol=0, atol=2e-5)
+
+
+def test_batch_skip_matches_oracle(S, orc, uot_batch_skip):
+    sets, pairs, s, kw, r = uot_batch_skip
+    for p in (0, 5, 9):
+        i, j = pairs[p]
+        (x, a), (y, b) = sets[i], sets[j]
+        P = orc.OracleProblem(a, b, kw["eps"], s[p], 1.0, x=x, y=y, seed=kw["seed"], pid=kw["problem_id"] + p,
+                              cost_norm=S.COST_SCALE, cost_scale=SCALE)
+        sk = P.sparsify(sampler="skip")
+        o = orc.spar_sink(P, tol=kw["tol"], max_iter=5000, log_domain=True, sketch=sk)
+        rb = r["results"][p]
+        assert rb["nnz"] == sk["nnz"], p
+        assert abs(rb["iters"] - o["info"]["iters"]) <= max(3, 0.05 * o["info"]["iters"]), p
+        assert abs(rb["obj"] - o["obj"]) <= 1e-5 * abs(o["obj"]), p
+
+
+def test_batch_skip_ot_matches_oracle(S, orc):
+    sets = [(x, (w / w.sum()).astype(np.float32).astype(np.float64)) for x, w in _sets(6, [350, 500, 610])]
+    pairs = [(0, 1), (1, 2), (2, 0), (1, 1)]
+    s = [8000.0, 12000.0, 9000.0, 15000.0]
+    r = S.spar_sink_batched(sets, pairs, s, eps=0.02, tol=1e-5, max_iter=5000, seed=5, cost_norm=S.COST_MAXNORM,
+                            sampler="skip")
+    assert r["status_code"] == 0
+    for p, (i, j) in enumerate(pairs):
+        (x, a), (y, b) = sets[i], sets[j]
+        P = orc.OracleProblem(a, b, 0.02, s[p], math.inf, x=x, y=y, seed=5, pid=p)
+        sk = P.sparsify(sampler="skip")
+        o = orc.spar_sink(P, tol=1e-5, max_iter=5000, log_domain=True, sketch=sk)
+        rb = r["results"][p]
+        assert rb["nnz"] == sk["nnz"], p
+        assert abs(rb["obj"] - o["obj"]) <= 1e-5 * abs(o["obj"]) + 1e-7, (p, rb["obj"], o["obj"])
+
+
+def test_batch_graph_follows_the_sampler(S, uot_batch, uot_batch_skip):
+    """A captured batch keyed by its parameters: the same workspace replayed with
+    the other sampler runs that sampler's sketch."""
+    sets, pairs, s, kw, r_el = uot_batch
+    _, _, _, _, r_sk = uot_batch_skip
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g1 = S.spar_sink_batched(sets, pairs, s, use_graph=1, **kw)
+        g2 = S.spar_sink_batched(sets, pairs, s, use_graph=1, sampler="skip", workspace=g1["workspace"], **kw)
+        g3 = S.spar_sink_batched(sets, pairs, s, use_graph=1, workspace=g1["workspace"], **kw)
+    torch.cuda.synchronize()
+    for p in range(len(pairs)):
+        assert g1["results"][p]["nnz"] == g3["results"][p]["nnz"] == r_el["results"][p]["nnz"], p
+        assert g2["results"][p]["nnz"] == r_sk["results"][p]["nnz"], p
