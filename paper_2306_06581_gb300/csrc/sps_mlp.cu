@@ -35,6 +35,8 @@ constexpr int H = SPS_MLP_HIDDEN;
 constexpr int TP = 32;          // points per tile
 constexpr int NT = 256;         // threads of the tile kernel
 constexpr int HP = H + 1;       // padded row stride of W2 in shared memory
+constexpr int HB = H + 8;       // row stride (BF16 elements) of the split h1 copies: conflict-free fragment loads
+constexpr int PB = TP + 8;      // row stride (BF16) of the point-contiguous copies of the backward
 
 struct Off {                    // offsets (floats) of one side's parameters
   int F, D0, We, ce, W1, b1, W2, b2, w3, b3, size;
@@ -137,7 +139,7 @@ __global__ void k_pool_bwd(Side S) {
 
 // Shared memory of the tile kernel (floats).
 struct TileMem {
-  int W1, b1, W2, b2, w3, h0, h1, h2, dh1, outv, dout, P, dW1, dW2, db1, db2, dw3, misc, total;
+  int W1, b1, W2, b2, w3, h0, h1, h1b, h2, dh1, h1T, dh2b, dh2T, outv, dout, P, dW1, db1, db2, dw3, misc, total;
 };
 
 __host__ __device__ inline TileMem tile_mem(int D0, int train) {
@@ -145,24 +147,53 @@ __host__ __device__ inline TileMem tile_mem(int D0, int train) {
   int k = 0;
   m.W1 = k; k += H * D0;
   m.b1 = k; k += H;
-  m.W2 = k; k += H * HP;
+  m.W2 = k; k += H * HB / 2;        // W2 in BF16 (exact), rows of HB
   m.b2 = k; k += H;
   m.w3 = k; k += H;
   m.h0 = k; k += TP * D0;
   m.h1 = k; k += TP * H;
+  m.h1b = k; k += 3 * TP * HB / 2;   // h1 as three BF16 parts (hi, mid, lo), TP rows of HB
   m.h2 = k; k += TP * H;
   m.dh1 = k; k += train ? TP * H : 0;
+  m.h1T = k; k += train ? 2 * H * PB / 2 : 0;    // h1 (hi, mid) point-contiguous: [part][unit][point]
+  m.dh2b = k; k += train ? 2 * TP * HB / 2 : 0;  // dh2 (hi, mid): [part][point][unit]
+  m.dh2T = k; k += train ? 2 * H * PB / 2 : 0;   // dh2 (hi, mid) point-contiguous
   m.outv = k; k += TP * 4;
   m.dout = k; k += TP;
   m.P = k; k += E;
   m.dW1 = k; k += train ? H * D0 : 0;
-  m.dW2 = k; k += train ? H * HP : 0;
   m.db1 = k; k += train ? H : 0;
   m.db2 = k; k += train ? H : 0;
   m.dw3 = k; k += train ? H : 0;
   m.misc = k; k += 8 + E;
   m.total = k;
   return m;
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core tiles (mma.sync m16n8k16, BF16 operands, FP32 accumulation).
+// Fragment ownership follows the PTX definition of the shape: with g = lane / 4
+// and q = lane % 4, A (16 x 16, row-major) registers hold (g, 2q..2q+1),
+// (g + 8, 2q..), (g, 2q + 8..), (g + 8, 2q + 8..); B (16 x 8, column-major)
+// holds rows 2q..2q+1 and 2q + 8..2q + 9 of column g; C holds (g, 2q..2q+1) and
+// (g + 8, 2q..2q+1).  An FP32 activation x enters as three BF16 parts
+// hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid), whose sum carries
+// its 24 significant bits; the weights are BF16 already, so every product is
+// exact and the three MMAs give the layer to FP32 accumulation accuracy.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& hi, __nv_bfloat16& mid, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  const float r1 = __fsub_rn(x, __bfloat162float(hi));
+  mid = __float2bfloat16_rn(r1);
+  lo = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
 }
 
 // Forward (and for TRAIN the backward) of tiles of TP points; persistent
@@ -176,7 +207,8 @@ __global__ void __launch_bounds__(NT) k_mlp_tile(Side S) {
   const int t = threadIdx.x;
   // weights into shared memory (FP32 from the BF16 copy)
   for (int k = t; k < H * o.D0; k += NT) sm[M.W1 + k] = bf(S.wb, o.W1 + k);
-  for (int k = t; k < H * H; k += NT) sm[M.W2 + (k / H) * HP + (k % H)] = bf(S.wb, o.W2 + k);
+  __nv_bfloat16* w2s = reinterpret_cast<__nv_bfloat16*>(sm + M.W2);
+  for (int k = t; k < H * H; k += NT) w2s[(k / H) * HB + (k % H)] = S.wb[o.W2 + k];
   for (int k = t; k < H; k += NT) {
     sm[M.b1 + k] = bf(S.wb, o.b1 + k);
     sm[M.b2 + k] = bf(S.wb, o.b2 + k);
@@ -186,7 +218,6 @@ __global__ void __launch_bounds__(NT) k_mlp_tile(Side S) {
   for (int e = t; e < E; e += NT) sm[M.P + e] = wsum > 0.0f ? S.pool[e] / wsum : 0.0f;
   if (TRAIN) {
     for (int k = t; k < H * o.D0; k += NT) sm[M.dW1 + k] = 0.0f;
-    for (int k = t; k < H * HP; k += NT) sm[M.dW2 + k] = 0.0f;
     for (int k = t; k < H; k += NT) { sm[M.db1 + k] = 0.0f; sm[M.db2 + k] = 0.0f; sm[M.dw3 + k] = 0.0f; }
     if (t < 8 + E) sm[M.misc + t] = 0.0f;   // [0] db3, [1] loss, [8..] dpool
   }
@@ -195,6 +226,46 @@ __global__ void __launch_bounds__(NT) k_mlp_tile(Side S) {
   float wtot = 0.0f;
   if (TRAIN) wtot = S.pool[E + 1];
   const int hh = t & (H - 1), g = t >> 7;   // hidden unit, point half
+  const int warp = t >> 5, lane = t & 31, gq = lane >> 2, tq = lane & 3;
+  // W2 as MMA B fragments, kept in registers for every tile: warp w computes
+  // output units [16 w, 16 w + 16) (two n-tiles of 8) over the 8 k-steps.
+  // Read from the shared BF16 copy (rows of HB, an even stride, so every pair
+  // is 4-byte aligned; a side's weights in global memory may start at an odd
+  // BF16 offset).
+  __syncthreads();
+  uint32_t Bw[H / 16][2][2];
+#pragma unroll
+  for (int ks = 0; ks < H / 16; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int n = 16 * warp + 8 * nt + gq, k = 16 * ks + 2 * tq;
+      Bw[ks][nt][0] = *reinterpret_cast<const uint32_t*>(w2s + n * HB + k);
+      Bw[ks][nt][1] = *reinterpret_cast<const uint32_t*>(w2s + n * HB + k + 8);
+    }
+  // TRAIN: W2 as the B operand of dh1 = dh2 W2 (B element (j, k) = W2[j][k],
+  // two units j a register), and the warp's 16 rows of dW2 in registers
+  uint32_t BwT[TRAIN ? H / 16 : 1][2][2];
+  float dw2[TRAIN ? H / 8 : 1][4];
+  if (TRAIN) {
+#pragma unroll
+    for (int ks = 0; ks < H / 16; ++ks)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int k = 16 * warp + 8 * nt + gq, j = 16 * ks + 2 * tq;
+        const auto pk = [&](int jj) {
+          return (uint32_t)__bfloat16_as_ushort(w2s[jj * HB + k]) |
+                 ((uint32_t)__bfloat16_as_ushort(w2s[(jj + 1) * HB + k]) << 16);
+        };
+        BwT[ks][nt][0] = pk(j);
+        BwT[ks][nt][1] = pk(j + 8);
+      }
+#pragma unroll
+    for (int nt = 0; nt < H / 8; ++nt) dw2[nt][0] = dw2[nt][1] = dw2[nt][2] = dw2[nt][3] = 0.0f;
+  }
+  __nv_bfloat16* h1b = reinterpret_cast<__nv_bfloat16*>(sm + M.h1b);
+  __nv_bfloat16* h1T = reinterpret_cast<__nv_bfloat16*>(sm + M.h1T);
+  __nv_bfloat16* dh2b = reinterpret_cast<__nv_bfloat16*>(sm + M.dh2b);
+  __nv_bfloat16* dh2T = reinterpret_cast<__nv_bfloat16*>(sm + M.dh2T);
   const int ntiles = (S.sn + TP - 1) / TP;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int p0 = tile * TP;
@@ -222,26 +293,62 @@ __global__ void __launch_bounds__(NT) k_mlp_tile(Side S) {
         for (int q = 0; q < TP / 2; ++q) acc[q] = fmaf(w, sm[M.h0 + (2 * q + g) * o.D0 + c], acc[q]);
       }
 #pragma unroll
-      for (int q = 0; q < TP / 2; ++q) sm[M.h1 + (2 * q + g) * H + hh] = fmaxf(acc[q], 0.0f);
+      for (int q = 0; q < TP / 2; ++q) {
+        const int p = 2 * q + g;
+        const float v = fmaxf(acc[q], 0.0f);
+        sm[M.h1 + p * H + hh] = v;
+        __nv_bfloat16 hi, mid, lo;
+        split3(v, hi, mid, lo);
+        h1b[(0 * TP + p) * HB + hh] = hi;
+        h1b[(1 * TP + p) * HB + hh] = mid;
+        h1b[(2 * TP + p) * HB + hh] = lo;
+        if (TRAIN) {
+          h1T[(0 * H + hh) * PB + p] = hi;
+          h1T[(1 * H + hh) * PB + p] = mid;
+        }
+      }
     }
     __syncthreads();
-    // h2 = relu(W2 h1 + b2)
+    // h2 = relu(W2 h1 + b2) on the tensor cores: the tile's 32 points are two
+    // m-tiles; each of the three parts of h1 meets the warp's W2 fragments
     {
-      float acc[TP / 2];
+      float acc[2][2][4];
 #pragma unroll
-      for (int q = 0; q < TP / 2; ++q) acc[q] = sm[M.b2 + hh];
-      for (int c = 0; c < H; ++c) {
-        const float w = sm[M.W2 + hh * HP + c];
+      for (int nt = 0; nt < 2; ++nt) {
+        const int n = 16 * warp + 8 * nt + 2 * tq;
+        const float c0 = sm[M.b2 + n], c1 = sm[M.b2 + n + 1];
 #pragma unroll
-        for (int q = 0; q < TP / 2; ++q) acc[q] = fmaf(w, sm[M.h1 + (2 * q + g) * H + c], acc[q]);
+        for (int mt = 0; mt < 2; ++mt) {
+          acc[mt][nt][0] = c0; acc[mt][nt][1] = c1; acc[mt][nt][2] = c0; acc[mt][nt][3] = c1;
+        }
       }
 #pragma unroll
-      for (int q = 0; q < TP / 2; ++q) sm[M.h2 + (2 * q + g) * H + hh] = fmaxf(acc[q], 0.0f);
+      for (int ks = 0; ks < H / 16; ++ks)
+#pragma unroll
+        for (int part = 0; part < 3; ++part)
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt) {
+            const __nv_bfloat16* r0 = h1b + (part * TP + 16 * mt + gq) * HB + 16 * ks + 2 * tq;
+            const __nv_bfloat16* r8 = r0 + 8 * HB;
+            const uint32_t a[4] = {*reinterpret_cast<const uint32_t*>(r0), *reinterpret_cast<const uint32_t*>(r8),
+                                   *reinterpret_cast<const uint32_t*>(r0 + 8), *reinterpret_cast<const uint32_t*>(r8 + 8)};
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_bf16(acc[mt][nt], a, Bw[ks][nt][0], Bw[ks][nt][1]);
+          }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int p = 16 * mt + gq, n = 16 * warp + 8 * nt + 2 * tq;
+          sm[M.h2 + p * H + n] = fmaxf(acc[mt][nt][0], 0.0f);
+          sm[M.h2 + p * H + n + 1] = fmaxf(acc[mt][nt][1], 0.0f);
+          sm[M.h2 + (p + 8) * H + n] = fmaxf(acc[mt][nt][2], 0.0f);
+          sm[M.h2 + (p + 8) * H + n + 1] = fmaxf(acc[mt][nt][3], 0.0f);
+        }
     }
     __syncthreads();
-    // out = w3 . h2 + b3: partial sums over hidden units per warp
+    // out = w3 . h2 + b3: partial sums over hidden units per warp (warps 0-3: g = 0, warps 4-7: g = 1)
     {
-      const int warp = t >> 5, lane = t & 31;   // warps 0-3: g = 0, warps 4-7: g = 1
 #pragma unroll
       for (int q = 0; q < TP / 2; ++q) {
         const int p = 2 * q + g;
@@ -286,44 +393,94 @@ __global__ void __launch_bounds__(NT) k_mlp_tile(Side S) {
         s3 += dp * h;
         const float d2 = h > 0.0f ? dp * sm[M.w3 + hh] : 0.0f;
         sm[M.h2 + p * H + hh] = d2;
+        const __nv_bfloat16 dhi = __float2bfloat16_rn(d2);
+        const __nv_bfloat16 dmid = __float2bfloat16_rn(__fsub_rn(d2, __bfloat162float(dhi)));
+        dh2b[(0 * TP + p) * HB + hh] = dhi;
+        dh2b[(1 * TP + p) * HB + hh] = dmid;
+        dh2T[(0 * H + hh) * PB + p] = dhi;
+        dh2T[(1 * H + hh) * PB + p] = dmid;
         s2 += d2;
       }
       atomicAdd(&sm[M.dw3 + hh], s3);
       atomicAdd(&sm[M.db2 + hh], s2);
     }
     __syncthreads();
-    // dW2[hh][k] += sum_p dh2[p][hh] h1[p][k]: thread (hh, k half)
-    {
-      float d2[TP];
+    // dW2[hh][k] += sum_p dh2[p][hh] h1[p][k] on the tensor cores, a contraction
+    // over the tile's 32 points: warp w owns rows hh of [16 w, 16 w + 16) in
+    // registers (dw2) for every tile; both operands enter as two BF16 parts
+    // (hi hi + hi mid + mid hi: relative error near 2^-16)
 #pragma unroll
-      for (int p = 0; p < TP; ++p) d2[p] = sm[M.h2 + p * H + hh];
-      for (int k = 64 * g; k < 64 * g + 64; ++k) {
-        float a = 0.0f;
+    for (int ks = 0; ks < TP / 16; ++ks) {
+      uint32_t a[2][4];
 #pragma unroll
-        for (int p = 0; p < TP; ++p) a = fmaf(d2[p], sm[M.h1 + p * H + k], a);
-        sm[M.dW2 + hh * HP + k] += a;
+      for (int part = 0; part < 2; ++part) {
+        const __nv_bfloat16* r0 = dh2T + (part * H + 16 * warp + gq) * PB + 16 * ks + 2 * tq;
+        const __nv_bfloat16* r8 = r0 + 8 * PB;
+        a[part][0] = *reinterpret_cast<const uint32_t*>(r0);
+        a[part][1] = *reinterpret_cast<const uint32_t*>(r8);
+        a[part][2] = *reinterpret_cast<const uint32_t*>(r0 + 8);
+        a[part][3] = *reinterpret_cast<const uint32_t*>(r8 + 8);
+      }
+#pragma unroll
+      for (int nt = 0; nt < H / 8; ++nt) {
+        uint32_t bq[2][2];
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          const __nv_bfloat16* q0 = h1T + (part * H + 8 * nt + gq) * PB + 16 * ks + 2 * tq;
+          bq[part][0] = *reinterpret_cast<const uint32_t*>(q0);
+          bq[part][1] = *reinterpret_cast<const uint32_t*>(q0 + 8);
+        }
+        mma_bf16(dw2[nt], a[0], bq[0][0], bq[0][1]);
+        mma_bf16(dw2[nt], a[0], bq[1][0], bq[1][1]);
+        mma_bf16(dw2[nt], a[1], bq[0][0], bq[0][1]);
       }
     }
-    // dh1[p][k] = [h1 > 0] sum_hh W2[hh][k] dh2[p][hh]: thread (k = hh index, point half)
+    // dh1[p][k] = [h1 > 0] sum_j dh2[p][j] W2[j][k] on the tensor cores: warp w
+    // computes units k of [16 w, 16 w + 16) for the tile's two m-tiles of points
     {
-      const int k = hh;
-      float acc[TP / 2];
+      float acc[2][2][4];
 #pragma unroll
-      for (int q = 0; q < TP / 2; ++q) acc[q] = 0.0f;
-      for (int j = 0; j < H; ++j) {
-        const float w = sm[M.W2 + j * HP + k];
+      for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int q = 0; q < TP / 2; ++q) acc[q] = fmaf(w, sm[M.h2 + (2 * q + g) * H + j], acc[q]);
-      }
-      float s1 = 0.0f;
+        for (int nt = 0; nt < 2; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.0f;
 #pragma unroll
-      for (int q = 0; q < TP / 2; ++q) {
-        const int p = 2 * q + g;
-        const float d1 = sm[M.h1 + p * H + k] > 0.0f ? acc[q] : 0.0f;
-        sm[M.dh1 + p * H + k] = d1;
-        s1 += d1;
-      }
-      atomicAdd(&sm[M.db1 + k], s1);
+      for (int ks = 0; ks < H / 16; ++ks)
+#pragma unroll
+        for (int part = 0; part < 2; ++part)
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt) {
+            const __nv_bfloat16* r0 = dh2b + (part * TP + 16 * mt + gq) * HB + 16 * ks + 2 * tq;
+            const __nv_bfloat16* r8 = r0 + 8 * HB;
+            const uint32_t a[4] = {*reinterpret_cast<const uint32_t*>(r0), *reinterpret_cast<const uint32_t*>(r8),
+                                   *reinterpret_cast<const uint32_t*>(r0 + 8), *reinterpret_cast<const uint32_t*>(r8 + 8)};
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_bf16(acc[mt][nt], a, BwT[ks][nt][0], BwT[ks][nt][1]);
+          }
+      float s1[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};   // [nt][unit k or k + 1]: this thread's points
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int p = 16 * mt + gq, k = 16 * warp + 8 * nt + 2 * tq;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int pp = p + (e >> 1) * 8, kk = k + (e & 1);
+            const float d1 = sm[M.h1 + pp * H + kk] > 0.0f ? acc[mt][nt][e] : 0.0f;
+            sm[M.dh1 + pp * H + kk] = d1;
+            s1[nt][e & 1] += d1;
+          }
+        }
+      // db1: the eight lanes of a column pair (same q) hold the other points
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          float v = s1[nt][e];
+          v += __shfl_xor_sync(0xffffffffu, v, 4);
+          v += __shfl_xor_sync(0xffffffffu, v, 8);
+          v += __shfl_xor_sync(0xffffffffu, v, 16);
+          if (gq == 0) atomicAdd(&sm[M.db1 + 16 * warp + 8 * nt + 2 * tq + e], v);
+        }
     }
     __syncthreads();
     // dW1[k][c] += sum_p dh1[p][k] h0[p][c]; dP[e] += sum_p sum_k W1[k][F+e] dh1[p][k]
@@ -349,7 +506,14 @@ __global__ void __launch_bounds__(NT) k_mlp_tile(Side S) {
   if (!TRAIN) return;
   __syncthreads();
   for (int k = t; k < H * o.D0; k += NT) atomicAdd(&S.grad[o.W1 + k], sm[M.dW1 + k]);
-  for (int k = t; k < H * H; k += NT) atomicAdd(&S.grad[o.W2 + k], sm[M.dW2 + (k / H) * HP + (k % H)]);
+#pragma unroll
+  for (int nt = 0; nt < H / 8; ++nt) {   // this warp's rows of dW2, from registers
+    const int hr = 16 * warp + gq, k = 8 * nt + 2 * tq;
+    atomicAdd(&S.grad[o.W2 + hr * H + k], dw2[nt][0]);
+    atomicAdd(&S.grad[o.W2 + hr * H + k + 1], dw2[nt][1]);
+    atomicAdd(&S.grad[o.W2 + (hr + 8) * H + k], dw2[nt][2]);
+    atomicAdd(&S.grad[o.W2 + (hr + 8) * H + k + 1], dw2[nt][3]);
+  }
   for (int k = t; k < H; k += NT) {
     atomicAdd(&S.grad[o.b1 + k], sm[M.db1 + k]);
     atomicAdd(&S.grad[o.b2 + k], sm[M.db2 + k]);
