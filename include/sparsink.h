@@ -201,6 +201,10 @@ typedef struct {
   int32_t* row_idx;   /* nnz, ascending inside each column (stable transpose) */
   void* valT;         /* nnz, values in CSC order */
   int32_t* csr_pos;   /* nnz, CSR position of each CSC entry */
+  double sum1, sum2;  /* the exact sums of the sampling probabilities, rounded to binary64 once:
+                         OT (Eq. pij-ot) sum_i sqrt(a_i) and sum_j sqrt(b_j); UOT (Eq. pij-uot) the
+                         normaliser Z = sum_ij A_i B_j F(C_ij) in sum1 (sum2 = 0); equal
+                         probabilities: 0 */
 } sps_sketch;
 
 /* Operation codes for sps_workspace_bytes. */

@@ -540,7 +540,13 @@ sps_status sparsify_kernel(const sps_problem* prob, const sps_params* prm, void*
   out->row_idx = at<int32_t>(ws, L.row_idx);
   out->valT = ws + L.valT;
   out->csr_pos = at<int32_t>(ws, L.csr_pos);
-  return cuda_fail(cudaStreamSynchronize(st), "stream synchronize");
+  SketchScalars sc;
+  SPS_TRY(cuda_fail(cudaMemcpyAsync(&sc, ws + L.scal, sizeof(sc), cudaMemcpyDeviceToHost, st), "scalars read-back"));
+  SPS_TRY(cuda_fail(cudaStreamSynchronize(st), "stream synchronize"));
+  const bool equal = prm->probs == SPS_PROBS_EQUAL;
+  out->sum1 = equal ? 0.0 : sc.sum1;
+  out->sum2 = equal || !isinf(prm->lambda) ? 0.0 : sc.sum2;
+  return SPS_OK;
 }
 
 sps_status spar_sink_ot(const sps_problem* prob, const sps_params* prm, void* ws, size_t ws_bytes, void* alpha_out,

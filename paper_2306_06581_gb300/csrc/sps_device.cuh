@@ -73,6 +73,9 @@ __device__ __forceinline__ float spec_exp(float x) {
   const int ki = (int)k;
   const int k1 = ki / 2;
   const int k2 = ki - k1;
+  // p lies in [1/2, 2): for -125 <= k <= 126 both scalings below are exact
+  // and the result is normal, so adding k to p's exponent gives the same bits
+  if (ki >= -125 && ki <= 126) return __int_as_float(__float_as_int(p) + (ki << 23));
   return __fmul_rn(__fmul_rn(p, pow2f_small(k1)), pow2f_small(k2));
 }
 

@@ -76,7 +76,8 @@ class Result(C.Structure):
 class Sketch(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nnz", C.c_int64), ("capacity", C.c_int64),
                 ("kdtype", C.c_int32), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("val", C.c_void_p),
-                ("col_ptr", C.c_void_p), ("row_idx", C.c_void_p), ("valT", C.c_void_p), ("csr_pos", C.c_void_p)]
+                ("col_ptr", C.c_void_p), ("row_idx", C.c_void_p), ("valT", C.c_void_p), ("csr_pos", C.c_void_p),
+                ("sum1", C.c_double), ("sum2", C.c_double)]
 
 
 _lib = None
@@ -293,7 +294,7 @@ def sparsify_kernel(a, b, x=None, y=None, C_=None, *, eps, s, lam=math.inf, dtyp
             "row_ptr": view(sk.row_ptr, n + 1, torch.int32), "col_idx": view(sk.col_idx, nnz, torch.int32),
             "val": view(sk.val, nnz, vdt), "col_ptr": view(sk.col_ptr, m + 1, torch.int32),
             "row_idx": view(sk.row_idx, nnz, torch.int32), "valT": view(sk.valT, nnz, vdt),
-            "csr_pos": view(sk.csr_pos, nnz, torch.int32)}
+            "csr_pos": view(sk.csr_pos, nnz, torch.int32), "sum1": sk.sum1, "sum2": sk.sum2}
 
 
 def spar_sink_ot_noalloc(a, b, x=None, y=None, C_=None, *, eps, s, tol=1e-6, max_iter=1000, dtype="f32",

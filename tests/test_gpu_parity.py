@@ -252,3 +252,19 @@ def test_single_pass_log_domain_solve_equals_two_pass(S, lam):
     r2 = f(a, b, x, y, sketch_mode=1, **kw)
     assert r1["nnz"] == r2["nnz"] and r1["iters"] == r2["iters"] and r1["obj"] == r2["obj"]
     assert torch.equal(r1["alpha"], r2["alpha"])
+
+
+@pytest.mark.parametrize("n,m,d,lam", [(300, 257, 5, 1.0), (513, 700, 10, 0.5), (64, 2000, 2, 2.0), (400, 350, 3, math.inf)])
+def test_exact_normalisers_bit_equal(S, orc, n, m, d, lam):
+    """The sampling normalisers are exact sums rounded once: UOT Z of Eq. (pij-uot)
+    (a fixed-point window per thread plus a full-range slow path on the GPU, the
+    oracle's own exact sum on the CPU), OT sum sqrt(a) and sum sqrt(b)."""
+    w = inputs.small_problem(n=n, m=m, d=d, seed=3 * n + m, mass_b=1.0 if math.isinf(lam) else 1.5)
+    x, y, a, b = _round32(w)
+    s = max(10.0, 0.05 * n * m)
+    g = S.sparsify_kernel(a, b, x, y, eps=0.1, s=s, lam=lam, dtype="f32", seed=5, problem_id=1)
+    P = _oracle_problem(orc, x, y, a, b, 0.1, lam, s, seed=5, pid=1)
+    _, _, sc = P.factors()
+    assert g["sum1"] == sc.sum1 and g["sum1"] > 0.0
+    if math.isinf(lam):
+        assert g["sum2"] == sc.sum2 and g["sum2"] > 0.0
