@@ -802,26 +802,44 @@ __global__ void __launch_bounds__(256) k_el_fill(int rows, int R, int nblk, int 
       if (lane == 0 && prev >= 0) reinterpret_cast<int*>(pack + prev + 68)[0] = h;
       prev = off;
       constexpr long long st = ell_step_bytes(vb);
-      for (int k = 0; k < h; ++k) {
-        unsigned char* sp = gp + kEllHdr + k * st;   // step k: 32 indices, then 32 values
-        const long long slot = (off + kEllHdr + k * st + 64) / vb + lane;
-        unsigned short q = 0;
-        float lk = neg_inf();
-        if (k < len) {
+      // eight steps at a time: the run's indices and log K~ are loaded first
+      // (every lane reads its own row's run), then the steps are written
+      for (int k0 = 0; k0 < h; k0 += 8) {
+        int qv[8];
+        float lv[8];
+        bool okv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int k = k0 + u;
           const long long e = (long long)src + k;
-          if (e >= 0 && e < nnz_lim) {
-            q = (unsigned short)(idx[e] - c * W);
-            perm[e] = (int)slot;
-            lk = logv[e];
-          } else {
-            oob(ctrl, 9, e);
-            ctrl->ell_overflow = 1;
-          }
-        } else {
-          reinterpret_cast<V*>(sp + 64)[lane] = from_d<V>(0.0);
+          okv[u] = k < h && k < len && e >= 0 && e < nnz_lim;
+          qv[u] = okv[u] ? idx[e] : 0;
+          lv[u] = okv[u] ? logv[e] : neg_inf();
         }
-        logk[slot] = lk;
-        reinterpret_cast<unsigned short*>(sp)[lane] = q;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int k = k0 + u;
+          if (k >= h) break;
+          unsigned char* sp = gp + kEllHdr + k * st;   // step k: 32 indices, then 32 values
+          const long long slot = (off + kEllHdr + k * st + 64) / vb + lane;
+          unsigned short q = 0;
+          float lk = neg_inf();
+          if (k < len) {
+            const long long e = (long long)src + k;
+            if (okv[u]) {
+              q = (unsigned short)(qv[u] - c * W);
+              perm[e] = (int)slot;
+              lk = lv[u];
+            } else {
+              oob(ctrl, 9, e);
+              ctrl->ell_overflow = 1;
+            }
+          } else {
+            reinterpret_cast<V*>(sp + 64)[lane] = from_d<V>(0.0);
+          }
+          logk[slot] = lk;
+          reinterpret_cast<unsigned short*>(sp)[lane] = q;
+        }
       }
       off += ell_group_bytes(h, vb);
     }
@@ -850,7 +868,7 @@ __global__ void __launch_bounds__(256) k_el_fill(int rows, int R, int nblk, int 
 // write a whole 32-lane row of a step.  The other side's potentials pass
 // through shared memory (xs) chunk by chunk, as the gathered vector does in
 // ell_pass.  mx: shared scratch of the block's rows.
-template <typename V>
+template <typename V, int NB>
 __device__ void ell_absorb(const LogArgs& A, int side, float* xs, float* mx) {
   constexpr int vb = (int)sizeof(V);
   constexpr long long st = ell_step_bytes(vb);
@@ -881,7 +899,14 @@ __device__ void ell_absorb(const LogArgs& A, int side, float* xs, float* mx) {
       const long long pe = min(max(__ldg(po + c + 1), off), s1);
       const int j0 = c * A.W, jn = min(A.W, nx - j0);
       __syncthreads();   // the previous chunk is no longer read
-      for (int k = threadIdx.x; k < jn; k += blockDim.x) xs[k] = __ldcg(oth + j0 + k);
+      if ((((uintptr_t)(oth + j0)) & 15) == 0) {   // 16-byte copies, all in flight at once
+        const int n4 = jn >> 2;
+        for (int k = threadIdx.x; k < n4; k += blockDim.x) cp_async16(xs + 4 * k, oth + j0 + 4 * k);
+        for (int k = 4 * n4 + threadIdx.x; k < jn; k += blockDim.x) xs[k] = __ldcg(oth + j0 + k);
+      } else {
+        for (int k = threadIdx.x; k < jn; k += blockDim.x) xs[k] = __ldcg(oth + j0 + k);
+      }
+      cp_async_wait_all();
       __syncthreads();
       while (off < pe) {
         const int H = __ldg(reinterpret_cast<const int*>(pack + off + 64));
@@ -895,15 +920,15 @@ __device__ void ell_absorb(const LogArgs& A, int side, float* xs, float* mx) {
         const float pi = mine ? __ldcg(pot + r0 + row) : neg_inf();
         const float ei = (pass == 1 && mine) ? mx[row] : 0.0f;
         float m = neg_inf();
-        // eight steps at a time: their indices and log K~, then the staged
+        // NB steps at a time: their indices and log K~, then the staged
         // potentials, then the values (loads first: the stores go to the
         // same buffer as the indices)
-        for (int k0 = 0; k0 < H; k0 += 8) {
-          const int nk = min(8, H - k0);
-          unsigned q[8];
-          float lk[8], o[8];
+        for (int k0 = 0; k0 < H; k0 += NB) {
+          const int nk = min(NB, H - k0);
+          unsigned q[NB];
+          float lk[NB], o[NB];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < NB; ++u) {
             q[u] = 0u;
             lk[u] = neg_inf();
             if (u < nk) {
@@ -913,9 +938,9 @@ __device__ void ell_absorb(const LogArgs& A, int side, float* xs, float* mx) {
             }
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) o[u] = u < nk ? xs[min(q[u], (unsigned)(jn - 1))] : neg_inf();
+          for (int u = 0; u < NB; ++u) o[u] = u < nk ? xs[min(q[u], (unsigned)(jn - 1))] : neg_inf();
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < NB; ++u) {
             if (u < nk) {
               float z = neg_inf();
               if (pi != neg_inf() && o[u] != neg_inf()) z = absorbed_z(lk[u], pi, o[u], A.inv_eps);
@@ -951,8 +976,8 @@ template <typename V>
 __global__ void __launch_bounds__(kStgThreads, 1) k_absorb_pack(LogArgs A) {
   extern __shared__ __align__(16) float absorb_sh[];   // W entries of the other side's potentials, then rows
   if (*(volatile int*)&A.ctrl->ell_overflow) return;
-  ell_absorb<V>(A, 0, absorb_sh, absorb_sh + A.W);
-  ell_absorb<V>(A, 1, absorb_sh, absorb_sh + A.W);
+  ell_absorb<V, 16>(A, 0, absorb_sh, absorb_sh + A.W);
+  ell_absorb<V, 16>(A, 1, absorb_sh, absorb_sh + A.W);
 }
 
 // Fold the scalings of the pair t into the potentials (this block's rows and
@@ -1090,8 +1115,8 @@ __global__ void __launch_bounds__(STG ? kStgThreads : kIterThreads, 1) k_iterate
       if (!grid_barrier(ctrl)) return;
       if constexpr (STG) {
         if (grp) {
-          ell_absorb<V>(A, 0, dsm, dsm + A.W);
-          ell_absorb<V>(A, 1, dsm, dsm + A.W);
+          ell_absorb<V, 8>(A, 0, dsm, dsm + A.W);   // inside the persistent kernel: its register budget
+          ell_absorb<V, 8>(A, 1, dsm, dsm + A.W);
         } else {
           rewrite_block<V>(A);
         }
