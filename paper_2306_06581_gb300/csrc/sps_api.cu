@@ -155,7 +155,7 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
     L->csr_pos = take((size_t)cap * 4);
     L->tmp_row = take((size_t)cap * 4);
     L->tmp_src = take((size_t)cap * 4);
-    if (Q->log_domain) {
+    if (Q->log_domain && op == SPS_OP_SPAR_SINK) {   // sparsify_kernel returns K~ itself
       L->logval = take((size_t)cap * 4);
       L->logvalT = take((size_t)cap * 4);
     }
@@ -172,7 +172,7 @@ bool plan_layout(const sps_problem* P, const sps_params* Q, int op, Layout* L) {
       L->pad_ofs = take((size_t)(2 * cells + 1) * 4);
       L->pad_col = take((size_t)pcap * 4);
       L->pad_val = take((size_t)pcap * vb);   // written unless log K~ is formed in binary32
-      if (Q->log_domain) L->pad_lv = take((size_t)pcap * 4);
+      if (Q->log_domain && op == SPS_OP_SPAR_SINK) L->pad_lv = take((size_t)pcap * 4);
       if (!isinf(Q->lambda)) L->zsum = take((size_t)cells * 4);
       L->csum = take((size_t)g.nchunk * 4);
     }

@@ -342,7 +342,7 @@ __device__ __forceinline__ void rank_place(const int* sm, int L, int off, int s0
     if (e < L) {
       row_idx[s0 + rank[k]] = r[k];
       csr_pos[s0 + rank[k]] = src[k];
-      valT[s0 + rank[k]] = gather_val(val, src[k], nnz, ctrl);
+      if (val) valT[s0 + rank[k]] = gather_val(val, src[k], nnz, ctrl);
       if (lv) lvT[s0 + rank[k]] = gather_val(lv, src[k], nnz, ctrl);
     }
   }
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(32 * kSortWarps, 4) k_csc_sort(int m, const in
         const int src = tmp_src[s0 + e];
         row_idx[s0 + rank] = re;
         csr_pos[s0 + rank] = src;
-        valT[s0 + rank] = gather_val(val, src, nnz, ctrl);
+        if (val) valT[s0 + rank] = gather_val(val, src, nnz, ctrl);
         if (lv) lvT[s0 + rank] = gather_val(lv, src, nnz, ctrl);
       }
     }
@@ -494,10 +494,13 @@ sps_status launch_factors(const ProbDev& pd, const Layout& L, char* ws, cudaStre
 template <typename V>
 static void csc_sort(const ProbDev& pd, const Layout& L, char* ws, cudaStream_t st) {
   const int gs = grid_for((int64_t)pd.m * 32, 32 * kSortWarps);
+  // the stabilised solve with binary32 points forms only log K~ in the fill (the
+  // absorption writes K' later): no values to transpose then
+  const bool vals = !(L.logval && !pd.cv.x64 && !pd.cv.C32 && !pd.cv.C64 && pd.cost_kind != SPS_COST_WFR);
   k_csc_sort<V><<<gs, 32 * kSortWarps, 0, st>>>(pd.m, at<int>(ws, L.col_ptr), at<int>(ws, L.tmp_row),
-                                                at<int>(ws, L.tmp_src), at<V>(ws, L.val),
+                                                at<int>(ws, L.tmp_src), vals ? at<V>(ws, L.val) : nullptr,
                                                 at<int>(ws, L.row_idx), at<int>(ws, L.csr_pos),
-                                                at<V>(ws, L.valT), at<Ctrl>(ws, L.ctrl),
+                                                vals ? at<V>(ws, L.valT) : nullptr, at<Ctrl>(ws, L.ctrl),
                                                 L.logval ? at<float>(ws, L.logval) : nullptr,
                                                 L.logvalT ? at<float>(ws, L.logvalT) : nullptr);
 }

@@ -266,13 +266,14 @@ _NP_DT = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: tor
 
 def sparsify_kernel(a, b, x=None, y=None, C_=None, *, eps, s, lam=math.inf, dtype="f32", kdtype=None, seed=0x5EED,
                     problem_id=0, cost_norm=COST_MAXNORM, cost_scale=1.0, sketch_mode=0, workspace=None,
-                    device=None, sampler="element", cost_kind="sqeuclid", eta=0.0, probs="paper"):
-    """Eq. (pois) sketch K~ as CSR + CSC tensor views (copied out of the workspace)."""
+                    device=None, sampler="element", cost_kind="sqeuclid", eta=0.0, probs="paper", log_domain=0):
+    """Eq. (pois) sketch K~ as CSR + CSC tensor views (copied out of the workspace).
+    log_domain only changes the params passed (the sketch is the same)."""
     M = make_problem(a, b, x, y, C_, dtype, cost_norm, cost_scale, device, cost_kind, eta)
     dev = M.keep[0].device
     kd = kdtype or dtype
-    prm = make_params(eps, lam, s, 0.0, 1, 0, 0, seed, problem_id, kd, sketch_mode=sketch_mode, sampler=sampler,
-                      probs=probs)
+    prm = make_params(eps, lam, s, 0.0, 1, 0, 0, seed, problem_id, kd, log_domain=log_domain, sketch_mode=sketch_mode,
+                      sampler=sampler, probs=probs)
     nbytes = sps_workspace_bytes(M.prob, prm, OP_SPARSIFY)
     if nbytes == 0:
         raise SpsError(SPS_ERR_INVALID_ARG, last_error())

@@ -268,3 +268,19 @@ def test_exact_normalisers_bit_equal(S, orc, n, m, d, lam):
     assert g["sum1"] == sc.sum1 and g["sum1"] > 0.0
     if math.isinf(lam):
         assert g["sum2"] == sc.sum2 and g["sum2"] > 0.0
+
+
+@pytest.mark.parametrize("sampler,sketch_mode", [("element", 0), ("element", 1), ("skip", 0)])
+def test_sparsify_values_ignore_log_domain_params(S, sampler, sketch_mode):
+    """sparsify_kernel returns K~ itself whatever the params' log_domain says (the
+    stabilised solve keeps only log K~ internally, the sparsifier never does)."""
+    w = inputs.small_problem(n=400, m=300, d=3, seed=17)
+    x, y, a, b = _round32(w)
+    kw = dict(eps=0.1, s=0.1 * 400 * 300, dtype="f32", seed=3, sampler=sampler, sketch_mode=sketch_mode)
+    g0 = S.sparsify_kernel(a, b, x, y, **kw)
+    g1 = S.sparsify_kernel(a, b, x, y, log_domain=1, **kw)
+    assert g0["nnz"] == g1["nnz"] > 0
+    for k in ("col_idx", "row_idx", "csr_pos"):
+        assert torch.equal(g0[k], g1[k]), k
+    assert torch.equal(g0["val"].view(torch.int32), g1["val"].view(torch.int32))
+    assert torch.equal(g0["valT"].view(torch.int32), g1["valT"].view(torch.int32))
