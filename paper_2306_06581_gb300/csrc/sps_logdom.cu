@@ -402,8 +402,46 @@ __device__ __forceinline__ void ell_need(EllRing& R, unsigned cons, unsigned end
 // hold the same row at once (a row belongs to one slice and appears once in a
 // chunk's groups): plain loads and stores of acc, no atomics.  A group's
 // header names the next group's height, so one wait covers a whole group (up
-// to KB steps).  The stream runs ahead across chunk boundaries; the chunk of x
-// arrives by cp.async between two block barriers.
+// to KB steps).  The stream runs ahead across chunk boundaries.  The chunk of
+// x arrives by one bulk copy on its own mbarrier (when x is 16-byte aligned):
+// every warp counts itself done with chunk c in shared memory, the warp that
+// completes the count issues chunk c + 1 into the same buffer, and all wait for
+// that phase only, so the stream's windows in flight are not drained at a
+// switch.  Otherwise by cp.async between two block barriers.
+__device__ __forceinline__ void mbar_arrive_plain(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Chunk c of x into xs, issued by one thread: the whole 16-byte part by a bulk
+// copy, the last (at most 3) entries by plain stores made before the arrive
+// (whose release makes them visible to the phase's waiters).
+__device__ __forceinline__ void ell_issue_chunk(const float* x, int nx, int W, int c, float* xs, uint64_t* bar) {
+  const int j0 = c * W;
+  const int jn = min(W, nx - j0);
+  const int n4 = jn & ~3;
+  for (int k = n4; k < jn; ++k) xs[k] = __ldcg(x + j0 + k);
+  if (n4 > 0) {
+    mbar_arrive_expect_tx(bar, (unsigned)n4 * 4u);
+    bulk_copy_g2s(xs, x + j0, (unsigned)n4 * 4u, bar);
+  } else {
+    mbar_arrive_plain(bar);
+  }
+}
+
+// Bounded wait for a phase of the chunk barrier by every thread; a wait that
+// gives up records the failure (the solve then reports it) instead of hanging.
+__device__ __forceinline__ void ell_wait_chunk(uint64_t* bar, unsigned parity, Ctrl* ctrl) {
+  long long polls = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if (++polls > kSpinLimit) {
+      ctrl->wait_timeout = 1;
+      ctrl->status = SPS_ERR_CUDA;
+      ctrl->done = 1;
+      break;
+    }
+  }
+}
+
 template <typename V>
 __device__ __forceinline__ void ell_pass(const unsigned char* __restrict__ pack, const long long* __restrict__ poff,
                                          const float* x, int nx, int nr, int W, int J, float* xs, float* acc,
@@ -431,21 +469,40 @@ __device__ __forceinline__ void ell_pass(const unsigned char* __restrict__ pack,
   const unsigned l2 = 2u * lane, lv = 64u + (unsigned)vb * lane;
   unsigned p = R.r0;   // read position (uniform over the warp)
   int Hc = -1;         // height of the group at p, when known from the previous header
+  __shared__ __align__(8) uint64_t xbar;   // chunk barrier (one phase a chunk)
+  __shared__ int xdone;                     // warps done with the current chunk, counted over the pass
+  const bool bulk = (((uintptr_t)x) & 15) == 0;   // chunk starts c W are multiples of 1024 entries
+  if (bulk) {
+    if (t == 0) {
+      mbar_init(&xbar, 1);
+      fence_mbarrier_init();
+      xdone = 0;
+    }
+    __syncthreads();   // the barrier is set (and acc is initialised)
+    if (t == 0) {
+      fence_proxy_async_global();   // x was written by ordinary stores before the last grid barrier
+      ell_issue_chunk(x, nx, W, 0, xs, &xbar);
+    }
+  }
   for (int c = 0; c < J; ++c) {
     const int j0 = c * W;
     const int jn = min(W, nx - j0);
     const long long e1 = __ldg(po + c + 1);
     const unsigned pe = (unsigned)(min(max(e1, a0 + (long long)p), s1) - a0);   // end of this part
-    __syncthreads();   // the previous chunk is no longer read (and acc is initialised)
-    if ((((uintptr_t)(x + j0)) & 15) == 0) {
-      const int n4 = jn >> 2;
-      for (int k = t; k < n4; k += T) cp_async16(xs + 4 * k, x + j0 + 4 * k);
-      for (int k = 4 * n4 + t; k < jn; k += T) xs[k] = __ldcg(x + j0 + k);
+    if (bulk) {
+      ell_wait_chunk(&xbar, (unsigned)(c & 1), ctrl);
     } else {
-      for (int k = t; k < jn; k += T) xs[k] = __ldcg(x + j0 + k);
+      __syncthreads();   // the previous chunk is no longer read (and acc is initialised)
+      if ((((uintptr_t)(x + j0)) & 15) == 0) {
+        const int n4 = jn >> 2;
+        for (int k = t; k < n4; k += T) cp_async16(xs + 4 * k, x + j0 + 4 * k);
+        for (int k = 4 * n4 + t; k < jn; k += T) xs[k] = __ldcg(x + j0 + k);
+      } else {
+        for (int k = t; k < jn; k += T) xs[k] = __ldcg(x + j0 + k);
+      }
+      cp_async_wait_all();   // also lands the stream windows issued so far
+      __syncthreads();
     }
-    cp_async_wait_all();   // also lands the stream windows issued so far
-    __syncthreads();
     while (p < pe) {
       if (Hc < 0) {
         ell_need(R, p, min(p + kEllHdr, pe));
@@ -493,6 +550,17 @@ __device__ __forceinline__ void ell_pass(const unsigned char* __restrict__ pack,
       Hc = Hn > 0 ? Hn : -1;
     }
     p = max(p, pe);
+    if (bulk) {   // this warp is done with chunk c; the last one to finish issues chunk c + 1
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_block();   // the warp's reads of xs precede the count
+        const int prev = atomicAdd(&xdone, 1);
+        if (prev == kEllWarps * (c + 1) - 1 && c + 1 < J) {
+          fence_proxy_async_shared();   // those reads precede the bulk copy's writes
+          ell_issue_chunk(x, nx, W, c + 1, xs, &xbar);
+        }
+      }
+    }
   }
   cp_async_wait_all();   // nothing of the stream stays in flight
   __syncthreads();
