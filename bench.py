@@ -661,7 +661,7 @@ def _warm_start_leg(args, w, S, x, y, a, b, kd, logd, cold):
     data = []
     for k in range(args.ws_instances):
         wk = inputs.ot_gmm16(args.ws_n, seed=1000 + k)
-        inst, al, be, _ = WS.solve_targets(wk, w.eps, wk.s, seed=wk.seed, kdtype=kd)
+        inst, al, be, _ = WS.solve_targets(wk, w.eps, wk.s, seed=wk.seed, kdtype=kd, sampler=args.sampler)
         data.append((inst, al, be))
     t1 = time.perf_counter()
     net = WS.WarmStart(w.d, seed=5)
@@ -669,7 +669,8 @@ def _warm_start_leg(args, w, S, x, y, a, b, kd, logd, cold):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     st = torch.cuda.current_stream()
-    kw = dict(eps=w.eps, s=w.s, tol=TOL, max_iter=20000, dtype="f32", kdtype=kd, seed=w.seed, log_domain=logd)
+    kw = dict(eps=w.eps, s=w.s, tol=TOL, max_iter=20000, dtype="f32", kdtype=kd, seed=w.seed, log_domain=logd,
+              sampler=args.sampler)
     runs = []
     for rep in range(2):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -681,7 +682,22 @@ def _warm_start_leg(args, w, S, x, y, a, b, kd, logd, cold):
         e1.synchronize()
         runs.append((e0.elapsed_time(e1), r))
     ms, r = runs[-1]
-    return {"ms": round(ms, 3), "iters": r["iters"], "cold_iters": cold["iters"],
+    # the exact cost divisor alone (it synchronises), then the network's inference alone (both sides)
+    tc = time.perf_counter()
+    cm = S.cost_max(x, y)
+    cm_ms = (time.perf_counter() - tc) * 1e3
+    inst = net.instance(x, a, y, b, cm)
+    net.predict(inst)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(5):
+        net.predict(inst)
+    e1.record(st)
+    e1.synchronize()
+    inf_ms = e0.elapsed_time(e1) / 5
+    return {"ms": round(ms, 3), "sampler": args.sampler, "iters": r["iters"], "cold_iters": cold["iters"],
+            "cost_max_ms": round(cm_ms, 3), "inference_ms": round(inf_ms, 3),
+            "inference_share": round(inf_ms / ms, 4),
             "obj_rel_diff_vs_cold": abs(r["obj"] - cold["obj"]) / abs(cold["obj"]),
             "ms_iterations": round(r["ms_iter"], 3), "cold_ms_iterations": round(cold["ms_iter"], 3),
             "training": {"instances": args.ws_instances, "n": args.ws_n, "steps": args.ws_steps,

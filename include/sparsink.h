@@ -430,6 +430,16 @@ sps_status sps_mlp_sync_bf16(const float* params, void* params_bf16, int32_t d, 
  * of SPS_COST_MAXNORM), read back to the host. */
 sps_status sps_cost_max(const float* x, int32_t n, const float* y, int32_t m, int32_t d, double* cost_max,
                         void* ws, sps_stream stream);
+/* The same maximum, bit for bit, with a caller workspace (device memory) of
+ * sps_cost_max_workspace_bytes(n, m, d) bytes (0: invalid sizes; 1 <= d <= 16).
+ * Above 1e8 pairs it evaluates only the pairs that can reach the maximum, as
+ * the solver's own sketch does (grid cells bounded by their boxes for d <= 4,
+ * radial bounds about the bounding-box centre for d > 4; the full sweep after
+ * an overflowing candidate list), instead of all n m of them.  A smaller
+ * workspace returns SPS_ERR_WORKSPACE; the call synchronises its stream. */
+size_t sps_cost_max_workspace_bytes(int32_t n, int32_t m, int32_t d);
+sps_status sps_cost_max_ws(const float* x, int32_t n, const float* y, int32_t m, int32_t d, double* cost_max,
+                           void* ws, size_t ws_bytes, sps_stream stream);
 /* Predicted potentials alpha^ (n) and beta^ (m). */
 sps_status sps_mlp_infer(const void* params_bf16, const sps_mlp_instance* inst, float* alpha_out,
                          float* beta_out, void* ws, sps_stream stream);

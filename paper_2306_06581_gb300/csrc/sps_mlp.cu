@@ -705,6 +705,46 @@ sps_status sps_cost_max(const float* x, int32_t n, const float* y, int32_t m, in
   return SPS_OK;
 }
 
+// The same maximum with a caller workspace sized for the pruned search of the
+// solver's sketch (sps_costmax.cu): above 1e8 pairs only the cell pairs (d <= 4)
+// or radial candidate sets (d > 4) that can reach the maximum are evaluated,
+// the full sweep running only when the candidate list overflowed.
+constexpr double kPrunePairs = 1e8;
+constexpr size_t kCmScalBytes = 4096;   // SketchScalars at offset 0, then the scratch
+static_assert(sizeof(SketchScalars) <= kCmScalBytes, "cost max scalars");
+
+size_t sps_cost_max_workspace_bytes(int32_t n, int32_t m, int32_t d) {
+  if (n < 1 || m < 1 || d < 1 || d > 16) return 0;
+  const bool prune = (double)n * (double)m > kPrunePairs;
+  return 256 + kCmScalBytes + (prune ? cost_max_scratch_bytes(n, m, d) : 0);
+}
+
+sps_status sps_cost_max_ws(const float* x, int32_t n, const float* y, int32_t m, int32_t d, double* cost_max,
+                           void* ws, size_t ws_bytes, sps_stream stream) {
+  if (!x || !y || !cost_max || !ws || n < 1 || m < 1 || d < 1 || d > 16) { set_error("bad cost_max arguments"); return SPS_ERR_INVALID_ARG; }
+  const size_t need = sps_cost_max_workspace_bytes(n, m, d);
+  if (ws_bytes < need) { set_error("cost_max workspace too small: %zu < %zu", ws_bytes, need); return SPS_ERR_WORKSPACE; }
+  cudaStream_t st = (cudaStream_t)stream;
+  char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  SketchScalars* sc = (SketchScalars*)base;
+  SPS_TRY(cuda_fail(cudaMemsetAsync(sc, 0, sizeof(SketchScalars), st), "memset"));
+  bool full = true;
+  if ((double)n * (double)m > kPrunePairs) {
+    const int* overflow = nullptr;
+    SPS_TRY(launch_cost_max_pruned(x, y, n, m, d, sc, base + kCmScalBytes, &overflow, st));
+    int ov = 1;
+    SPS_TRY(cuda_fail(cudaMemcpyAsync(&ov, overflow, sizeof(int), cudaMemcpyDeviceToHost, st), "read back"));
+    SPS_TRY(cuda_fail(cudaStreamSynchronize(st), "synchronize"));
+    full = ov != 0;
+  }
+  if (full) SPS_TRY(launch_cost_max_points(x, n, y, m, d, sc, st));
+  float f = 0.0f;
+  SPS_TRY(cuda_fail(cudaMemcpyAsync(&f, &sc->dmax32, sizeof(f), cudaMemcpyDeviceToHost, st), "read back"));
+  SPS_TRY(cuda_fail(cudaStreamSynchronize(st), "synchronize"));
+  *cost_max = (double)f;
+  return SPS_OK;
+}
+
 sps_status sps_mlp_infer(const void* params_bf16, const sps_mlp_instance* I, float* alpha_out, float* beta_out,
                          void* ws, sps_stream stream) {
   SPS_TRY(check_inputs(I));

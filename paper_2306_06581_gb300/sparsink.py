@@ -489,11 +489,15 @@ def _mlp_lib():
         L.sps_mlp_init.argtypes = [V, V, C.c_int32, C.c_uint64, V]
         L.sps_mlp_sync_bf16.argtypes = [V, V, C.c_int32, V]
         L.sps_cost_max.argtypes = [V, C.c_int32, V, C.c_int32, C.c_int32, V, V, V]
+        L.sps_cost_max_workspace_bytes.argtypes = [C.c_int32, C.c_int32, C.c_int32]
+        L.sps_cost_max_workspace_bytes.restype = S_
+        L.sps_cost_max_ws.argtypes = [V, C.c_int32, V, C.c_int32, C.c_int32, V, V, S_, V]
         L.sps_mlp_infer.argtypes = [V, V, V, V, V, V]
         L.sps_mlp_gauge_fix.argtypes = [V, V, V, V, V]
         L.sps_mlp_grad.argtypes = [V, V, V, V, V, V, V, V, V]
         L.sps_mlp_adam.argtypes = [V, V, V, V, V, C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float, V]
-        for f in ("sps_mlp_init", "sps_mlp_sync_bf16", "sps_cost_max", "sps_mlp_infer", "sps_mlp_gauge_fix",
+        for f in ("sps_mlp_init", "sps_mlp_sync_bf16", "sps_cost_max", "sps_cost_max_ws", "sps_mlp_infer",
+                  "sps_mlp_gauge_fix",
                   "sps_mlp_grad", "sps_mlp_adam"):
             getattr(L, f).restype = C.c_int
         L._mlp_ready = True
@@ -508,15 +512,26 @@ def _mlp_ws(device):
     return torch.empty(int(_mlp_lib().sps_mlp_workspace_bytes()) + 256, dtype=torch.uint8, device=device)
 
 
-def cost_max(x, y, device=None):
-    """Exact maximum of the binary32 squared distances (the SPS_COST_MAXNORM divisor)."""
+def cost_max(x, y, device=None, full_sweep=False):
+    """Exact maximum of the binary32 squared distances (the SPS_COST_MAXNORM
+    divisor): by default through sps_cost_max_ws (the pruned search above 1e8
+    pairs, in a workspace allocated here), or with full_sweep=True through
+    sps_cost_max (every pair)."""
     dev = torch.device(device) if device is not None else (x.device if isinstance(x, torch.Tensor) and x.is_cuda
                                                            else torch.device("cuda"))
     xd = _dev(x, torch.float32, dev).contiguous()
     yd = _dev(y, torch.float32, dev).contiguous()
     out = C.c_double(0.0)
-    st = _mlp_lib().sps_cost_max(_ptr(xd), xd.shape[0], _ptr(yd), yd.shape[0], xd.shape[1], C.byref(out),
-                                 _ptr(_mlp_ws(dev)), _stream())
+    L = _mlp_lib()
+    n, m, d = xd.shape[0], yd.shape[0], xd.shape[1]
+    if full_sweep:
+        st = L.sps_cost_max(_ptr(xd), n, _ptr(yd), m, d, C.byref(out), _ptr(_mlp_ws(dev)), _stream())
+    else:
+        nbytes = L.sps_cost_max_workspace_bytes(n, m, d)
+        if nbytes == 0:
+            raise SpsError(SPS_ERR_INVALID_ARG, "bad cost_max sizes")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        st = L.sps_cost_max_ws(_ptr(xd), n, _ptr(yd), m, d, C.byref(out), _ptr(ws), nbytes, _stream())
     _check(st, allow_not_converged=False)
     return out.value
 

@@ -2,7 +2,7 @@
 forward, backward and optimiser step runs in the library's CUDA kernels).
 
 Targets are the potentials that Spar-Sink itself returns on seeded training
-instances (stabilised iterations, cost divisor from sps_cost_max), with the
+instances (stabilised iterations, cost divisor from sps_cost_max_ws), with the
 OT gauge fixed (sum a alpha = sum b beta).  A trained WarmStart predicts
 starting potentials for sps_params.init_alpha / init_beta.
 """
@@ -50,7 +50,7 @@ class WarmStart:
         return loss
 
 
-def solve_targets(w, eps, s, tol=1e-5, max_iter=20000, seed=0x5EED, kdtype="f32"):
+def solve_targets(w, eps, s, tol=1e-5, max_iter=20000, seed=0x5EED, kdtype="f32", sampler="element"):
     """Spar-Sink on one instance; returns the instance's device tensors, the
     cost divisor and the gauge-fixed potentials (the training targets)."""
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -58,7 +58,7 @@ def solve_targets(w, eps, s, tol=1e-5, max_iter=20000, seed=0x5EED, kdtype="f32"
     x, y, a, b = t(w.x), t(w.y), t(w.a), t(w.b)
     cm = S.cost_max(x, y)
     r = S.spar_sink_ot(a, b, x, y, eps=eps, s=s, tol=tol, max_iter=max_iter, dtype="f32", kdtype=kdtype,
-                       seed=seed, cost_norm=S.COST_SCALE, cost_scale=cm, log_domain=1)
+                       seed=seed, cost_norm=S.COST_SCALE, cost_scale=cm, log_domain=1, sampler=sampler)
     inst = S.mlp_instance(x, a, y, b, cm, eps)
     al, be = r["alpha"].clone(), r["beta"].clone()
     S.mlp_gauge_fix(inst, al, be)

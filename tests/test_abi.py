@@ -211,6 +211,15 @@ def test_warm_start_arguments_validated(S):
         assert st == S.SPS_ERR_INVALID_ARG, e
         assert "eps" in S.last_error()
     assert L.sps_cost_max(f, 0, f, 5, 3, f, f, None) == S.SPS_ERR_INVALID_ARG
+    # the workspace form: sizes, then a workspace below the required size, refused before any launch
+    wb = L.sps_cost_max_workspace_bytes
+    assert wb(0, 5, 3) == 0 and wb(5, 5, 0) == 0 and wb(5, 5, 17) == 0
+    small, big3, big10 = wb(100, 100, 3), wb(20000, 20000, 3), wb(20000, 20000, 10)
+    assert 0 < small < big3 and 0 < small < big10      # the pruned search's scratch only above 1e8 pairs
+    assert L.sps_cost_max_ws(f, 100, f, 100, 3, f, f, small - 1, None) == S.SPS_ERR_WORKSPACE
+    assert "workspace" in S.last_error()
+    assert L.sps_cost_max_ws(f, 100, f, 0, 3, f, f, small, None) == S.SPS_ERR_INVALID_ARG
+    assert L.sps_cost_max_ws(None, 100, f, 100, 3, f, f, small, None) == S.SPS_ERR_INVALID_ARG
 
 
 def test_noalloc_refusals_need_no_device(S):

@@ -47,6 +47,21 @@ def test_cost_max_reproduces_maxnorm(S):
     assert r1["nnz"] == r2["nnz"] and r1["iters"] == r2["iters"] and r1["obj"] == r2["obj"]
 
 
+@pytest.mark.parametrize("d", [3, 10])
+def test_cost_max_pruned_equals_full_sweep(S, d):
+    # above 1e8 pairs the workspace form evaluates only the pairs that can reach the maximum (grid cells
+    # for d <= 4, radial bounds for d > 4); the maximum is the same binary32 value as every pair's
+    n, m = 12000, 10000
+    g = torch.Generator().manual_seed(40 + d)
+    x = torch.randn(n, d, generator=g).cuda()
+    y = (0.5 * torch.rand(m, d, generator=g) + 0.25).cuda()
+    pruned = S.cost_max(x, y)
+    full = S.cost_max(x, y, full_sweep=True)
+    assert pruned == full
+    ref = max(float(((x[i:i + 1000, None] - y[None]) ** 2).sum(-1).max()) for i in range(0, n, 1000))
+    assert abs(pruned - ref) <= 4e-7 * ref
+
+
 def test_inference_matches_reference(S, inst_data):
     from paper_2306_06581_gb300.warmstart import WarmStart
     x, a, y, b, cm = inst_data
