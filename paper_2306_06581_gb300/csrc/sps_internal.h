@@ -132,6 +132,7 @@ constexpr int kEllHdr = 80;                        // bytes of a group header
 constexpr int kEllBins = 256;                      // run-length bins of the sort (the last one holds >= 255)
 constexpr int kEllRing = 4096;                     // ring of one warp (a power of two)
 constexpr int kEllWin = 1024;                      // window: two 16-byte copies per lane
+constexpr int kEllPrefetch = 8;                    // windows of a warp's stream prefetched into L2 beyond its ring
 __host__ __device__ constexpr long long ell_step_bytes(int vb) { return 32LL * (2 + vb); }
 __host__ __device__ constexpr long long ell_group_bytes(int h, int vb) { return kEllHdr + (long long)h * ell_step_bytes(vb); }
 // Dynamic shared memory of the staged kernel: the chunk of the gathered

@@ -369,7 +369,14 @@ struct EllRing {
   unsigned char* ring;
   unsigned r0, r1;            // the stream, relative
   unsigned issued, nwin;
+  unsigned pf;                // windows below pf have been issued or prefetched into L2
 };
+
+// Bulk prefetch of [g, g + bytes) into L2 (16-byte aligned address, size a
+// multiple of 16); a hint with no completion and no shared-memory effect.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* g, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(g), "r"(bytes) : "memory");
+}
 
 // Make the relative bytes below `end` readable by the warp: issue the windows
 // that the read position `cons` allows (every byte below it has been read by
@@ -387,6 +394,17 @@ __device__ __forceinline__ void ell_need(EllRing& R, unsigned cons, unsigned end
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     ++R.issued;
+  }
+  if (kEllPrefetch > 0) {
+    // the next kEllPrefetch windows start their way from DRAM into L2, so that a
+    // window's copy into the ring mostly waits for L2 rather than DRAM: the bytes
+    // in flight are no longer bounded by the ring
+    const unsigned from = max(R.pf, R.issued), plim = min(R.nwin, R.issued + kEllPrefetch);
+    if (from < plim) {
+      const unsigned b0 = max(from * kEllWin, R.r0), b1 = min(plim * kEllWin, R.r1);
+      if ((threadIdx.x & 31) == 0 && b1 > b0) prefetch_l2_bulk(R.src + b0, b1 - b0);
+      R.pf = plim;
+    }
   }
   cp_async_wait_n((int)R.issued - 1 - (int)((end - 1) / kEllWin));
   __syncwarp();
@@ -465,6 +483,7 @@ __device__ __forceinline__ void ell_pass(const unsigned char* __restrict__ pack,
   R.r1 = (unsigned)(s1 - a0);
   R.nwin = R.r1 > R.r0 ? (R.r1 - 1) / kEllWin + 1 : 0;
   R.issued = 0;
+  R.pf = 0;
   ell_need(R, R.r0, R.r0 + 16);   // the first windows (the wait is for the first one only)
   const unsigned l2 = 2u * lane, lv = 64u + (unsigned)vb * lane;
   unsigned p = R.r0;   // read position (uniform over the warp)
