@@ -16,7 +16,7 @@ from paper_2306_06581_gb300 import inputs  # noqa: E402
 
 
 @pytest.mark.parametrize("make,expect", [(inputs.uot_n20000, 1.6e6), (inputs.ot_n200000, 5.418e8),
-                                         (inputs.ot_n1000000, 3.1477e9)])
+                                         (inputs.ot_n1000000, 3.1486e9)])
 def test_traffic_from_committed_profiles(make, expect):
     w = make()
     traffic, src_name = bench._traffic(w.name)
