@@ -101,7 +101,6 @@ static void plan_staging(int n, int m, int mode, int kd, Layout* L, Take& take) 
     L->el_pbytes[s] = take(parts[s] * 8);
     L->el_poff[s] = take((parts[s] + 1) * 8);
     L->el_tmp[s] = take((size_t)rows[s] * 12);
-    L->el_perm[s] = take((size_t)L->cap * 4);
     L->el_pack[s] = take((size_t)L->el_pack_cap);
     L->el_logk[s] = take((size_t)(L->el_pack_cap / vb) * 4);
   }

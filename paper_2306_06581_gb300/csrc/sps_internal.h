@@ -93,7 +93,6 @@ struct Layout {
   size_t el_poff[2];                //   their exclusive prefix sums [parts + 1]
   size_t el_tmp[2];                 //   layout scratch: (row, length, start) of every run of one slice
   size_t el_pack[2];                //   the grouped copy
-  size_t el_perm[2];                //   CSR (CSC) position -> value slot of the grouped copy
   size_t el_logk[2];                //   log K~ by value slot (-inf in padding), for absorptions in copy order
   int64_t el_pack_cap;              //   bytes planned for one grouped copy
   size_t pad_ofs, pad_col, pad_val, pad_lv, zsum, csum;   // single-pass sketch (0: two passes)

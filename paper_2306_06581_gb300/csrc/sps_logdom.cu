@@ -70,7 +70,6 @@ struct LogArgs {
   long long* el_poff[2];
   int* el_tmp[2];
   unsigned char* el_pack[2];
-  int* el_perm[2];
   float* el_logk[2];               // log K~ by value slot of the grouped copy (-inf in padding)
   long long pack_lim;              // bytes of one grouped copy
   long long nnz_lim;               // elements of the CSR / CSC arrays (bounds checks)
@@ -152,8 +151,8 @@ __device__ __forceinline__ void absorb_segment(int lo, int hi, const int* idx, c
   if (lane == 0) *e_out = e;
 }
 
-// Where K' of one side goes: the grouped copy through perm (staged passes) or
-// val / valT in CSR / CSC order.
+// Where K' of one side goes when it is absorbed in CSR / CSC order: val /
+// valT (the grouped copies are absorbed in copy order, by ell_absorb).
 template <typename V>
 struct AbsorbOut {
   V* out;
@@ -162,9 +161,10 @@ struct AbsorbOut {
 };
 template <typename V>
 __device__ __forceinline__ AbsorbOut<V> absorb_out(const LogArgs& A, int side) {
-  if (A.stage && !*(volatile int*)&A.ctrl->ell_overflow)
-    return {reinterpret_cast<V*>(A.el_pack[side]), A.el_perm[side], A.pack_lim / (long long)sizeof(V)};
   return {reinterpret_cast<V*>(side ? A.valT : A.val), nullptr, A.nnz_lim};
+}
+__device__ __forceinline__ bool grouped_copies(const LogArgs& A) {
+  return A.stage && !*(volatile int*)&A.ctrl->ell_overflow;
 }
 
 template <typename V>
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kT) k_absorb_all(LogArgs A, int t) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const AbsorbOut<V> R = absorb_out<V>(A, 0), C = absorb_out<V>(A, 1);
-  const bool grouped = R.perm != nullptr;   // the grouped copies were written by k_absorb_pack
+  const bool grouped = grouped_copies(A);   // the grouped copies were written by k_absorb_pack
   for (int i = gw; i < A.n && !grouped; i += nw)
     absorb_segment<V>(A.row_ptr[i], A.row_ptr[i + 1], A.col_idx, A.logval, A.alpha[i], A.beta, A.inv_eps, R.out,
                       A.erow + i, lane, R.perm, R.limit, A.ctrl);
@@ -802,15 +802,15 @@ __global__ void __launch_bounds__(1024) k_el_scan(long long P, const long long* 
 // The grouped copy of every part (one warp a slice, chunk by chunk): the runs
 // in sorted order (a bin's runs in row order) go to the slice's scratch as
 // (block-local row, length, first CSR position), then each group of 32 is
-// written: header, indices (padding 0), padding values 0, and perm of every
-// element (its value slot; absorption writes K' there).  A part whose bytes
+// written: header, indices (padding 0), padding values 0 and log K~ by value
+// slot (absorption writes K' over every slot, in copy order).  A part whose bytes
 // disagree with k_el_size sets ell_overflow.
 template <typename V>
 __global__ void __launch_bounds__(256) k_el_fill(int rows, int R, int nblk, int J, int W, const int* __restrict__ seg,
                                                  const int* __restrict__ idx, const int* __restrict__ S,
                                                  const long long* __restrict__ poff, int* __restrict__ tmp,
-                                                 unsigned char* __restrict__ pack, int* __restrict__ perm,
-                                                 const float* __restrict__ logv, float* __restrict__ logk,
+                                                 unsigned char* __restrict__ pack, const float* __restrict__ logv,
+                                                 float* __restrict__ logk,
                                                  long long nnz_lim, long long pack_lim, Ctrl* ctrl) {
   constexpr int vb = (int)sizeof(V);
   __shared__ int hist_sh[8][kEllBins];
@@ -915,7 +915,6 @@ __global__ void __launch_bounds__(256) k_el_fill(int rows, int R, int nblk, int 
             const long long e = (long long)src + k;
             if (okv[u]) {
               q = (unsigned short)(qv[u] - c * W);
-              perm[e] = (int)slot;
               lk = lv[u];
             } else {
               oob(ctrl, 9, e);
@@ -1305,7 +1304,6 @@ LogArgs make_log_args(const ProbDev& pd, const Layout& L, char* ws, const IterCf
     A.el_poff[s] = A.stage ? at<long long>(ws, L.el_poff[s]) : nullptr;
     A.el_tmp[s] = A.stage ? at<int>(ws, L.el_tmp[s]) : nullptr;
     A.el_pack[s] = A.stage ? at<unsigned char>(ws, L.el_pack[s]) : nullptr;
-    A.el_perm[s] = A.stage ? at<int>(ws, L.el_perm[s]) : nullptr;
     A.el_logk[s] = A.stage ? at<float>(ws, L.el_logk[s]) : nullptr;
   }
   A.pack_lim = A.stage ? L.el_pack_cap : 0;
@@ -1437,7 +1435,7 @@ void first_iteration_v(const LogArgs& A, const IterCfg& ic, const void* al0, con
   k_lse_half<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.col_ptr, A.row_idx, A.logvalT, A.alpha, A.b,
                                                          A.beta, A.eps, A.phi);
   if (A.stage) {
-    // chunk pointers, then the grouped copies (the absorption below writes K' through perm)
+    // chunk pointers, then the grouped copies (the absorption below writes K' in copy order)
     k_chunk_ptrs<<<grid1((int64_t)A.n * 32, kT), kT, 0, st>>>(A.n, A.row_ptr, A.col_idx, A.W, A.Jr, (int*)A.seg_r);
     k_chunk_ptrs<<<grid1((int64_t)A.m * 32, kT), kT, 0, st>>>(A.m, A.col_ptr, A.row_idx, A.W, A.Jc, (int*)A.seg_c);
     for (int side = 0; side < 2; ++side) {
@@ -1454,7 +1452,7 @@ void first_iteration_v(const LogArgs& A, const IterCfg& ic, const void* al0, con
                                     side);
       k_el_fill<V><<<(slices + 7) / 8, 256, 0, st>>>(rows, R, A.sblk, J, A.W, seg, idx, A.el_slice[side],
                                                      A.el_poff[side], A.el_tmp[side], A.el_pack[side],
-                                                     A.el_perm[side], side ? A.logvalT : A.logval,
+                                                     side ? A.logvalT : A.logval,
                                                      A.el_logk[side], A.nnz_lim, A.pack_lim, A.ctrl);
     }
   }
